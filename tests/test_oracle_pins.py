@@ -1,0 +1,400 @@
+"""Pins of the CPU oracle against what the paper's definitions and plain
+mathematics fix, independently of the oracle's own code:
+
+* every exact predicate on hand-derived boundary configurations (equality is
+  accepted, the next float32 constant on the strict side rejects);
+* every predicate against its geometric meaning evaluated another way
+  (angles, circumcentres, distances in float64) on random hits away from the
+  boundary;
+* the graph stages (doublets, Fishbone, CA connection, roots, DFS, cleaning)
+  against brute-force enumeration of hit sequences on a small event;
+* 100 % finding of noiseless helices (Sec. 4.2's efficiency definition);
+* the broken-line fit (Sec. 3.4) against exact helices (chi2 = 0, parameters
+  equal to the truth), the rigid limit (closed-form least squares), and the
+  statistics of fits of simulated scattered tracks (pulls ~ N(0,1)).
+"""
+import dataclasses
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import cuts as CU
+from synth import events as E
+from synth import geometry as G
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DISK = [0] * 4 + [1] * 6
+F32 = np.float32
+
+
+# ------------------------------------------------------------ boundaries
+def _golden_boundaries():
+    out = []
+    with open(os.path.join(HERE, "golden", "predicate_boundaries.txt")) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            t = line.split()
+            name, k = t[0], float(t[1])
+            v = [float(a) for a in t[2:]]
+            out.append((name, k, np.array(v, dtype=np.float32).reshape(-1, 4)))
+    return out
+
+
+# direction in which a larger constant loosens the cut
+_LOOSER_UP = dict(phiw=True, zip=True, pt=False, rz=True, curv=False, beamspot=True, dz=True, fb=True)
+
+
+@pytest.mark.parametrize("name,k,hits", _golden_boundaries(), ids=lambda v: v if isinstance(v, str) else "")
+def test_predicate_boundaries(name, k, hits):
+    assert oracle.pred(name, hits, k), f"{name} must accept exactly on its boundary"
+    strict = np.nextafter(F32(k), F32(0) if _LOOSER_UP[name] else F32(np.inf))
+    assert not oracle.pred(name, hits, float(strict)), f"{name} must reject one ulp past the boundary"
+
+
+# ------------------------------------------------- geometric meanings (f64)
+def _snap(v):
+    return np.rint(np.asarray(v, dtype=np.float64) * 16384.0) / 16384.0
+
+
+def _hit(rng, r_lo, r_hi, z_lo, z_hi, phi_c=0.0, phi_w=0.3):
+    r = rng.uniform(r_lo, r_hi)
+    ph = phi_c + rng.uniform(-phi_w, phi_w)
+    x, y, z = _snap(r * math.cos(ph)), _snap(r * math.sin(ph)), _snap(rng.uniform(z_lo, z_hi))
+    return np.array([x, y, z, _snap(math.hypot(x, y))])
+
+
+def _circum(a, b, c):
+    A = 2 * np.array([[b[0] - a[0], b[1] - a[1]], [c[0] - a[0], c[1] - a[1]]])
+    rhs = np.array([b[0] ** 2 + b[1] ** 2 - a[0] ** 2 - a[1] ** 2,
+                    c[0] ** 2 + c[1] ** 2 - a[0] ** 2 - a[1] ** 2])
+    ctr = np.linalg.solve(A, rhs)
+    return ctr, float(np.hypot(a[0] - ctr[0], a[1] - ctr[1]))
+
+
+def _meaning(name, h):
+    """Return (value, threshold_transform) so that accept <=> value <= f(k)."""
+    if name == "phiw":
+        i, o = h
+        d = math.atan2(o[1], o[0]) - math.atan2(i[1], i[0])
+        d = (d + math.pi) % (2 * math.pi) - math.pi
+        return abs(d), lambda k: math.atan(math.sqrt(k)) if abs(d) < math.pi / 2 else -1
+    if name in ("zip", "dz"):
+        i, o = (h[0], h[1]) if name == "zip" else (h[0], h[2])
+        if o[3] <= i[3]:
+            return 1.0, lambda k: -1.0
+        zint = i[2] - i[3] * (o[2] - i[2]) / (o[3] - i[3])
+        return abs(zint), lambda k: k
+    if name == "pt":
+        i, o = h
+        _, R = _circum(np.zeros(2), i[:2], o[:2])
+        return -R, lambda k: -math.sqrt(k) / 2
+    if name == "curv":
+        _, R = _circum(h[0][:2], h[1][:2], h[2][:2])
+        return -R, lambda k: -math.sqrt(k) / 2
+    if name == "beamspot":
+        ctr, R = _circum(h[0][:2], h[1][:2], h[2][:2])
+        pw = ctr @ ctr - R * R
+        return abs(pw) / (2 * R), lambda k: math.sqrt(k)
+    if name == "rz":
+        a, b, c = [np.array([p[3], p[2]]) for p in h]
+        ac = c - a
+        dist = abs(ac[0] * (b - a)[1] - ac[1] * (b - a)[0]) / np.linalg.norm(ac)
+        return dist, lambda k: math.sqrt(k)
+    if name == "fb":
+        h1, h2, hh = [p[:3] for p in h]
+        u, v = h1 - hh, h2 - hh
+        cs = u @ v / (np.linalg.norm(u) * np.linalg.norm(v))
+        sn = np.linalg.norm(np.cross(u, v)) / (np.linalg.norm(u) * np.linalg.norm(v))
+        return (sn if cs > 0 else 2.0), lambda k: math.sqrt(k)
+    raise KeyError(name)
+
+
+def _random_case(name, rng):
+    if name in ("phiw", "pt"):
+        i = _hit(rng, 2.8, 7, -20, 20)
+        o = _hit(rng, 7.5, 16, -26, 26)
+        return [i, o]
+    if name == "zip":
+        return [_hit(rng, 2.8, 7, -20, 20), _hit(rng, 7.5, 16, -26, 26)]
+    if name in ("rz", "curv", "beamspot", "dz"):
+        a = _hit(rng, 2.8, 3.2, -10, 10, phi_w=0.05)
+        b = _hit(rng, 6.6, 7.0, a[2] * 2.2 - 3, a[2] * 2.2 + 3, phi_w=0.08)
+        c = _hit(rng, 10.6, 11.2, a[2] * 3.7 - 5, a[2] * 3.7 + 5, phi_w=0.15)
+        return [a, b, c]
+    if name == "fb":
+        hh = _hit(rng, 10, 11, -5, 5, phi_w=0.1)
+        d = np.array([hh[0], hh[1], hh[2]]) * -0.4
+        h1 = _snap(hh[:3] + d + rng.normal(0, 0.003, 3))
+        h2 = _snap(hh[:3] + 1.1 * d + rng.normal(0, 0.003, 3))
+        return [np.append(h1, _snap(np.hypot(*h1[:2]))), np.append(h2, _snap(np.hypot(*h2[:2]))), hh]
+    raise KeyError(name)
+
+
+_K_RANGE = dict(phiw=(1e-3, 0.05), zip=(2.0, 20.0), pt=(1e2, 1e5), rz=(1e-3, 30.0),
+                curv=(1e2, 1e5), beamspot=(1e-4, 1e-1), dz=(0.02, 3.0), fb=(1e-7, 1e-4))
+
+
+@pytest.mark.parametrize("name", list(_K_RANGE))
+def test_predicate_meaning(name):
+    rng = np.random.default_rng(20081346 + len(name))
+    n_acc = n_rej = 0
+    for _ in range(1500):
+        h = _random_case(name, rng)
+        lo, hi = _K_RANGE[name]
+        k = float(F32(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+        val, thr = _meaning(name, h)
+        t = thr(k)
+        if abs(val - t) <= 1e-9 * max(1.0, abs(t)):
+            continue  # too close to call in float64
+        want = val <= t
+        got = oracle.pred(name, np.array(h, dtype=np.float32), k)
+        assert got == want, (name, h, k, val, t)
+        n_acc += want
+        n_rej += not want
+    assert n_acc > 50 and n_rej > 50, (n_acc, n_rej)
+
+
+# ------------------------------------------------- graph vs brute force
+def _small_event():
+    cfg = dataclasses.replace(E.CONFIGS[2], name="small", index=90, pileup=0, hard_tracks=0,
+                              fixed_tracks=40, noise_frac=0.15)
+    return E.make_batch(cfg)
+
+
+def test_graph_stages_against_brute_force():
+    b = _small_event()
+    cuts = CU.cuts_for_config(2)
+    ml = G.module_layer_table()
+    res = oracle.run(b, cuts, CU.FIT_PARAMS, ml, DISK, stage=3)
+    lay = ml[b["module"]]
+    H = np.stack([b["x"], b["y"], b["z"], b["r"]], 1).astype(np.float32)
+    n = H.shape[0]
+    # doublets
+    cells = {}
+    for p, pp in enumerate(cuts["pairs"]):
+        for o in np.nonzero(lay == pp["outer"])[0]:
+            for i in np.nonzero(lay == pp["inner"])[0]:
+                if not (pp["zlo"] <= b["z"][i] <= pp["zhi"]):
+                    continue
+                hh = H[[i, o]]
+                if (oracle.pred("zip", hh, pp["zmax"]) and oracle.pred("phiw", hh, pp["tan2_dphi"])
+                        and oracle.pred("pt", hh, pp["k_pt"])):
+                    cells[(int(i), int(o))] = p
+    got = {(int(c[0]), int(c[1])): int(c[2]) for c in res["cells"]}
+    assert got == cells
+    # Fishbone by definition
+    alive = {}
+    for (i, o) in cells:
+        dead = False
+        for (j, o2) in cells:
+            if o2 != o or j == i or lay[j] != lay[i]:
+                continue
+            if not oracle.pred("fb", H[[i, j, o]], cuts["fishbone_eps2"]):
+                continue
+            li = float(np.sum((H[i, :3].astype(np.float64) - H[o, :3]) ** 2))
+            lj = float(np.sum((H[j, :3].astype(np.float64) - H[o, :3]) ** 2))
+            if lj < li or (lj == li and j < i):
+                dead = True
+        alive[(i, o)] = not dead
+    got_alive = {(int(c[0]), int(c[1])): bool(a) for c, a in zip(res["cells"], res["cell_alive"])}
+    assert got_alive == alive
+    live = {c for c, a in alive.items() if a}
+
+    def ca_ok(a, bb, c):
+        reg = cuts["region"][1 if lay[bb] >= 4 else 0]
+        h3 = H[[a, bb, c]]
+        return (oracle.pred("dz", h3, reg["zmax"]) and oracle.pred("rz", h3, reg["tol_rz2"])
+                and oracle.pred("curv", h3, reg["k_curv"]) and oracle.pred("beamspot", h3, reg["rmax2"]))
+
+    edges = {(a, bb, c) for (a, bb) in live for (b2, c) in live if b2 == bb and ca_ok(a, bb, c)}
+    C = res["cells"]
+    got_edges = {(int(C[e0][0]), int(C[e0][1]), int(C[e1][1])) for e0, e1 in res["edges"]}
+    assert got_edges == edges
+    # maximal paths from roots by enumeration of hit sequences
+    nxt = {}
+    for (a, bb, c) in edges:
+        nxt.setdefault((a, bb), []).append(c)
+    has_in = {(bb, c) for (a, bb, c) in edges}
+    paths = set()
+
+    def extend(seq):
+        ext = nxt.get((seq[-2], seq[-1]), [])
+        if not ext or len(seq) == oracle.NMAX:
+            if len(seq) >= 3:
+                paths.add(tuple(int(v) for v in seq))
+            if not ext:
+                return
+            return
+        for c in ext:
+            extend(seq + [c])
+
+    for (a, bb) in live:
+        root = lay[a] == 0 or (lay[a] in (1, 4, 7) and (a, bb) not in has_in)
+        if root:
+            extend([a, bb])
+    got_paths = {tuple(int(v) for v in res["tuple_hits"][t, :res["tuple_n"][t]])
+                 for t in range(len(res["tuple_n"]))}
+    assert got_paths == paths
+    assert len(paths) > 10
+    # shared-doublet cleaning by definition
+    best = {}
+    for p in paths:
+        for q in range(len(p) - 1):
+            best[p[q:q + 2]] = max(best.get(p[q:q + 2], 0), len(p))
+    keep = {p for p in paths if all(len(p) >= best[p[q:q + 2]] for q in range(len(p) - 1))}
+    got_keep = {tuple(int(v) for v in res["tuple_hits"][t, :res["tuple_n"][t]])
+                for t in range(len(res["tuple_n"])) if res["tuple_alive"][t]}
+    assert got_keep == keep
+
+
+def test_cleaning_keeps_only_the_quadruplet():
+    """A lone barrel track crossing all four layers yields the quadruplet
+    B1B2B3B4 and, through the skip pairs, the triplets B1B3B4 and B1B2B4, which
+    share a cell with it; only the quadruplet survives (Sec. 3.3)."""
+    cfg = dataclasses.replace(E.CONFIGS[1], name="one", index=91, fixed_tracks=1, eta_max=0.3,
+                              pt_min=5.0, pt_max=6.0)
+    b = E.make_batch(cfg)
+    assert b["x"].size == 4
+    res = oracle.run(b, CU.cuts_for_config(1), CU.FIT_PARAMS, G.module_layer_table(), DISK, stage=3)
+    lay = G.module_layer_table()[b["module"]]
+    seqs = sorted(tuple(int(lay[h]) for h in res["tuple_hits"][t, :res["tuple_n"][t]])
+                  for t in range(len(res["tuple_n"])))
+    assert seqs == [(0, 1, 2, 3), (0, 1, 3), (0, 2, 3)]
+    alive = [tuple(int(lay[h]) for h in res["tuple_hits"][t, :res["tuple_n"][t]])
+             for t in range(len(res["tuple_n"])) if res["tuple_alive"][t]]
+    assert alive == [(0, 1, 2, 3)]
+
+
+def test_full_finding_on_noiseless_helices():
+    """Config 1: every generated track leaving >= 3 hits is found exactly once
+    as a tuple holding all its hits; no surviving tuple mixes tracks."""
+    b = E.make_batch(1)
+    res = oracle.run(b, CU.cuts_for_config(1), CU.FIT_PARAMS, G.module_layer_table(), DISK, stage=4)
+    tid = b["track"]
+    counts = np.bincount(tid[tid >= 0], minlength=b["trk_pt"].size)
+    want = {t for t in range(counts.size) if counts[t] >= 3}
+    found = {}
+    for t in res["track_tuple"]:
+        hits = res["tuple_hits"][t, :res["tuple_n"][t]]
+        ids = set(tid[hits].tolist())
+        assert len(ids) == 1 and -1 not in ids, "fake track"
+        (k,) = ids
+        assert res["tuple_n"][t] == counts[k], "track found without all its hits"
+        found[k] = found.get(k, 0) + 1
+    assert set(found) == want
+    assert all(v == 1 for v in found.values()), "duplicates"
+    assert len(want) >= 30
+
+
+# ------------------------------------------------------------------ fit
+def _helix_points(kappa, phi0, tanl, d0, z0, s_list):
+    """Points of the exact helix with perigee parameters (kappa = q/rho,
+    positive bending clockwise; PCA = d0 (sin phi0, -cos phi0))."""
+    k = -kappa
+    px, py = d0 * math.sin(phi0), -d0 * math.cos(phi0)
+    out = []
+    for s in s_list:
+        h = 0.5 * k * s
+        f = s * (math.sin(h) / h if h != 0 else 1.0)
+        out.append((px + f * math.cos(phi0 + h), py + f * math.sin(phi0 + h), z0 + s * tanl))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("kappa", [1 / 30.0, -1 / 45.0, 1 / 400.0, -1 / 8000.0])
+@pytest.mark.parametrize("n", [3, 4, 5])
+def test_fit_exact_helix(kappa, n):
+    phi0, tanl, d0, z0 = 0.7, 1.3, 0.004, -2.5
+    s = [3.0, 6.9, 11.0, 15.5, 19.0][:n]
+    P = _helix_points(kappa, phi0, tanl, d0, z0, s)
+    disk = [0, 0, 1, 1, 1][:n]
+    p, cov, chi2, ndf, ex = oracle.fit(P[:, 0], P[:, 1], P[:, 2], disk, CU.FIT_PARAMS)
+    assert ndf == 2 * n - 5
+    assert chi2 < 1e-12
+    assert abs(p[0] - kappa) <= 1e-9 * abs(kappa)
+    assert abs(p[1] - phi0) < 1e-10 and abs(p[2] - tanl) < 1e-10
+    assert abs(p[3] - d0) < 1e-10 and abs(p[4] - z0) < 1e-10
+    # covariance diagonal positive
+    diag = cov[[0, 2, 5, 9, 14]]
+    assert np.all(diag > 0)
+
+
+def test_fit_rigid_limit_is_least_squares():
+    """With scattering almost switched off the s-z line fit is the weighted
+    straight-line regression of z on s and the circle fit is the weighted
+    parabola fit of the offsets, whose second coefficient is dk/2.  The
+    scattering variance is scaled by 1e-8: the broken line then departs from
+    the rigid solution by ~1e-7 of the measurement weight ratio while the
+    normal matrix (condition ~1e6 w.r.t. the measurement scale) stays well
+    inside double precision; at 1e-12 the condition number reaches 1e12 and
+    rounding, not the model, dominates."""
+    rng = np.random.default_rng(7)
+    s = np.array([3.0, 6.9, 11.0, 15.5, 19.0])
+    P = _helix_points(1 / 60.0, 0.2, 0.8, 0.0, 1.0, s)
+    P[:, 2] += rng.normal(0, 20e-4, 5)
+    nrm = np.stack([-np.sin(0.2 + 0 * s), np.cos(0.2 + 0 * s)], 1)
+    P[:, :2] += rng.normal(0, 10e-4, (5, 1)) * nrm
+    p, cov, chi2, ndf, ex = oracle.fit(P[:, 0], P[:, 1], P[:, 2], [0] * 5, CU.FIT_PARAMS, ms_scale=1e-8)
+    # arc lengths and offsets as the fit defines them (prefit through 0, 2, 4)
+    k0, psi0 = ex[2], ex[3]
+    d = P[:, :2] - P[0, :2]
+    dist = np.hypot(d[:, 0], d[:, 1])
+    sx = np.where(dist > 0, 2 * np.arcsin(np.clip(k0 * dist / 2, -1, 1)) / np.where(k0 != 0, k0, 1), 0)
+    t = np.array([math.cos(psi0), math.sin(psi0)])
+    nn = np.array([-t[1], t[0]])
+    X, Y = d @ t, d @ nn
+    U = k0 * (X * X + Y * Y) - 2 * Y
+    m = -U / (1 + np.sqrt(1 + k0 * U))
+    slope, icpt = np.polyfit(sx, P[:, 2], 1)          # equal weights (all barrel)
+    assert abs(p[2] - slope) < 1e-8
+    c2, c1, c0 = np.polyfit(sx, m, 2)
+    assert abs(ex[5] - 2 * c2) < 1e-10
+    res_line = P[:, 2] - (slope * sx + icpt)
+    res_circ = m - np.polyval([c2, c1, c0], sx)
+    want = np.sum(res_line ** 2) / (20e-4) ** 2 + np.sum(res_circ ** 2) / (10e-4) ** 2
+    assert abs(chi2 - want) < 1e-3 * want + 1e-6
+
+
+def test_fit_three_hits_has_zero_circle_chi2():
+    P = _helix_points(1 / 50.0, -1.0, 0.3, 0.01, 0.5, [3.0, 7.0, 11.0])
+    P[:, :2] += np.array([[1e-3, -2e-3], [0, 1e-3], [-1e-3, 0]])
+    _, _, chi2, ndf, ex = oracle.fit(P[:, 0], P[:, 1], P[:, 2], [0, 0, 0], CU.FIT_PARAMS)
+    assert ndf == 1
+    assert abs(ex[1]) < 1e-9
+
+
+def test_fit_pulls_on_scattered_tracks():
+    """Tracks simulated with scattering kinks at inner hits: residuals of the
+    fitted parameters divided by their fitted errors are N(0,1) and chi2
+    averages ndf (tracks matched to one simulated particle)."""
+    cfg = dataclasses.replace(E.CONFIGS[2], ms_skip_first=True, noise_frac=0.0, overlaps=False)
+    b = E.make_batch(cfg)
+    res = oracle.run(b, CU.cuts_for_config(2), CU.FIT_PARAMS, G.module_layer_table(), DISK, stage=4)
+    tt = res["track_tuple"]
+    n = res["tuple_n"][tt]
+    Hh = res["tuple_hits"][tt]
+    tid = b["track"]
+    match = np.array([tid[Hh[i, 0]] if np.all(tid[Hh[i, :n[i]]] == tid[Hh[i, 0]]) else -1
+                      for i in range(len(tt))])
+    g = match >= 0
+    assert g.sum() > 1000
+    P, cv, mt = res["params"][g], res["cov"][g], match[g]
+    q, pt, eta, phi = b["trk_q"][mt], b["trk_pt"][mt], b["trk_eta"][mt], b["trk_phi"][mt]
+    vtx = b["trk_vertex"][mt]
+    tanl = np.sinh(eta)
+    arc = -(vtx[:, 0] * np.cos(phi) + vtx[:, 1] * np.sin(phi))
+    truth = [q / E.rho_of_pt(pt), phi, tanl, vtx[:, 0] * np.sin(phi) - vtx[:, 1] * np.cos(phi),
+             vtx[:, 2] + tanl * arc]
+    var = cv[:, [0, 2, 5, 9, 14]]
+    for j in range(5):
+        d = P[:, j] - truth[j]
+        if j == 1:
+            d = (d + np.pi) % (2 * np.pi) - np.pi
+        pull = d / np.sqrt(var[:, j])
+        assert abs(np.mean(pull)) < 0.1, j
+        assert 0.9 < np.std(pull) < 1.15, (j, np.std(pull))
+    c2 = res["chi2"][g] / res["ndf"][g]
+    assert 0.85 < np.mean(res["chi2"][g]) / np.mean(res["ndf"][g]) < 1.15, np.mean(c2)
