@@ -1,0 +1,248 @@
+/*
+ * pt.h - C ABI of the GB300 pixel seeding + broken-line fitting library.
+ *
+ * Implements the data-parallel hot path of Bocci, Kortelainen, Innocente,
+ * Pantaleo, Rovere, "Heterogeneous reconstruction of tracks and primary
+ * vertices with the CMS pixel tracker" (arXiv 2008.13461): from reconstructed
+ * pixel hits to fitted tracks, in four calls issued in order on one CUDA
+ * stream:
+ *
+ *   pt_build_doublets  Sec. 3.2 (doublets on layer pairs under the Table 1
+ *                      cuts PhiW, ZW, ZIP, PT, hits tiled in phi) and the
+ *                      Fishbone of Sec. 3.3;
+ *   pt_connect_cells   Sec. 3.2 (Cellular-Automaton connection: R-z
+ *                      alignment, curvature, beamspot and dz compatibility);
+ *   pt_find_ntuplets   Sec. 3.2 (root doublets, depth-first search) and the
+ *                      shared-doublet cleaning of Sec. 3.3;
+ *   pt_fit_tracks      Sec. 3.4 (broken-line fit: transverse pre-fit, s-z
+ *                      line fit, transverse circle fit, combined parameters
+ *                      and covariance).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - All array pointers are DEVICE pointers owned by the caller (the library
+ *    allocates nothing).  Structs passed by pointer are read on the host
+ *    during the call and may be reused afterwards.
+ *  - `ws` is a caller-allocated device workspace of at least
+ *    pt_workspace_size() bytes, 256-byte aligned.  It carries state from one
+ *    call to the next: the four calls must receive the same ws, hits and
+ *    config, in order.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream) and never synchronise, so a sequence of calls can be
+ *    captured in a CUDA graph.  Argument errors are returned synchronously;
+ *    errors found on the device (capacity overflow, malformed input) are
+ *    recorded in the workspace and returned by pt_read_counts(), the only
+ *    call that synchronises the stream.
+ *  - Capacities are upper bounds on outputs.  On overflow the counters keep
+ *    counting, so pt_read_counts() reports the sizes needed; the outputs of
+ *    that run are then incomplete and must be discarded.
+ *  - Inputs must satisfy the exactness contract: every hit coordinate
+ *    (x, y, z, r) is a float32 multiple of 2^-14 cm with magnitude below
+ *    64 cm, and each hit lies inside the envelope of its layer.  Violations
+ *    set PT_FLAG_INPUT.  Under the contract every doublet / cell / n-tuplet
+ *    decision is the sign of an integer polynomial in the hit coordinates and
+ *    the exact binary values of the float32 cut constants, and is decided
+ *    exactly (a float32 evaluation with a proven error bound, falling back to
+ *    exact integer arithmetic when the bound cannot decide).
+ *  - Output order is unspecified (atomics); sets are deterministic.
+ */
+#ifndef PT_H
+#define PT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PT_N_LAYERS 10      /* 4 barrel + 3 + 3 disks */
+#define PT_MAX_PAIRS 32
+#define PT_NMAX 8           /* maximum hits per n-tuplet */
+
+typedef enum {
+    PT_OK = 0,
+    PT_ERR_INVALID_ARG = 1, /* NULL pointer, bad size, bad tuning, small ws */
+    PT_ERR_CAPACITY = 2,    /* a device buffer overflowed (pt_read_counts) */
+    PT_ERR_INPUT = 3,       /* input violates the contract (pt_read_counts) */
+    PT_ERR_CUDA = 4         /* a CUDA runtime call failed */
+} pt_status;
+
+/* bits of pt_counts.flags */
+#define PT_FLAG_CELLS 1u    /* cell capacity exceeded */
+#define PT_FLAG_EDGES 2u    /* edge capacity exceeded */
+#define PT_FLAG_TUPLES 4u   /* n-tuplet capacity exceeded */
+#define PT_FLAG_TRACKS 8u   /* track capacity exceeded */
+#define PT_FLAG_INPUT 16u   /* module id out of range, coordinate off the grid
+                               or outside its layer envelope */
+
+#define PT_LAYER_BARREL 0
+#define PT_LAYER_DISK 1
+
+/* One detector layer: its kind and the envelope that contains every hit on
+ * it (used to bound search windows; hits outside set PT_FLAG_INPUT). */
+typedef struct {
+    int32_t kind;           /* PT_LAYER_BARREL or PT_LAYER_DISK */
+    float rmin, rmax, zmin, zmax;
+} pt_layer;
+
+/* Geometry: layers plus the module -> layer table (device, n_modules). */
+typedef struct {
+    pt_layer layer[PT_N_LAYERS];
+    const int32_t *module_layer;
+    int32_t n_modules;
+} pt_geometry;
+
+/* Doublet cuts of one layer pair (Table 1), each stored in the form its
+ * predicate uses (i = inner hit, o = outer hit; C = i x o, Dt = i . o in the
+ * transverse plane):
+ *   PhiW  Dt > 0 and C^2 <= tan2_dphi * Dt^2
+ *   ZW    zlo <= z_i <= zhi
+ *   ZIP   r_o > r_i and |z_i r_o - z_o r_i| <= zmax (r_o - r_i)
+ *   PT    k_pt C^2 <= |o-i|^2 |i|^2 |o|^2      (k_pt = 4 rho_min^2)   */
+typedef struct {
+    int32_t inner, outer;   /* layer indices, inner closer to the beam */
+    float tan2_dphi, zlo, zhi, zmax, k_pt;
+} pt_pair_cuts;
+
+/* Cellular-Automaton cuts for cells (a,b),(b,c) (Sec. 3.2), chosen by the
+ * kind of the shared hit b's layer (barrel / endcap, Sec. 4.2):
+ *   dz    |z_a r_c - z_c r_a| <= zmax (r_c - r_a)
+ *   R-z   X^2 <= tol_rz2 ((r_c-r_a)^2 + (z_c-z_a)^2),
+ *         X = (r_b-r_a)(z_c-z_b) - (z_b-z_a)(r_c-r_b)
+ *   curv  |ab|^2 |bc|^2 |ca|^2 >= k_curv O^2, O = (b-a) x (c-a)
+ *   R_max I^2 <= rmax2 |ab|^2 |bc|^2 |ca|^2, I = in-circle determinant of
+ *         (a, b, c, origin)                                               */
+typedef struct {
+    float tol_rz2, k_curv, rmax2, zmax;
+} pt_ca_cuts;
+
+/* All cut constants.  Every float constant must lie in [2^-40, 2^40].
+ * Fishbone (Sec. 3.3): cells (h1,h) and (h2,h) sharing the outer hit h, with
+ * inner hits on one layer, are aligned when u = h1-h, v = h2-h satisfy
+ * u.v > 0 and |u x v|^2 <= fishbone_eps2 |u|^2 |v|^2; an aligned cell dies if
+ * its sibling is strictly shorter (3-D), or equally long with a smaller
+ * input index.  min_hits: n-tuplets shorter than this are not fitted. */
+typedef struct {
+    int32_t n_pairs;
+    pt_pair_cuts pair[PT_MAX_PAIRS];
+    pt_ca_cuts region[2];   /* [0] barrel, [1] endcap */
+    float fishbone_eps2;
+    int32_t min_hits;
+} pt_cuts;
+
+/* Broken-line fit constants (Sec. 3.4): field (T), hit resolutions (cm),
+ * material per module crossing (radiation lengths). */
+typedef struct {
+    float bz, sigma_rphi, sigma_z, sigma_r, x0_barrel, x0_disk;
+    int32_t reserved;
+} pt_fit_params;
+
+/* Speed knobs; results do not depend on them. */
+typedef struct {
+    int32_t n_phi_bins;     /* azimuthal tiles per layer, 16..1024 */
+    int32_t n_t_bins;       /* tiles along z (barrel) or r (disks), 1..64 */
+    int32_t doublet_lanes;  /* lanes per outer hit: 4, 8, 16 or 32 */
+    int32_t connect_lanes;  /* lanes per outer cell: 4, 8, 16 or 32 */
+    int32_t blocks_per_sm;  /* persistent grid size factor, 1..32 */
+} pt_tuning;
+
+typedef struct {
+    int64_t cells, edges, tuples, tracks;
+} pt_capacity;
+
+typedef struct {
+    pt_geometry geometry;
+    pt_cuts cuts;
+    pt_fit_params fit;
+    pt_tuning tuning;
+    pt_capacity capacity;
+} pt_config;
+
+/* Hits of a batch of events (structure of arrays, device).  Event e owns
+ * hits [ev_off[e], ev_off[e+1]); ev_off[0] = 0, ev_off[n_events] = n_hits. */
+typedef struct {
+    const float *x, *y, *z, *r;
+    const int32_t *module;
+    const int32_t *ev_off;
+    int32_t n_hits, n_events;
+} pt_hits;
+
+/* Cells (doublets).  inner/outer are indices into the BINNED hit order
+ * (pt_hit_order() maps them to input indices); pair indexes cuts.pair;
+ * alive is 0 for cells removed by the Fishbone.  capacity.cells entries. */
+typedef struct {
+    int32_t *inner, *outer;
+    uint8_t *pair, *alive;
+} pt_cells;
+
+/* CA edges: cell src (a,b) -> cell dst (b,c).  capacity.edges entries. */
+typedef struct {
+    int32_t *src, *dst;
+} pt_edges;
+
+/* n-tuplets: hits[t*PT_NMAX + k] input hit indices inner to outer,
+ * cells[t*PT_NMAX + k] cell indices (k < n-1), n[t] hit count, alive[t] 0 if
+ * removed by the shared-doublet cleaning.  capacity.tuples entries. */
+typedef struct {
+    int32_t *hits, *cells;
+    uint8_t *n, *alive;
+} pt_tuples;
+
+/* Fitted tracks: params[k*5 + j] = (kappa [1/cm, q/rho, positive bends
+ * clockwise for B along +z], phi0, tan(lambda), d0 [cm, PCA = d0 (sin phi0,
+ * -cos phi0)], z0 [cm]); cov[k*15 + ...] lower triangle of the 5x5 covariance
+ * in that order, row major; chi2; ndf = 2n-5; tuple = n-tuplet index.
+ * capacity.tracks entries. */
+typedef struct {
+    float *params, *cov, *chi2;
+    int8_t *ndf;
+    int32_t *tuple;
+} pt_tracks;
+
+typedef struct {
+    int64_t n_cells, n_edges, n_tuples, n_tracks; /* counts produced (or needed) */
+    int64_t n_alive_cells, n_alive_tuples;
+    int64_t n_exact_fallbacks;                    /* predicates decided exactly */
+    uint32_t flags;                               /* PT_FLAG_* */
+} pt_counts;
+
+/* Bytes of workspace needed for `hits` and `cfg` (reads only n_hits,
+ * n_events of hits and tuning + capacity of cfg).  Returns 0 if invalid. */
+size_t pt_workspace_size(const pt_hits *hits, const pt_config *cfg);
+
+/* Sec. 3.2 + 3.3: tile hits per (event, layer, phi, z|r), build doublets of
+ * all layer pairs, apply the Fishbone.  Resets the workspace counters. */
+pt_status pt_build_doublets(void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg,
+                            pt_cells *cells, void *stream);
+
+/* Sec. 3.2: connect live cells sharing a hit into the CA graph. */
+pt_status pt_connect_cells(void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg,
+                           const pt_cells *cells, pt_edges *edges, void *stream);
+
+/* Sec. 3.2 + 3.3: roots, depth-first search for maximal paths of >= 3 hits,
+ * shared-doublet cleaning. */
+pt_status pt_find_ntuplets(void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg,
+                           const pt_cells *cells, const pt_edges *edges, pt_tuples *tuples,
+                           void *stream);
+
+/* Sec. 3.4: broken-line fit of every live n-tuplet with >= min_hits hits. */
+pt_status pt_fit_tracks(void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg,
+                        const pt_tuples *tuples, pt_tracks *tracks, void *stream);
+
+/* Synchronises `stream`, then reports counts and device flags.  Returns
+ * PT_ERR_CAPACITY or PT_ERR_INPUT when the corresponding flags are set. */
+pt_status pt_read_counts(const void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg,
+                         pt_counts *out, void *stream);
+
+/* Device pointer (inside ws) to int32[n_hits]: binned position -> input hit
+ * index, valid after pt_build_doublets. */
+const int32_t *pt_hit_order(const void *ws, size_t ws_bytes, const pt_hits *hits,
+                            const pt_config *cfg);
+
+const char *pt_status_string(pt_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

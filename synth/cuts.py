@@ -39,7 +39,16 @@ def _f32(v) -> float:
 
 
 def make_cuts(pt_min: float = 0.5, barrel_only: bool = False, min_hits: int = 3,
-              zmax: float = 15.0, rmax_doublet: float = 0.1) -> dict:
+              zmax: float = 12.0, rmax_doublet: float = 0.01, pt_factor: float = 0.9,
+              ca_tol=(0.02, 0.03), ca_rmax=(0.05, 0.1), ca_curv_factor: float = 0.8,
+              dphi_scale: float = 1.0) -> dict:
+    """Cut table for tracks above pt_min (GeV).  zmax: luminous-region half
+    length (12 cm = 3.4 sigma of the vertex z spread); rmax_doublet: transverse
+    impact allowance in the doublet phi window; pt_factor / ca_curv_factor:
+    fraction of the pt_min radius used by the PT and CA curvature cuts;
+    ca_tol / ca_rmax: R-z alignment distance and beamspot R_max (cm) for the
+    barrel and endcap CA cut sets.  Defaults were chosen on the PU50 sample
+    for ~99% efficiency of tracks leaving >= 3 layer hits."""
     lay = {L.index: L for L in G.layers()}
     pairs = G.PAIRS_BARREL if barrel_only else G.PAIRS_FULL
     rho = float(rho_of_pt(pt_min))
@@ -53,7 +62,7 @@ def make_cuts(pt_min: float = 0.5, barrel_only: bool = False, min_hits: int = 3,
         dphi = (math.asin(min(1.0, ro_max / (2 * rr))) - math.asin(min(1.0, ri_min / (2 * rr)))
                 + math.asin(min(1.0, rmax_doublet / ri_min))
                 + math.asin(min(1.0, rmax_doublet / ro_min)))
-        dphi = 1.1 * dphi + 0.005
+        dphi = dphi_scale * dphi + 0.005
         dphi = min(dphi, 1.2)
         zlo, zhi = Li.zmin, Li.zmax
         if Li.kind == G.LAYER_BARREL and Lo.kind == G.LAYER_DISK:
@@ -66,13 +75,13 @@ def make_cuts(pt_min: float = 0.5, barrel_only: bool = False, min_hits: int = 3,
             tan2_dphi=_f32(math.tan(dphi) ** 2),
             zlo=_f32(zlo), zhi=_f32(zhi),
             zmax=_f32(zmax),
-            k_pt=_f32(4.0 * (0.75 * rho) ** 2),
+            k_pt=_f32(4.0 * (pt_factor * rho) ** 2),
         ))
     region = []
-    for tol, rmax in ((0.05, 0.15), (0.08, 0.25)):
+    for tol, rmax in zip(ca_tol, ca_rmax):
         region.append(dict(
             tol_rz2=_f32((tol * soft) ** 2),
-            k_curv=_f32(4.0 * (0.7 * rho) ** 2),
+            k_curv=_f32(4.0 * (ca_curv_factor * rho) ** 2),
             rmax2=_f32((rmax * soft) ** 2),
             zmax=_f32(zmax),
         ))

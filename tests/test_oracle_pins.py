@@ -377,7 +377,11 @@ def test_fit_pulls_on_scattered_tracks():
     n = res["tuple_n"][tt]
     Hh = res["tuple_hits"][tt]
     tid = b["track"]
-    match = np.array([tid[Hh[i, 0]] if np.all(tid[Hh[i, :n[i]]] == tid[Hh[i, 0]]) else -1
+    per_track = np.bincount(tid[tid >= 0], minlength=b["trk_pt"].size)
+    # tuples made of all the hits of one simulated particle (a tuple that
+    # skips one of its hits would put an unmodelled kink in a segment)
+    match = np.array([tid[Hh[i, 0]] if (np.all(tid[Hh[i, :n[i]]] == tid[Hh[i, 0]])
+                                        and per_track[tid[Hh[i, 0]]] == n[i]) else -1
                       for i in range(len(tt))])
     g = match >= 0
     assert g.sum() > 1000
