@@ -1,0 +1,178 @@
+"""ctypes binding of the C ABI in include/pt.h (argument marshalling only).
+
+Every function here forwards to the CUDA library libpt_gb300.so built in-tree
+by ``paper_2008_13461_gb300.build``; there is no fallback implementation.  If
+the library cannot be loaded, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+N_LAYERS = 10
+MAX_PAIRS = 32
+NMAX = 8
+
+PT_OK, PT_ERR_INVALID_ARG, PT_ERR_CAPACITY, PT_ERR_INPUT, PT_ERR_CUDA = range(5)
+FLAG_CELLS, FLAG_EDGES, FLAG_TUPLES, FLAG_TRACKS, FLAG_INPUT = 1, 2, 4, 8, 16
+
+
+class Layer(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("rmin", C.c_float), ("rmax", C.c_float),
+                ("zmin", C.c_float), ("zmax", C.c_float)]
+
+
+class Geometry(C.Structure):
+    _fields_ = [("layer", Layer * N_LAYERS), ("module_layer", C.c_void_p), ("n_modules", C.c_int32)]
+
+
+class PairCuts(C.Structure):
+    _fields_ = [("inner", C.c_int32), ("outer", C.c_int32), ("tan2_dphi", C.c_float),
+                ("zlo", C.c_float), ("zhi", C.c_float), ("zmax", C.c_float), ("k_pt", C.c_float)]
+
+
+class CaCuts(C.Structure):
+    _fields_ = [("tol_rz2", C.c_float), ("k_curv", C.c_float), ("rmax2", C.c_float), ("zmax", C.c_float)]
+
+
+class Cuts(C.Structure):
+    _fields_ = [("n_pairs", C.c_int32), ("pair", PairCuts * MAX_PAIRS), ("region", CaCuts * 2),
+                ("fishbone_eps2", C.c_float), ("min_hits", C.c_int32)]
+
+
+class FitParams(C.Structure):
+    _fields_ = [("bz", C.c_float), ("sigma_rphi", C.c_float), ("sigma_z", C.c_float),
+                ("sigma_r", C.c_float), ("x0_barrel", C.c_float), ("x0_disk", C.c_float),
+                ("reserved", C.c_int32)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("n_phi_bins", C.c_int32), ("n_t_bins", C.c_int32), ("doublet_lanes", C.c_int32),
+                ("connect_lanes", C.c_int32), ("blocks_per_sm", C.c_int32)]
+
+
+class Capacity(C.Structure):
+    _fields_ = [("cells", C.c_int64), ("edges", C.c_int64), ("tuples", C.c_int64), ("tracks", C.c_int64)]
+
+
+class Config(C.Structure):
+    _fields_ = [("geometry", Geometry), ("cuts", Cuts), ("fit", FitParams), ("tuning", Tuning),
+                ("capacity", Capacity)]
+
+
+class Hits(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p), ("r", C.c_void_p),
+                ("module", C.c_void_p), ("ev_off", C.c_void_p), ("n_hits", C.c_int32),
+                ("n_events", C.c_int32)]
+
+
+class Cells(C.Structure):
+    _fields_ = [("inner", C.c_void_p), ("outer", C.c_void_p), ("pair", C.c_void_p), ("alive", C.c_void_p)]
+
+
+class Edges(C.Structure):
+    _fields_ = [("src", C.c_void_p), ("dst", C.c_void_p)]
+
+
+class Tuples(C.Structure):
+    _fields_ = [("hits", C.c_void_p), ("cells", C.c_void_p), ("n", C.c_void_p), ("alive", C.c_void_p)]
+
+
+class Tracks(C.Structure):
+    _fields_ = [("params", C.c_void_p), ("cov", C.c_void_p), ("chi2", C.c_void_p), ("ndf", C.c_void_p),
+                ("tuple", C.c_void_p)]
+
+
+class Counts(C.Structure):
+    _fields_ = [("n_cells", C.c_int64), ("n_edges", C.c_int64), ("n_tuples", C.c_int64),
+                ("n_tracks", C.c_int64), ("n_alive_cells", C.c_int64), ("n_alive_tuples", C.c_int64),
+                ("n_exact_fallbacks", C.c_int64), ("flags", C.c_uint32)]
+
+
+# every symbol declared in include/pt.h
+EXPORTS = ("pt_workspace_size", "pt_build_doublets", "pt_connect_cells", "pt_find_ntuplets",
+           "pt_fit_tracks", "pt_read_counts", "pt_hit_order", "pt_status_string")
+
+_lib = None
+
+
+def lib(build_if_missing: bool = True):
+    """Load libpt_gb300.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; run paper_2008_13461_gb300.build.build()")
+    L = C.CDLL(path)
+    P = C.POINTER
+    L.pt_workspace_size.restype = C.c_size_t
+    L.pt_workspace_size.argtypes = [P(Hits), P(Config)]
+    common = [C.c_void_p, C.c_size_t, P(Hits), P(Config)]
+    L.pt_build_doublets.restype = C.c_int
+    L.pt_build_doublets.argtypes = common + [P(Cells), C.c_void_p]
+    L.pt_connect_cells.restype = C.c_int
+    L.pt_connect_cells.argtypes = common + [P(Cells), P(Edges), C.c_void_p]
+    L.pt_find_ntuplets.restype = C.c_int
+    L.pt_find_ntuplets.argtypes = common + [P(Cells), P(Edges), P(Tuples), C.c_void_p]
+    L.pt_fit_tracks.restype = C.c_int
+    L.pt_fit_tracks.argtypes = common + [P(Tuples), P(Tracks), C.c_void_p]
+    L.pt_read_counts.restype = C.c_int
+    L.pt_read_counts.argtypes = common + [P(Counts), C.c_void_p]
+    L.pt_hit_order.restype = C.c_void_p
+    L.pt_hit_order.argtypes = common
+    L.pt_status_string.restype = C.c_char_p
+    L.pt_status_string.argtypes = [C.c_int]
+    _lib = L
+    return L
+
+
+class PtError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = lib().pt_status_string(status).decode()
+        super().__init__(f"{what}: {msg} (status {status})")
+        self.status = status
+
+
+def check(status: int, what: str) -> None:
+    if status != PT_OK:
+        raise PtError(status, what)
+
+
+# thin wrappers with the ABI's names -------------------------------------
+def workspace_size(hits: Hits, cfg: Config) -> int:
+    return int(lib().pt_workspace_size(C.byref(hits), C.byref(cfg)))
+
+
+def build_doublets(ws, ws_bytes, hits, cfg, cells, stream) -> None:
+    check(lib().pt_build_doublets(ws, ws_bytes, C.byref(hits), C.byref(cfg), C.byref(cells), stream),
+          "pt_build_doublets")
+
+
+def connect_cells(ws, ws_bytes, hits, cfg, cells, edges, stream) -> None:
+    check(lib().pt_connect_cells(ws, ws_bytes, C.byref(hits), C.byref(cfg), C.byref(cells), C.byref(edges),
+                                 stream), "pt_connect_cells")
+
+
+def find_ntuplets(ws, ws_bytes, hits, cfg, cells, edges, tuples, stream) -> None:
+    check(lib().pt_find_ntuplets(ws, ws_bytes, C.byref(hits), C.byref(cfg), C.byref(cells), C.byref(edges),
+                                 C.byref(tuples), stream), "pt_find_ntuplets")
+
+
+def fit_tracks(ws, ws_bytes, hits, cfg, tuples, tracks, stream) -> None:
+    check(lib().pt_fit_tracks(ws, ws_bytes, C.byref(hits), C.byref(cfg), C.byref(tuples), C.byref(tracks),
+                              stream), "pt_fit_tracks")
+
+
+def read_counts(ws, ws_bytes, hits, cfg, stream) -> tuple[int, Counts]:
+    c = Counts()
+    st = lib().pt_read_counts(ws, ws_bytes, C.byref(hits), C.byref(cfg), C.byref(c), stream)
+    return st, c
+
+
+def hit_order(ws, ws_bytes, hits, cfg) -> int:
+    return lib().pt_hit_order(ws, ws_bytes, C.byref(hits), C.byref(cfg))

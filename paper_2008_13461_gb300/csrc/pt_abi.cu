@@ -1,0 +1,356 @@
+// C ABI of the seeding + fitting library (declarations and contracts in
+// include/pt.h): argument validation, workspace layout, kernel launches.
+#include <math.h>
+#include <string.h>
+
+#include "pt_common.cuh"
+#include "pt_kernels.cuh"
+
+using namespace ptk;
+
+namespace {
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+bool tuning_ok(const pt_tuning &t) {
+    auto lanes_ok = [](int g) { return g == 4 || g == 8 || g == 16 || g == 32; };
+    return t.n_phi_bins >= 16 && t.n_phi_bins <= 1024 && t.n_t_bins >= 1 && t.n_t_bins <= 64 &&
+           lanes_ok(t.doublet_lanes) && lanes_ok(t.connect_lanes) && t.blocks_per_sm >= 1 &&
+           t.blocks_per_sm <= 32;
+}
+
+bool capacity_ok(const pt_capacity &c) {
+    const int64_t lim = 0x7fffffff;
+    return c.cells >= 0 && c.cells <= lim && c.edges >= 0 && c.edges <= lim && c.tuples >= 0 &&
+           c.tuples <= lim && c.tracks >= 0 && c.tracks <= lim;
+}
+
+bool layout(const pt_hits *h, const pt_config *cfg, WsLayout &L) {
+    if (!h || !cfg || h->n_hits < 0 || h->n_events < 1) return false;
+    if (!tuning_ok(cfg->tuning) || !capacity_ok(cfg->capacity)) return false;
+    const int64_t n_bins =
+        (int64_t)h->n_events * PT_N_LAYERS * cfg->tuning.n_phi_bins * cfg->tuning.n_t_bins;
+    if (n_bins >= 0x7fffffff) return false;
+    const size_t nh = (size_t)(h->n_hits > 0 ? h->n_hits : 1);
+    const size_t nc = (size_t)(cfg->capacity.cells > 0 ? cfg->capacity.cells : 1);
+    L.n_bins = n_bins;
+    L.n_scan_blocks = (int32_t)((n_bins + kScanItems - 1) / kScanItems);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align256(o + bytes);
+        return at;
+    };
+    L.counters = take(sizeof(int32_t) * kCounters);
+    L.bin_cnt = take(sizeof(int32_t) * (size_t)(n_bins + 1));
+    L.scan_part = take(sizeof(int32_t) * (size_t)(L.n_scan_blocks + 1));
+    L.hit_bin = take(4 * nh);
+    L.hit_rank = take(4 * nh);
+    L.bx = take(4 * nh);
+    L.by = take(4 * nh);
+    L.bz = take(4 * nh);
+    L.br = take(4 * nh);
+    L.blayer = take(nh);
+    L.bev = take(4 * nh);
+    L.perm = take(4 * nh);
+    L.in_off = take(4 * nh);
+    L.in_cnt = take(4 * nh);
+    L.edge_off = take(4 * nc);
+    L.edge_cnt = take(4 * nc);
+    L.has_out = take(nc);
+    L.maxlen = take(4 * nc);
+    L.total = o;
+    return true;
+}
+
+// Longest path (in hits) of the layer-pair graph, or -1 if it has a cycle.
+int longest_layer_path(const pt_cuts &c) {
+    int best[PT_N_LAYERS];
+    for (int i = 0; i < PT_N_LAYERS; i++) best[i] = 1;
+    for (int round = 0; round <= PT_N_LAYERS; round++) {
+        bool changed = false;
+        for (int k = 0; k < c.n_pairs; k++) {
+            int a = c.pair[k].inner, b = c.pair[k].outer;
+            if (best[a] + 1 > best[b]) {
+                best[b] = best[a] + 1;
+                changed = true;
+            }
+        }
+        if (!changed) {
+            int m = 1;
+            for (int i = 0; i < PT_N_LAYERS; i++) m = best[i] > m ? best[i] : m;
+            return m;
+        }
+    }
+    return -1;
+}
+
+bool const_ok(float v) { return isfinite(v) && v >= ldexpf(1.0f, -30) && v <= ldexpf(1.0f, 40); }
+
+bool config_ok(const pt_config *cfg) {
+    const pt_cuts &c = cfg->cuts;
+    const pt_geometry &g = cfg->geometry;
+    if (!g.module_layer || g.n_modules <= 0) return false;
+    for (int i = 0; i < PT_N_LAYERS; i++) {
+        const pt_layer &l = g.layer[i];
+        if ((l.kind != PT_LAYER_BARREL && l.kind != PT_LAYER_DISK) || !(l.rmin < l.rmax) || !(l.zmin < l.zmax) ||
+            !isfinite(l.rmin) || !isfinite(l.rmax) || !isfinite(l.zmin) || !isfinite(l.zmax))
+            return false;
+    }
+    if (c.n_pairs < 1 || c.n_pairs > PT_MAX_PAIRS) return false;
+    int per_outer[PT_N_LAYERS] = {0};
+    for (int k = 0; k < c.n_pairs; k++) {
+        const pt_pair_cuts &p = c.pair[k];
+        if (p.inner < 0 || p.inner >= PT_N_LAYERS || p.outer < 0 || p.outer >= PT_N_LAYERS || p.inner == p.outer)
+            return false;
+        for (int j = 0; j < k; j++)
+            if (c.pair[j].inner == p.inner && c.pair[j].outer == p.outer) return false;
+        if (++per_outer[p.outer] > kMaxPairsPerLayer) return false;
+        if (!const_ok(p.tan2_dphi) || !const_ok(p.zmax) || !const_ok(p.k_pt)) return false;
+        if (!isfinite(p.zlo) || !isfinite(p.zhi) || p.zlo > p.zhi) return false;
+    }
+    for (int r = 0; r < 2; r++) {
+        const pt_ca_cuts &q = c.region[r];
+        if (!const_ok(q.tol_rz2) || !const_ok(q.k_curv) || !const_ok(q.rmax2) || !const_ok(q.zmax)) return false;
+    }
+    if (!const_ok(c.fishbone_eps2) || c.fishbone_eps2 >= 1.0f) return false;
+    if (c.min_hits < 3 || c.min_hits > PT_NMAX) return false;
+    const int lp = longest_layer_path(c);
+    if (lp < 0 || lp > PT_NMAX) return false;
+    const pt_fit_params &f = cfg->fit;
+    if (!(f.bz > 0) || !(f.sigma_rphi > 0) || !(f.sigma_z > 0) || !(f.sigma_r > 0) || !(f.x0_barrel > 0) ||
+        !(f.x0_disk > 0))
+        return false;
+    return true;
+}
+
+bool hits_ok(const pt_hits *h) {
+    if (!h || h->n_hits < 0 || h->n_events < 1 || !h->ev_off) return false;
+    if (h->n_hits > 0 && (!h->x || !h->y || !h->z || !h->r || !h->module)) return false;
+    return true;
+}
+
+int num_sms() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
+// Fill kernel parameters; outputs not yet produced may be null.
+Params make_params(void *ws, const WsLayout &L, const pt_hits *h, const pt_config *cfg) {
+    Params p;
+    memset(&p, 0, sizeof p);
+    char *w = (char *)ws;
+    p.x = h->x; p.y = h->y; p.z = h->z; p.r = h->r;
+    p.module = h->module;
+    p.ev_off = h->ev_off;
+    p.module_layer = cfg->geometry.module_layer;
+    p.n_hits = h->n_hits;
+    p.n_events = h->n_events;
+    p.n_modules = cfg->geometry.n_modules;
+    p.counters = (int32_t *)(w + L.counters);
+    p.bin_cnt = (int32_t *)(w + L.bin_cnt);
+    p.scan_part = (int32_t *)(w + L.scan_part);
+    p.hit_bin = (int32_t *)(w + L.hit_bin);
+    p.hit_rank = (int32_t *)(w + L.hit_rank);
+    p.bx = (float *)(w + L.bx);
+    p.by = (float *)(w + L.by);
+    p.bz = (float *)(w + L.bz);
+    p.br = (float *)(w + L.br);
+    p.blayer = (int8_t *)(w + L.blayer);
+    p.bev = (int32_t *)(w + L.bev);
+    p.perm = (int32_t *)(w + L.perm);
+    p.in_off = (int32_t *)(w + L.in_off);
+    p.in_cnt = (int32_t *)(w + L.in_cnt);
+    p.edge_off = (int32_t *)(w + L.edge_off);
+    p.edge_cnt = (int32_t *)(w + L.edge_cnt);
+    p.has_out = (uint8_t *)(w + L.has_out);
+    p.maxlen = (int32_t *)(w + L.maxlen);
+    p.cap_cells = cfg->capacity.cells;
+    p.cap_edges = cfg->capacity.edges;
+    p.cap_tuples = cfg->capacity.tuples;
+    p.cap_tracks = cfg->capacity.tracks;
+    p.n_phi = cfg->tuning.n_phi_bins;
+    p.n_t = cfg->tuning.n_t_bins;
+    p.n_bins = L.n_bins;
+    p.n_scan_blocks = L.n_scan_blocks;
+    const pt_cuts &c = cfg->cuts;
+    for (int i = 0; i < PT_N_LAYERS; i++) p.layer[i] = cfg->geometry.layer[i];
+    p.n_pairs = c.n_pairs;
+    for (int k = 0; k < c.n_pairs; k++) {
+        p.pair[k] = c.pair[k];
+        // PhiW accepts |dphi| <= atan(sqrt(tan2)); the window adds a margin
+        // far above float32 rounding of the angles involved
+        p.pair_dphi[k] = (float)(atan(sqrt((double)c.pair[k].tan2_dphi)) + 1e-4);
+        const int lo = c.pair[k].outer;
+        p.pairs_by_outer[lo][p.n_pairs_by_outer[lo]++] = (int8_t)k;
+    }
+    p.region[0] = c.region[0];
+    p.region[1] = c.region[1];
+    p.fishbone_eps2 = c.fishbone_eps2;
+    p.min_hits = c.min_hits;
+    p.fit = cfg->fit;
+    return p;
+}
+
+pt_status check_common(void *ws, size_t ws_bytes, const pt_hits *h, const pt_config *cfg, WsLayout &L) {
+    if (!ws || ((uintptr_t)ws & 255) || !hits_ok(h) || !cfg || !config_ok(cfg)) return PT_ERR_INVALID_ARG;
+    if (!layout(h, cfg, L) || ws_bytes < L.total) return PT_ERR_INVALID_ARG;
+    return PT_OK;
+}
+
+int grid_for(const pt_config *cfg) {
+    int sms = num_sms();
+    return (sms > 0 ? sms : 1) * cfg->tuning.blocks_per_sm;
+}
+
+pt_status launched() { return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+size_t pt_workspace_size(const pt_hits *hits, const pt_config *cfg) {
+    WsLayout L;
+    if (!layout(hits, cfg, L)) return 0;
+    return L.total;
+}
+
+pt_status pt_build_doublets(void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg, pt_cells *cells,
+                            void *stream) {
+    WsLayout L;
+    pt_status st = check_common(ws, ws_bytes, hits, cfg, L);
+    if (st != PT_OK) return st;
+    if (!cells || (cfg->capacity.cells > 0 && (!cells->inner || !cells->outer || !cells->pair || !cells->alive)))
+        return PT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Params p = make_params(ws, L, hits, cfg);
+    p.cell_inner = cells->inner;
+    p.cell_outer = cells->outer;
+    p.cell_pair = cells->pair;
+    p.cell_alive = cells->alive;
+    if (cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * kCounters, s) != cudaSuccess) return PT_ERR_CUDA;
+    if (cudaMemsetAsync(p.bin_cnt, 0, sizeof(int32_t) * (size_t)(L.n_bins + 1), s) != cudaSuccess)
+        return PT_ERR_CUDA;
+    const int grid = grid_for(cfg);
+    launch_binning(p, grid, s);
+    launch_doublets(p, cfg->tuning.doublet_lanes, grid, s);
+    // alignment within eps (sin) implies |u^ - v^| <= 2 sin(asin(eps)/2) <= eps pi/2;
+    // 4e-6 covers the float32 rounding of the unit vectors
+    const float ut = (float)((sqrt((double)cfg->cuts.fishbone_eps2) * 1.5707963267948966 + 4e-6) *
+                             (sqrt((double)cfg->cuts.fishbone_eps2) * 1.5707963267948966 + 4e-6));
+    launch_fishbone(p, ut, grid, s);
+    return launched();
+}
+
+pt_status pt_connect_cells(void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg,
+                           const pt_cells *cells, pt_edges *edges, void *stream) {
+    WsLayout L;
+    pt_status st = check_common(ws, ws_bytes, hits, cfg, L);
+    if (st != PT_OK) return st;
+    if (!cells || !edges || (cfg->capacity.edges > 0 && (!edges->src || !edges->dst))) return PT_ERR_INVALID_ARG;
+    Params p = make_params(ws, L, hits, cfg);
+    p.cell_inner = cells->inner;
+    p.cell_outer = cells->outer;
+    p.cell_pair = cells->pair;
+    p.cell_alive = cells->alive;
+    p.edge_src = edges->src;
+    p.edge_dst = edges->dst;
+    launch_connect(p, cfg->tuning.connect_lanes, grid_for(cfg), (cudaStream_t)stream);
+    return launched();
+}
+
+pt_status pt_find_ntuplets(void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg,
+                           const pt_cells *cells, const pt_edges *edges, pt_tuples *tuples, void *stream) {
+    WsLayout L;
+    pt_status st = check_common(ws, ws_bytes, hits, cfg, L);
+    if (st != PT_OK) return st;
+    if (!cells || !edges || !tuples ||
+        (cfg->capacity.tuples > 0 && (!tuples->hits || !tuples->cells || !tuples->n || !tuples->alive)))
+        return PT_ERR_INVALID_ARG;
+    Params p = make_params(ws, L, hits, cfg);
+    p.cell_inner = cells->inner;
+    p.cell_outer = cells->outer;
+    p.cell_pair = cells->pair;
+    p.cell_alive = cells->alive;
+    p.edge_src = edges->src;
+    p.edge_dst = edges->dst;
+    p.tup_hits = tuples->hits;
+    p.tup_cells = tuples->cells;
+    p.tup_n = tuples->n;
+    p.tup_alive = tuples->alive;
+    launch_ntuplets(p, grid_for(cfg), (cudaStream_t)stream);
+    return launched();
+}
+
+pt_status pt_fit_tracks(void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg,
+                        const pt_tuples *tuples, pt_tracks *tracks, void *stream) {
+    WsLayout L;
+    pt_status st = check_common(ws, ws_bytes, hits, cfg, L);
+    if (st != PT_OK) return st;
+    if (!tuples || !tracks ||
+        (cfg->capacity.tracks > 0 &&
+         (!tracks->params || !tracks->cov || !tracks->chi2 || !tracks->ndf || !tracks->tuple)))
+        return PT_ERR_INVALID_ARG;
+    Params p = make_params(ws, L, hits, cfg);
+    p.tup_hits = tuples->hits;
+    p.tup_cells = tuples->cells;
+    p.tup_n = tuples->n;
+    p.tup_alive = tuples->alive;
+    p.trk_params = tracks->params;
+    p.trk_cov = tracks->cov;
+    p.trk_chi2 = tracks->chi2;
+    p.trk_ndf = tracks->ndf;
+    p.trk_tuple = tracks->tuple;
+    const int grid = grid_for(cfg);
+    launch_select(p, grid, (cudaStream_t)stream);
+    launch_fit(p, grid, (cudaStream_t)stream);
+    return launched();
+}
+
+pt_status pt_read_counts(const void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg,
+                         pt_counts *out, void *stream) {
+    WsLayout L;
+    if (!ws || !out || !layout(hits, cfg, L) || ws_bytes < L.total) return PT_ERR_INVALID_ARG;
+    int32_t c[kCounters];
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(c, (const char *)ws + L.counters, sizeof c, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PT_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PT_ERR_CUDA;
+    out->n_cells = (uint32_t)c[C_CELLS];
+    out->n_edges = (uint32_t)c[C_EDGES];
+    out->n_tuples = (uint32_t)c[C_TUPLES];
+    out->n_tracks = (uint32_t)c[C_TRACKS];
+    out->n_alive_cells = (uint32_t)c[C_ALIVE_CELLS];
+    out->n_alive_tuples = (uint32_t)c[C_ALIVE_TUPLES];
+    out->n_exact_fallbacks = (uint32_t)c[C_FALLBACK];
+    out->flags = (uint32_t)c[C_FLAGS];
+    if (out->flags & PT_FLAG_INPUT) return PT_ERR_INPUT;
+    if (out->flags & (PT_FLAG_CELLS | PT_FLAG_EDGES | PT_FLAG_TUPLES | PT_FLAG_TRACKS)) return PT_ERR_CAPACITY;
+    return PT_OK;
+}
+
+const int32_t *pt_hit_order(const void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg) {
+    WsLayout L;
+    if (!ws || !layout(hits, cfg, L) || ws_bytes < L.total) return nullptr;
+    return (const int32_t *)((const char *)ws + L.perm);
+}
+
+const char *pt_status_string(pt_status s) {
+    switch (s) {
+    case PT_OK: return "ok";
+    case PT_ERR_INVALID_ARG: return "invalid argument";
+    case PT_ERR_CAPACITY: return "output capacity exceeded";
+    case PT_ERR_INPUT: return "input violates the contract";
+    case PT_ERR_CUDA: return "CUDA error";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,158 @@
+// Step a0: tile the hits of every (event, layer) in phi x t (t = z on barrel
+// layers, r on disks) -- the paper's phi-tiled hit structure of Sec. 3.2,
+// here two-dimensional.  Counting sort: per-hit tile + rank by atomics,
+// exclusive scan of the tile counts, scatter into a binned structure of
+// arrays.  Tiles only accelerate the doublet search; results do not depend
+// on them.
+#include "pt_common.cuh"
+#include "pt_kernels.cuh"
+
+namespace ptk {
+
+__device__ __forceinline__ bool on_grid(float v) {
+    float s = v * 16384.0f;
+    return fabsf(v) < 64.0f && s == rintf(s);
+}
+
+__global__ void __launch_bounds__(kThreads) k_bin_count(Params p) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < p.n_hits; h += stride) {
+        float x = p.x[h], y = p.y[h], z = p.z[h], r = p.r[h];
+        int m = p.module[h];
+        bool bad = m < 0 || m >= p.n_modules;
+        int L = bad ? 0 : p.module_layer[m];
+        bad = bad || L < 0 || L >= PT_N_LAYERS;
+        bad = bad || !on_grid(x) || !on_grid(y) || !on_grid(z) || !on_grid(r);
+        float tmin = 0.f, tmax = 1.f, t = 0.f;
+        if (!bad) {
+            const pt_layer ly = p.layer[L];
+            bad = r < ly.rmin || r > ly.rmax || z < ly.zmin || z > ly.zmax;
+            if (ly.kind == PT_LAYER_BARREL) {
+                t = z; tmin = ly.zmin; tmax = ly.zmax;
+            } else {
+                t = r; tmin = ly.rmin; tmax = ly.rmax;
+            }
+        }
+        if (bad) {
+            set_flag(p.counters, PT_FLAG_INPUT);
+            p.hit_bin[h] = -1;
+            continue;
+        }
+        // event of hit h: ev_off[e] <= h < ev_off[e+1]
+        int lo = 0, hi = p.n_events - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (__ldg(p.ev_off + mid) <= h) lo = mid; else hi = mid - 1;
+        }
+        int pb = phi_tile(atan2f(y, x), p.n_phi);
+        int tb = t_tile(t, tmin, tmax, p.n_t);
+        int bin = ((lo * PT_N_LAYERS + L) * p.n_phi + pb) * p.n_t + tb;
+        p.hit_bin[h] = bin;
+        p.hit_rank[h] = atomicAdd(p.bin_cnt + bin, 1);
+    }
+}
+
+// exclusive scan of bin_cnt[0 .. n_bins) in place; bin_cnt[n_bins] = total
+__device__ __forceinline__ int block_exclusive_scan(int v, int *smem_warp, int &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int s = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, s, d);
+        if (lane >= d) s += t;
+    }
+    if (lane == 31) smem_warp[warp] = s;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < (kThreads / 32) ? smem_warp[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += t;
+        }
+        if (lane < (kThreads / 32)) smem_warp[lane] = w;
+    }
+    __syncthreads();
+    int excl = s - v + (warp > 0 ? smem_warp[warp - 1] : 0);
+    total = smem_warp[kThreads / 32 - 1];
+    __syncthreads();
+    return excl;
+}
+
+constexpr int kPerThread = kScanItems / kThreads;   // 16
+
+__global__ void __launch_bounds__(kThreads) k_scan_reduce(Params p) {
+    __shared__ int sw[kThreads / 32];
+    int64_t base = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPerThread;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kPerThread; k++) {
+        int64_t i = base + k;
+        if (i < p.n_bins) s += p.bin_cnt[i];
+    }
+    int total;
+    block_exclusive_scan(s, sw, total);
+    if (threadIdx.x == 0) p.scan_part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_partials(Params p) {
+    __shared__ int sw[kThreads / 32];
+    int carry = 0;
+    for (int b0 = 0; b0 < p.n_scan_blocks; b0 += kThreads) {
+        int i = b0 + threadIdx.x;
+        int v = i < p.n_scan_blocks ? p.scan_part[i] : 0;
+        int total;
+        int e = block_exclusive_scan(v, sw, total);
+        if (i < p.n_scan_blocks) p.scan_part[i] = carry + e;
+        carry += total;
+    }
+    if (threadIdx.x == 0) p.bin_cnt[p.n_bins] = carry;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_apply(Params p) {
+    __shared__ int sw[kThreads / 32];
+    int64_t base = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPerThread;
+    int v[kPerThread];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kPerThread; k++) {
+        int64_t i = base + k;
+        v[k] = i < p.n_bins ? p.bin_cnt[i] : 0;
+        s += v[k];
+    }
+    int total;
+    int e = block_exclusive_scan(s, sw, total) + p.scan_part[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kPerThread; k++) {
+        int64_t i = base + k;
+        if (i < p.n_bins) p.bin_cnt[i] = e;
+        e += v[k];
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_bin_fill(Params p) {
+    const int stride = gridDim.x * blockDim.x;
+    const int per_event = PT_N_LAYERS * p.n_phi * p.n_t;
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < p.n_hits; h += stride) {
+        int bin = p.hit_bin[h];
+        if (bin < 0) continue;
+        int pos = p.bin_cnt[bin] + p.hit_rank[h];
+        p.bx[pos] = p.x[h];
+        p.by[pos] = p.y[h];
+        p.bz[pos] = p.z[h];
+        p.br[pos] = p.r[h];
+        p.perm[pos] = h;
+        p.bev[pos] = bin / per_event;
+        p.blayer[pos] = (int8_t)((bin / (p.n_phi * p.n_t)) % PT_N_LAYERS);
+    }
+}
+
+void launch_binning(const Params &p, int grid, cudaStream_t s) {
+    k_bin_count<<<grid, kThreads, 0, s>>>(p);
+    k_scan_reduce<<<p.n_scan_blocks, kThreads, 0, s>>>(p);
+    k_scan_partials<<<1, kThreads, 0, s>>>(p);
+    k_scan_apply<<<p.n_scan_blocks, kThreads, 0, s>>>(p);
+    k_bin_fill<<<grid, kThreads, 0, s>>>(p);
+}
+
+}  // namespace ptk

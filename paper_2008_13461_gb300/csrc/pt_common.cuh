@@ -43,7 +43,8 @@ struct Params {
     float *bx, *by, *bz, *br;
     int8_t *blayer;
     int32_t *bev, *perm, *in_off, *in_cnt, *edge_off, *edge_cnt;
-    uint8_t *has_out, *maxlen;
+    uint8_t *has_out;
+    int32_t *maxlen;
     // outputs
     int32_t *cell_inner, *cell_outer;
     uint8_t *cell_pair, *cell_alive;
@@ -184,7 +185,7 @@ __device__ __forceinline__ Big big_shl(const Big &a, int k) {
 }
 
 // sign of (B - K * 2^s * A) for a float32 constant K (its exact binary value)
-__device__ __noinline__ int big_cmp_scaled(const Big &B, float K, int s, const Big &A) {
+static __device__ __noinline__ int big_cmp_scaled(const Big &B, float K, int s, const Big &A) {
     int ex;
     float fr = frexpf(K, &ex);
     long long m = (long long)ldexpf(fr, 24);
@@ -216,7 +217,7 @@ __device__ __forceinline__ GHit ghit(float x, float y, float z, float r) {
 }
 
 // ---- exact forms (integer polynomials; see pt.h for the predicates)
-__device__ __noinline__ int exact_phiw(GHit i, GHit o, float T, int32_t *counters) {
+static __device__ __noinline__ int exact_phiw(GHit i, GHit o, float T, int32_t *counters) {
     atomicAdd(counters + C_FALLBACK, 1);
     long long Dt = i.x * o.x + i.y * o.y;
     if (Dt <= 0) return 0;
@@ -225,7 +226,7 @@ __device__ __noinline__ int exact_phiw(GHit i, GHit o, float T, int32_t *counter
     return big_cmp_scaled(big_mul(c, c), T, 0, big_mul(d, d)) <= 0;
 }
 
-__device__ __noinline__ int exact_zip(GHit i, GHit o, float zmax, int32_t *counters) {
+static __device__ __noinline__ int exact_zip(GHit i, GHit o, float zmax, int32_t *counters) {
     atomicAdd(counters + C_FALLBACK, 1);
     if (!(o.r > i.r)) return 0;
     long long L = i.z * o.r - o.z * i.r;
@@ -233,7 +234,7 @@ __device__ __noinline__ int exact_zip(GHit i, GHit o, float zmax, int32_t *count
     return big_cmp_scaled(big_from(L), zmax, 14, big_from(o.r - i.r)) <= 0;
 }
 
-__device__ __noinline__ int exact_pt(GHit i, GHit o, float K, int32_t *counters) {
+static __device__ __noinline__ int exact_pt(GHit i, GHit o, float K, int32_t *counters) {
     atomicAdd(counters + C_FALLBACK, 1);
     long long C = i.x * o.y - i.y * o.x;
     long long dx = o.x - i.x, dy = o.y - i.y;
@@ -243,7 +244,7 @@ __device__ __noinline__ int exact_pt(GHit i, GHit o, float K, int32_t *counters)
     return big_cmp_scaled(P, K, 28, big_mul(c, c)) >= 0;
 }
 
-__device__ __noinline__ int exact_rz(GHit a, GHit b, GHit c, float tol2, int32_t *counters) {
+static __device__ __noinline__ int exact_rz(GHit a, GHit b, GHit c, float tol2, int32_t *counters) {
     atomicAdd(counters + C_FALLBACK, 1);
     Big X = big_sub(big_mul(big_from(b.r - a.r), big_from(c.z - b.z)),
                     big_mul(big_from(b.z - a.z), big_from(c.r - b.r)));
@@ -254,7 +255,7 @@ __device__ __noinline__ int exact_rz(GHit a, GHit b, GHit c, float tol2, int32_t
 
 __device__ __forceinline__ long long sq2(long long dx, long long dy) { return dx * dx + dy * dy; }
 
-__device__ __noinline__ int exact_curv(GHit a, GHit b, GHit c, float K, int32_t *counters) {
+static __device__ __noinline__ int exact_curv(GHit a, GHit b, GHit c, float K, int32_t *counters) {
     atomicAdd(counters + C_FALLBACK, 1);
     long long O = (b.x - a.x) * (c.y - a.y) - (b.y - a.y) * (c.x - a.x);
     Big P = big_mul(big_mul(big_from(sq2(b.x - a.x, b.y - a.y)), big_from(sq2(c.x - b.x, c.y - b.y))),
@@ -263,7 +264,7 @@ __device__ __noinline__ int exact_curv(GHit a, GHit b, GHit c, float K, int32_t 
     return big_cmp_scaled(P, K, 28, big_mul(o, o)) >= 0;
 }
 
-__device__ __noinline__ int exact_beamspot(GHit a, GHit b, GHit c, float rmax2, int32_t *counters) {
+static __device__ __noinline__ int exact_beamspot(GHit a, GHit b, GHit c, float rmax2, int32_t *counters) {
     atomicAdd(counters + C_FALLBACK, 1);
     Big a2 = big_from(sq2(a.x, a.y)), b2 = big_from(sq2(b.x, b.y)), c2 = big_from(sq2(c.x, c.y));
     Big m1 = big_sub(big_mul(big_from(b.y), c2), big_mul(b2, big_from(c.y)));
@@ -275,7 +276,7 @@ __device__ __noinline__ int exact_beamspot(GHit a, GHit b, GHit c, float rmax2, 
     return big_cmp_scaled(big_mul(I, I), rmax2, 28, P) <= 0;
 }
 
-__device__ __noinline__ int exact_fb(GHit h1, GHit h2, GHit h, float eps2, int32_t *counters) {
+static __device__ __noinline__ int exact_fb(GHit h1, GHit h2, GHit h, float eps2, int32_t *counters) {
     atomicAdd(counters + C_FALLBACK, 1);
     long long ux = h1.x - h.x, uy = h1.y - h.y, uz = h1.z - h.z;
     long long vx = h2.x - h.x, vy = h2.y - h.y, vz = h2.z - h.z;

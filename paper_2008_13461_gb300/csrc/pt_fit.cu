@@ -1,0 +1,333 @@
+// Step a6: broken-line fit (Sec. 3.4; method of Blobel 2006), one thread per
+// track, specialised at compile time for the number of hits so that every
+// array lives in registers.
+//
+//  1. pre-fit: circle through hits 0, n/2, n-1 gives the curvature k0 and the
+//     direction psi0 at hit 0; arc lengths s_i (chord formula) and signed
+//     offsets m_i of the hits from that circle (left of the motion positive);
+//  2. multiple-scattering variances of the kinks at the inner hits (Highland,
+//     momentum from k0 and the pre-fit dip);
+//  3. s-z line fit: unknowns v_i, measurement z_i (sigma_z; disks sigma_r
+//     |tan lambda0|), kinks of the slope;
+//  4. transverse circle fit: unknowns u_i and dk, measurement m_i
+//     (sigma_rphi), kinks of the offset slope minus dk times the mean step;
+//  5. perigee parameters w.r.t. the beam line and their covariance (line block
+//     by its linear Jacobian, circle block by the analytic Jacobian).
+//
+// Precision: geometry in float32 -- coordinate differences are exact on the
+// 2^-14 cm grid, and the near-cancelling 2x2 products (pre-fit orientation,
+// projections on the pre-fit frame) use FMA-compensated evaluation -- and
+// the normal equations, their Cholesky factorisation, solutions and chi2 in
+// float64, where the kink weights (up to ~1e10) and measurement weights
+// (~1e6) make the matrices too ill-conditioned for float32.
+#include "pt_common.cuh"
+#include "pt_kernels.cuh"
+
+namespace ptk {
+
+// a*b - c*d with one rounding error (Kahan's algorithm with FMA)
+__device__ __forceinline__ float det2(float a, float b, float c, float d) {
+    float w = c * d;
+    float e = fmaf(-c, d, w);
+    float f = fmaf(a, b, -w);
+    return f + e;
+}
+
+__device__ __forceinline__ float asinc(float x) {
+    x = fminf(fmaxf(x, -1.0f), 1.0f);
+    return fabsf(x) < 1e-4f ? 1.0f + x * x * (1.0f / 6.0f) : asinf(x) / x;
+}
+
+template <int M>
+__device__ __forceinline__ int pidx(int r, int c) { return r * (r + 1) / 2 + c; }
+
+// in-place Cholesky of a packed lower-triangular SPD matrix
+template <int M>
+__device__ __forceinline__ void chol(double *A) {
+#pragma unroll
+    for (int j = 0; j < M; j++) {
+        double s = A[pidx<M>(j, j)];
+#pragma unroll
+        for (int k = 0; k < j; k++) s -= A[pidx<M>(j, k)] * A[pidx<M>(j, k)];
+        const double d = sqrt(s > 0.0 ? s : 1e-300);
+        A[pidx<M>(j, j)] = d;
+        const double id = 1.0 / d;
+#pragma unroll
+        for (int i = j + 1; i < M; i++) {
+            double t = A[pidx<M>(i, j)];
+#pragma unroll
+            for (int k = 0; k < j; k++) t -= A[pidx<M>(i, k)] * A[pidx<M>(j, k)];
+            A[pidx<M>(i, j)] = t * id;
+        }
+    }
+}
+
+template <int M>
+__device__ __forceinline__ void chol_solve(const double *L, double *b) {
+#pragma unroll
+    for (int i = 0; i < M; i++) {
+        double t = b[i];
+#pragma unroll
+        for (int k = 0; k < i; k++) t -= L[pidx<M>(i, k)] * b[k];
+        b[i] = t / L[pidx<M>(i, i)];
+    }
+#pragma unroll
+    for (int i = M - 1; i >= 0; i--) {
+        double t = b[i];
+#pragma unroll
+        for (int k = i + 1; k < M; k++) t -= L[pidx<M>(k, i)] * b[k];
+        b[i] = t / L[pidx<M>(i, i)];
+    }
+}
+
+template <int N>
+__device__ void fit_track(const Params &p, int64_t k, int32_t t) {
+    const int32_t *hid = p.tup_hits + (int64_t)t * PT_NMAX;
+    float hx[N], hy[N], hz[N];
+    bool disk[N];
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        const int h = hid[i];
+        hx[i] = p.x[h];
+        hy[i] = p.y[h];
+        hz[i] = p.z[h];
+        disk[i] = p.layer[p.module_layer[p.module[h]]].kind == PT_LAYER_DISK;
+    }
+    // 1) pre-fit circle through hits 0, n/2, n-1
+    constexpr int ib = N / 2, ic = N - 1;
+    const float abx = hx[ib] - hx[0], aby = hy[ib] - hy[0];
+    const float acx = hx[ic] - hx[0], acy = hy[ic] - hy[0];
+    const float bcx = hx[ic] - hx[ib], bcy = hy[ic] - hy[ib];
+    const float orient = det2(abx, acy, aby, acx);
+    const float dab = sqrtf(abx * abx + aby * aby), dbc = sqrtf(bcx * bcx + bcy * bcy);
+    const float dca = sqrtf(acx * acx + acy * acy);
+    const float den = dab * dbc * dca;
+    const float k0 = den > 0.f ? 2.0f * orient / den : 0.f;
+    const float psi0 = atan2f(aby, abx) - asinf(fminf(fmaxf(0.5f * k0 * dab, -1.f), 1.f));
+    float sn, cs;
+    sincosf(psi0, &sn, &cs);
+    float s[N], m[N], ds[N];
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        const float dx = hx[i] - hx[0], dy = hy[i] - hy[0];
+        const float dist = sqrtf(dx * dx + dy * dy);
+        s[i] = dist * asinc(0.5f * k0 * dist);
+        const float X = det2(dx, cs, -dy, sn);     // dx cs + dy sn
+        const float Y = det2(dy, cs, dx, sn);      // -dx sn + dy cs
+        const float U = k0 * (X * X + Y * Y) - 2.0f * Y;
+        const float q = 1.0f + k0 * U;
+        m[i] = -U / (1.0f + sqrtf(fmaxf(q, 0.f)));
+    }
+    ds[0] = 0.f;
+#pragma unroll
+    for (int i = 1; i < N; i++) ds[i] = fmaxf(s[i] - s[i - 1], 1e-4f);
+    const float tanl0 = (hz[N - 1] - hz[0]) / fmaxf(s[N - 1], 1e-4f);
+    const float sec2 = 1.0f + tanl0 * tanl0;
+    const float pt0 = 0.00299792458f * p.fit.bz / fmaxf(fabsf(k0), 1e-7f);
+    const float pmom = pt0 * sqrtf(sec2);
+    const float atl = fmaxf(fabsf(tanl0), 1e-3f);
+    // 2) scattering variances of the kinks at hits 1 .. n-2
+    double vb[N], vg[N];
+#pragma unroll
+    for (int i = 1; i < N - 1; i++) {
+        const float xx0 = disk[i] ? p.fit.x0_disk * sqrtf(sec2) / atl : p.fit.x0_barrel * sqrtf(sec2);
+        const float th = 0.0136f / pmom * sqrtf(xx0) * (1.0f + 0.038f * logf(xx0));
+        const double th2 = (double)th * th;
+        vb[i] = fmax(th2 * sec2, 1e-20);
+        vg[i] = fmax(th2 * sec2 * sec2, 1e-20);
+    }
+    // 3) line fit in s-z
+    double A[N * (N + 1) / 2], v[N], wz[N];
+#pragma unroll
+    for (int i = 0; i < N * (N + 1) / 2; i++) A[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        const double sz = disk[i] ? (double)p.fit.sigma_r * atl : (double)p.fit.sigma_z;
+        wz[i] = 1.0 / (sz * sz);
+        A[pidx<N>(i, i)] = wz[i];
+        v[i] = wz[i] * hz[i];
+    }
+#pragma unroll
+    for (int i = 1; i < N - 1; i++) {
+        const double g0 = 1.0 / ds[i], g2 = 1.0 / ds[i + 1], g1 = -(g0 + g2), w = 1.0 / vg[i];
+        A[pidx<N>(i - 1, i - 1)] += g0 * g0 * w;
+        A[pidx<N>(i, i - 1)] += g1 * g0 * w;
+        A[pidx<N>(i, i)] += g1 * g1 * w;
+        A[pidx<N>(i + 1, i - 1)] += g2 * g0 * w;
+        A[pidx<N>(i + 1, i)] += g2 * g1 * w;
+        A[pidx<N>(i + 1, i + 1)] += g2 * g2 * w;
+    }
+    chol<N>(A);
+    chol_solve<N>(A, v);
+    double chi2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; i++) chi2 += wz[i] * (v[i] - hz[i]) * (v[i] - hz[i]);
+#pragma unroll
+    for (int i = 1; i < N - 1; i++) {
+        const double gam = (v[i + 1] - v[i]) / ds[i + 1] - (v[i] - v[i - 1]) / ds[i];
+        chi2 += gam * gam / vg[i];
+    }
+    double Cv[2][2];
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        double e[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) e[i] = (i == c) ? 1.0 : 0.0;
+        chol_solve<N>(A, e);
+        Cv[0][c] = e[0];
+        Cv[1][c] = e[1];
+    }
+    // 4) circle fit: unknowns u_0 .. u_{n-1}, dk
+    constexpr int M = N + 1;
+    double B[M * (M + 1) / 2], x[M];
+#pragma unroll
+    for (int i = 0; i < M * (M + 1) / 2; i++) B[i] = 0.0;
+    const double wu = 1.0 / ((double)p.fit.sigma_rphi * p.fit.sigma_rphi);
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        B[pidx<M>(i, i)] = wu;
+        x[i] = wu * m[i];
+    }
+    x[N] = 0.0;
+#pragma unroll
+    for (int i = 1; i < N - 1; i++) {
+        const double h0 = 1.0 / ds[i], h2 = 1.0 / ds[i + 1], h1 = -(h0 + h2);
+        const double h3 = -0.5 * ((double)ds[i] + ds[i + 1]), w = 1.0 / vb[i];
+        B[pidx<M>(i - 1, i - 1)] += h0 * h0 * w;
+        B[pidx<M>(i, i - 1)] += h1 * h0 * w;
+        B[pidx<M>(i, i)] += h1 * h1 * w;
+        B[pidx<M>(i + 1, i - 1)] += h2 * h0 * w;
+        B[pidx<M>(i + 1, i)] += h2 * h1 * w;
+        B[pidx<M>(i + 1, i + 1)] += h2 * h2 * w;
+        B[pidx<M>(N, i - 1)] += h3 * h0 * w;
+        B[pidx<M>(N, i)] += h3 * h1 * w;
+        B[pidx<M>(N, i + 1)] += h3 * h2 * w;
+        B[pidx<M>(N, N)] += h3 * h3 * w;
+    }
+    chol<M>(B);
+    chol_solve<M>(B, x);
+    const double dk = x[N];
+#pragma unroll
+    for (int i = 0; i < N; i++) chi2 += wu * (x[i] - m[i]) * (x[i] - m[i]);
+#pragma unroll
+    for (int i = 1; i < N - 1; i++) {
+        const double be = (x[i + 1] - x[i]) / ds[i + 1] - (x[i] - x[i - 1]) / ds[i] -
+                          dk * 0.5 * ((double)ds[i] + ds[i + 1]);
+        chi2 += be * be / vb[i];
+    }
+    double Cc[3][3];
+    {
+        const int sel[3] = {0, 1, N};
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            double e[M];
+#pragma unroll
+            for (int i = 0; i < M; i++) e[i] = (i == sel[c]) ? 1.0 : 0.0;
+            chol_solve<M>(B, e);
+#pragma unroll
+            for (int r = 0; r < 3; r++) Cc[r][c] = e[sel[r]];
+        }
+    }
+    // 5) perigee of the fitted circle through P with direction psi
+    const float kf = (float)((double)k0 + dk);
+    const float u0 = (float)x[0];
+    const float px = hx[0] - u0 * sn, py = hy[0] + u0 * cs;
+    const float ds1 = ds[1];
+    const float psi = psi0 + (float)((x[1] - x[0]) / ds1 - dk * 0.5 * ds1);
+    float sp, cp;
+    sincosf(psi, &sp, &cp);
+    const float Xo = -det2(px, cp, -py, sp);       // -(P . t)
+    const float Yo = det2(px, sp, py, cp);         // -(P . n)
+    const float U = kf * (Xo * Xo + Yo * Yo) - 2.0f * Yo;
+    const float S = sqrtf(fmaxf(1.0f + kf * U, 0.f));
+    const float d0 = -U / (1.0f + S);
+    const float Aa = kf * Xo, Bb = 1.0f - kf * Yo;
+    const float dpsi = atan2f(Aa, Bb);
+    float phi0 = psi + dpsi;
+    phi0 = phi0 - 6.28318531f * rintf(phi0 * 0.159154943f);
+    const float arc = kf != 0.f ? dpsi / kf : Xo;
+    const double tanl = (v[1] - v[0]) / ds1;
+    const double z0 = v[0] + tanl * arc;
+    // circle-block Jacobian d(kappa, phi0, d0) / d(u0, u1, dk)
+    float J[3][3];
+    {
+        const float dPx[3] = {-sn, 0.f, 0.f}, dPy[3] = {cs, 0.f, 0.f};
+        const float dps[3] = {-1.0f / ds1, 1.0f / ds1, -0.5f * ds1};
+        const float dkk[3] = {0.f, 0.f, 1.f};
+        const float iS = S > 0.f ? 1.0f / S : 0.f;
+        const float ab2 = Aa * Aa + Bb * Bb;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const float dX = -(dPx[j] * cp + dPy[j] * sp) + Yo * dps[j];
+            const float dY = (dPx[j] * sp - dPy[j] * cp) - Xo * dps[j];
+            const float dU = (Xo * Xo + Yo * Yo) * dkk[j] + 2.0f * kf * Xo * dX + (2.0f * kf * Yo - 2.0f) * dY;
+            const float dS = 0.5f * iS * (U * dkk[j] + kf * dU);
+            const float dd0 = -dU / (1.0f + S) + U / ((1.0f + S) * (1.0f + S)) * dS;
+            const float dA = Xo * dkk[j] + kf * dX, dB = -Yo * dkk[j] - kf * dY;
+            const float ddpsi = (Bb * dA - Aa * dB) / ab2;
+            J[0][j] = -dkk[j];
+            J[1][j] = dps[j] + ddpsi;
+            J[2][j] = dd0;
+        }
+    }
+    float Fc[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            double acc = 0.0;
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+#pragma unroll
+                for (int d = 0; d < 3; d++) acc += (double)J[a][c] * Cc[c][d] * J[b][d];
+            Fc[a][b] = (float)acc;
+        }
+    const double Jl[2][2] = {{-1.0 / ds1, 1.0 / ds1}, {1.0 - arc / ds1, arc / ds1}};
+    float Fl[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            double acc = 0.0;
+#pragma unroll
+            for (int c = 0; c < 2; c++)
+#pragma unroll
+                for (int d = 0; d < 2; d++) acc += Jl[a][c] * Cv[c][d] * Jl[b][d];
+            Fl[a][b] = (float)acc;
+        }
+    float *par = p.trk_params + k * 5;
+    par[0] = -kf;
+    par[1] = phi0;
+    par[2] = (float)tanl;
+    par[3] = d0;
+    par[4] = (float)z0;
+    // order (kappa, phi0, tanl, d0, z0): circle block on {0,1,3}, line on {2,4}
+    float *cv = p.trk_cov + k * 15;
+    cv[0] = Fc[0][0];
+    cv[1] = Fc[1][0]; cv[2] = Fc[1][1];
+    cv[3] = 0.f; cv[4] = 0.f; cv[5] = Fl[0][0];
+    cv[6] = Fc[2][0]; cv[7] = Fc[2][1]; cv[8] = 0.f; cv[9] = Fc[2][2];
+    cv[10] = 0.f; cv[11] = 0.f; cv[12] = Fl[1][0]; cv[13] = 0.f; cv[14] = Fl[1][1];
+    p.trk_chi2[k] = (float)chi2;
+    p.trk_ndf[k] = (int8_t)(2 * N - 5);
+}
+
+__global__ void __launch_bounds__(kThreads) k_fit(Params p) {
+    const int64_t nk = min((int64_t)p.counters[C_TRACKS], p.cap_tracks);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nk; k += stride) {
+        const int32_t t = p.trk_tuple[k];
+        switch (p.tup_n[t]) {
+        case 3: fit_track<3>(p, k, t); break;
+        case 4: fit_track<4>(p, k, t); break;
+        case 5: fit_track<5>(p, k, t); break;
+        case 6: fit_track<6>(p, k, t); break;
+        case 7: fit_track<7>(p, k, t); break;
+        default: fit_track<8>(p, k, t); break;
+        }
+    }
+}
+
+void launch_fit(const Params &p, int grid, cudaStream_t s) { k_fit<<<grid, kThreads, 0, s>>>(p); }
+
+}  // namespace ptk

@@ -1,0 +1,115 @@
+// Steps a4 + a5: roots, depth-first search and shared-doublet cleaning
+// (Sec. 3.2, 3.3).
+//
+// The paper runs one DFS per root along outgoing edges.  Here every maximal
+// path is enumerated from its other end: one thread per leaf cell (live, no
+// outer neighbour) walks incoming edges -- stored contiguously per cell by
+// the connection kernel -- back to cells with no inner neighbour, and emits
+// the path when that cell is a root (inner hit on BPix1, or on BPix2 /
+// FPix1+- which, having no inner neighbour, qualifies) and the path has at
+// least three hits.  Root-to-leaf paths are the same set either way, and no
+// outgoing-edge lists need to be built.  Path length is bounded on the host
+// (the layer-pair graph admits no path longer than PT_NMAX hits).
+#include "pt_common.cuh"
+#include "pt_kernels.cuh"
+
+namespace ptk {
+
+__device__ __forceinline__ bool root_layer(int L) { return L == 0 || L == 1 || L == 4 || L == 7; }
+
+__global__ void __launch_bounds__(kThreads) k_dfs(Params p) {
+    const int64_t n_cells = min((int64_t)p.counters[C_CELLS], p.cap_cells);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += stride) {
+        if (!p.cell_alive[c] || p.has_out[c] || p.edge_cnt[c] == 0) continue;
+        int32_t st_cell[PT_NMAX - 1];
+        int32_t st_it[PT_NMAX - 1];
+        int depth = 0;
+        st_cell[0] = (int32_t)c;
+        st_it[0] = 0;
+        while (depth >= 0) {
+            const int x = st_cell[depth];
+            const int ne = p.edge_cnt[x];
+            if (ne == 0) {
+                // start of a path: emit if it is a root and the path has >= 3 hits
+                if (depth >= 1 && root_layer(p.blayer[p.cell_inner[x]])) {
+                    const int t = atomicAdd(p.counters + C_TUPLES, 1);
+                    if (t < p.cap_tuples) {
+                        const int n = depth + 2;
+                        int32_t *hits = p.tup_hits + (int64_t)t * PT_NMAX;
+                        int32_t *cells = p.tup_cells + (int64_t)t * PT_NMAX;
+                        hits[0] = p.perm[p.cell_inner[x]];
+                        for (int k = 0; k <= depth; k++) {
+                            const int cc = st_cell[depth - k];
+                            cells[k] = cc;
+                            hits[k + 1] = p.perm[p.cell_outer[cc]];
+                        }
+                        p.tup_n[t] = (uint8_t)n;
+                        p.tup_alive[t] = 1;
+                    } else {
+                        set_flag(p.counters, PT_FLAG_TUPLES);
+                    }
+                }
+                depth--;
+                continue;
+            }
+            if (st_it[depth] < ne) {
+                const int64_t eidx = (int64_t)p.edge_off[x] + st_it[depth];
+                st_it[depth]++;
+                if (eidx >= p.cap_edges || depth + 1 >= PT_NMAX - 1) continue;
+                depth++;
+                st_cell[depth] = p.edge_src[eidx];
+                st_it[depth] = 0;
+            } else {
+                depth--;
+            }
+        }
+    }
+}
+
+// L(c) = longest n-tuplet containing cell c
+__global__ void __launch_bounds__(kThreads) k_clean_max(Params p) {
+    const int64_t nt = min((int64_t)p.counters[C_TUPLES], p.cap_tuples);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
+        const int n = p.tup_n[t];
+        const int32_t *cells = p.tup_cells + t * PT_NMAX;
+        for (int k = 0; k < n - 1; k++) atomicMax(p.maxlen + cells[k], n);
+    }
+}
+
+// keep an n-tuplet unless one of its cells belongs to a longer one
+__global__ void __launch_bounds__(kThreads) k_clean_keep(Params p) {
+    const int64_t nt = min((int64_t)p.counters[C_TUPLES], p.cap_tuples);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
+        const int n = p.tup_n[t];
+        const int32_t *cells = p.tup_cells + t * PT_NMAX;
+        bool keep = true;
+        for (int k = 0; k < n - 1; k++) keep = keep && n >= p.maxlen[cells[k]];
+        p.tup_alive[t] = keep;
+        if (keep) atomicAdd(p.counters + C_ALIVE_TUPLES, 1);
+    }
+}
+
+// queue the surviving n-tuplets with >= min_hits hits for the fit
+__global__ void __launch_bounds__(kThreads) k_select_tracks(Params p) {
+    const int64_t nt = min((int64_t)p.counters[C_TUPLES], p.cap_tuples);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
+        if (!p.tup_alive[t] || p.tup_n[t] < p.min_hits) continue;
+        const int k = atomicAdd(p.counters + C_TRACKS, 1);
+        if (k < p.cap_tracks) p.trk_tuple[k] = (int32_t)t;
+        else set_flag(p.counters, PT_FLAG_TRACKS);
+    }
+}
+
+void launch_select(const Params &p, int grid, cudaStream_t s) { k_select_tracks<<<grid, kThreads, 0, s>>>(p); }
+
+void launch_ntuplets(const Params &p, int grid, cudaStream_t s) {
+    k_dfs<<<grid, kThreads, 0, s>>>(p);
+    k_clean_max<<<grid, kThreads, 0, s>>>(p);
+    k_clean_keep<<<grid, kThreads, 0, s>>>(p);
+}
+
+}  // namespace ptk

@@ -1,0 +1,194 @@
+"""Batched seeding + fitting pipeline over the C ABI (include/pt.h).
+
+PyTorch provides device memory and streams; every step runs in the CUDA
+library.  A ``Pipeline`` holds the configuration (geometry, cuts, fit
+constants, tuning); ``Buffers`` holds the workspace and the output tensors for
+one problem size; ``launch`` enqueues the four stages on a stream without any
+host synchronisation (so it can be captured in a CUDA graph); ``run`` adds
+the count read-back and grows the buffers when a capacity was exceeded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+
+import torch
+
+from . import _lib as L
+
+DEFAULT_TUNING = dict(n_phi_bins=128, n_t_bins=16, doublet_lanes=8, connect_lanes=8, blocks_per_sm=8)
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+@dataclasses.dataclass
+class Buffers:
+    n_hits: int
+    n_events: int
+    capacity: dict
+    ws: torch.Tensor
+    cell_inner: torch.Tensor
+    cell_outer: torch.Tensor
+    cell_pair: torch.Tensor
+    cell_alive: torch.Tensor
+    edge_src: torch.Tensor
+    edge_dst: torch.Tensor
+    tup_hits: torch.Tensor
+    tup_cells: torch.Tensor
+    tup_n: torch.Tensor
+    tup_alive: torch.Tensor
+    trk_params: torch.Tensor
+    trk_cov: torch.Tensor
+    trk_chi2: torch.Tensor
+    trk_ndf: torch.Tensor
+    trk_tuple: torch.Tensor
+
+    def structs(self):
+        cells = L.Cells(_ptr(self.cell_inner), _ptr(self.cell_outer), _ptr(self.cell_pair), _ptr(self.cell_alive))
+        edges = L.Edges(_ptr(self.edge_src), _ptr(self.edge_dst))
+        tuples = L.Tuples(_ptr(self.tup_hits), _ptr(self.tup_cells), _ptr(self.tup_n), _ptr(self.tup_alive))
+        tracks = L.Tracks(_ptr(self.trk_params), _ptr(self.trk_cov), _ptr(self.trk_chi2), _ptr(self.trk_ndf),
+                          _ptr(self.trk_tuple))
+        return cells, edges, tuples, tracks
+
+
+@dataclasses.dataclass
+class Result:
+    counts: L.Counts
+    cells: dict
+    edges: dict
+    tuples: dict
+    tracks: dict
+    hit_order: torch.Tensor
+
+
+class Pipeline:
+    def __init__(self, layers, module_layer, cuts: dict, fit: dict, tuning: dict | None = None,
+                 device: str | torch.device = "cuda"):
+        self.device = torch.device(device)
+        self.module_layer = torch.as_tensor(module_layer, dtype=torch.int32).to(self.device).contiguous()
+        self.tuning = dict(DEFAULT_TUNING, **(tuning or {}))
+        cfg = L.Config()
+        for i, ly in enumerate(layers):
+            cfg.geometry.layer[i] = L.Layer(ly.kind, ly.rmin, ly.rmax, ly.zmin, ly.zmax)
+        cfg.geometry.module_layer = self.module_layer.data_ptr()
+        cfg.geometry.n_modules = self.module_layer.numel()
+        cfg.cuts.n_pairs = len(cuts["pairs"])
+        for i, p in enumerate(cuts["pairs"]):
+            cfg.cuts.pair[i] = L.PairCuts(p["inner"], p["outer"], p["tan2_dphi"], p["zlo"], p["zhi"], p["zmax"],
+                                          p["k_pt"])
+        for i, rg in enumerate(cuts["region"]):
+            cfg.cuts.region[i] = L.CaCuts(rg["tol_rz2"], rg["k_curv"], rg["rmax2"], rg["zmax"])
+        cfg.cuts.fishbone_eps2 = cuts["fishbone_eps2"]
+        cfg.cuts.min_hits = cuts["min_hits"]
+        cfg.fit = L.FitParams(fit["bz"], fit["sigma_rphi"], fit["sigma_z"], fit["sigma_r"], fit["x0_barrel"],
+                              fit["x0_disk"], 0)
+        t = self.tuning
+        cfg.tuning = L.Tuning(t["n_phi_bins"], t["n_t_bins"], t["doublet_lanes"], t["connect_lanes"],
+                              t["blocks_per_sm"])
+        self.cfg = cfg
+        L.lib()
+
+    # ------------------------------------------------------------ buffers
+    @staticmethod
+    def default_capacity(n_hits: int) -> dict:
+        n = max(n_hits, 64)
+        return dict(cells=96 * n, edges=12 * n, tuples=12 * n, tracks=12 * n)
+
+    def _hits(self, x, y, z, r, module, ev_off) -> L.Hits:
+        return L.Hits(x.data_ptr(), y.data_ptr(), z.data_ptr(), r.data_ptr(), module.data_ptr(), ev_off.data_ptr(),
+                      x.numel(), ev_off.numel() - 1)
+
+    def _cfg(self, capacity: dict) -> L.Config:
+        c = L.Config.from_buffer_copy(self.cfg)
+        c.capacity = L.Capacity(capacity["cells"], capacity["edges"], capacity["tuples"], capacity["tracks"])
+        return c
+
+    def allocate(self, n_hits: int, n_events: int, capacity: dict | None = None) -> Buffers:
+        cap = dict(capacity or self.default_capacity(n_hits))
+        cfg = self._cfg(cap)
+        h = L.Hits(None, None, None, None, None, None, n_hits, n_events)
+        nbytes = L.workspace_size(h, cfg)
+        if nbytes == 0:
+            raise ValueError("invalid sizes or tuning for the workspace")
+        d, i32, u8 = self.device, torch.int32, torch.uint8
+        ws = torch.empty(nbytes, dtype=u8, device=d)
+        nc, ne, nt, nk = (max(1, int(cap[k])) for k in ("cells", "edges", "tuples", "tracks"))
+        return Buffers(
+            n_hits, n_events, cap, ws,
+            torch.empty(nc, dtype=i32, device=d), torch.empty(nc, dtype=i32, device=d),
+            torch.empty(nc, dtype=u8, device=d), torch.empty(nc, dtype=u8, device=d),
+            torch.empty(ne, dtype=i32, device=d), torch.empty(ne, dtype=i32, device=d),
+            torch.empty(nt * L.NMAX, dtype=i32, device=d), torch.empty(nt * L.NMAX, dtype=i32, device=d),
+            torch.empty(nt, dtype=u8, device=d), torch.empty(nt, dtype=u8, device=d),
+            torch.empty(nk * 5, dtype=torch.float32, device=d), torch.empty(nk * 15, dtype=torch.float32, device=d),
+            torch.empty(nk, dtype=torch.float32, device=d), torch.empty(nk, dtype=torch.int8, device=d),
+            torch.empty(nk, dtype=i32, device=d))
+
+    # ------------------------------------------------------------- launch
+    def launch(self, bufs: Buffers, x, y, z, r, module, ev_off, stream: torch.cuda.Stream | None = None) -> None:
+        """Enqueue the four stages on `stream` (default: current stream); no sync."""
+        s = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        h = self._hits(x, y, z, r, module, ev_off)
+        cfg = self._cfg(bufs.capacity)
+        cells, edges, tuples, tracks = bufs.structs()
+        ws, nb = bufs.ws.data_ptr(), bufs.ws.numel()
+        L.build_doublets(ws, nb, h, cfg, cells, s)
+        L.connect_cells(ws, nb, h, cfg, cells, edges, s)
+        L.find_ntuplets(ws, nb, h, cfg, cells, edges, tuples, s)
+        L.fit_tracks(ws, nb, h, cfg, tuples, tracks, s)
+
+    def counts(self, bufs: Buffers, x, y, z, r, module, ev_off, stream=None) -> tuple[int, L.Counts]:
+        s = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        return L.read_counts(bufs.ws.data_ptr(), bufs.ws.numel(), self._hits(x, y, z, r, module, ev_off),
+                             self._cfg(bufs.capacity), s)
+
+    def hit_order(self, bufs: Buffers, x, y, z, r, module, ev_off) -> torch.Tensor:
+        """Binned position -> input hit index (a view into the workspace)."""
+        h = self._hits(x, y, z, r, module, ev_off)
+        ptr = L.hit_order(bufs.ws.data_ptr(), bufs.ws.numel(), h, self._cfg(bufs.capacity))
+        off = ptr - bufs.ws.data_ptr()
+        return bufs.ws[off:off + 4 * max(1, x.numel())].view(torch.int32)[:x.numel()]
+
+    def result(self, bufs: Buffers, counts: L.Counts, x, y, z, r, module, ev_off) -> Result:
+        nc, ne, nt, nk = counts.n_cells, counts.n_edges, counts.n_tuples, counts.n_tracks
+        return Result(
+            counts=counts,
+            cells=dict(inner=bufs.cell_inner[:nc], outer=bufs.cell_outer[:nc], pair=bufs.cell_pair[:nc],
+                       alive=bufs.cell_alive[:nc]),
+            edges=dict(src=bufs.edge_src[:ne], dst=bufs.edge_dst[:ne]),
+            tuples=dict(hits=bufs.tup_hits[:nt * L.NMAX].view(-1, L.NMAX), cells=bufs.tup_cells[:nt * L.NMAX]
+                        .view(-1, L.NMAX), n=bufs.tup_n[:nt], alive=bufs.tup_alive[:nt]),
+            tracks=dict(params=bufs.trk_params[:nk * 5].view(-1, 5), cov=bufs.trk_cov[:nk * 15].view(-1, 15),
+                        chi2=bufs.trk_chi2[:nk], ndf=bufs.trk_ndf[:nk], tuple=bufs.trk_tuple[:nk]),
+            hit_order=self.hit_order(bufs, x, y, z, r, module, ev_off),
+        )
+
+    def run(self, x, y, z, r, module, ev_off, bufs: Buffers | None = None, max_retries: int = 3):
+        """Run the batch and read the counts back; grow buffers on overflow.
+        Returns (Result, Buffers)."""
+        if bufs is None:
+            bufs = self.allocate(x.numel(), ev_off.numel() - 1)
+        for _ in range(max_retries + 1):
+            self.launch(bufs, x, y, z, r, module, ev_off)
+            st, c = self.counts(bufs, x, y, z, r, module, ev_off)
+            if st == L.PT_OK:
+                return self.result(bufs, c, x, y, z, r, module, ev_off), bufs
+            if st != L.PT_ERR_CAPACITY:
+                raise L.PtError(st, f"pipeline (flags 0x{c.flags:x})")
+            need = dict(cells=c.n_cells, edges=c.n_edges, tuples=c.n_tuples, tracks=c.n_tracks)
+            cap = {k: max(bufs.capacity[k], int(need[k] * 1.25) + 1024) for k in need}
+            bufs = self.allocate(x.numel(), ev_off.numel() - 1, cap)
+        raise L.PtError(L.PT_ERR_CAPACITY, "pipeline: capacity still exceeded after retries")
+
+    def run_per_event(self, x, y, z, r, module, ev_off_host, bufs_list=None):
+        """The plain per-event form: the same kernels on one event at a time,
+        with a host read of the counts after each stage."""
+        out = []
+        for e in range(len(ev_off_host) - 1):
+            a, b = int(ev_off_host[e]), int(ev_off_host[e + 1])
+            off = torch.tensor([0, b - a], dtype=torch.int32, device=self.device)
+            out.append(self.run(x[a:b], y[a:b], z[a:b], r[a:b], module[a:b], off)[0])
+        return out

@@ -1,0 +1,47 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports
+every function include/pt.h declares (no compute call is made)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pt_[a-z_]+)\s*\(", src)))
+
+
+def test_header_lists_the_stage_entry_points():
+    names = declared_functions()
+    for n in ("pt_build_doublets", "pt_connect_cells", "pt_find_ntuplets", "pt_fit_tracks"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2008_13461_gb300 import _lib, build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+    assert set(_lib.EXPORTS) == set(declared_functions())
+
+
+def test_status_strings_without_gpu():
+    from paper_2008_13461_gb300 import _lib
+    L = _lib.lib()
+    assert L.pt_status_string(0) == b"ok"
+    assert L.pt_status_string(2) == b"output capacity exceeded"
+
+
+def test_workspace_size_is_host_only():
+    from paper_2008_13461_gb300 import _lib as L
+    cfg = L.Config()
+    cfg.tuning = L.Tuning(128, 16, 8, 8, 8)
+    cfg.capacity = L.Capacity(1000, 100, 100, 100)
+    h = L.Hits(None, None, None, None, None, None, 5000, 4)
+    n = L.workspace_size(h, cfg)
+    assert n > 4 * 128 * 16 * 10 * 4
+    cfg.tuning = L.Tuning(7, 16, 8, 8, 8)
+    assert L.workspace_size(h, cfg) == 0
