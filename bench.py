@@ -1,0 +1,442 @@
+"""Throughput benchmark of the pixel seeding + broken-line fitting path.
+
+One step = the four stages (doublets + Fishbone, CA connection, n-tuplets +
+cleaning, broken-line fit) over one batch of 64 synthetic PU200 events (about
+1.7 M hits), inputs resident on the GPU.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+N > 1 runs under torchrun, one rank per GPU, each rank on its own 64 events
+(weak scaling, no collective on the data path).  --impl reference times the
+CPU oracle (the plain FP64 / exact-integer implementation the GPU path is
+checked against) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "events/s and tracks/s at PU200 (1 GB300) vs plain per-event GPU; % HBM roofline"
+WORKLOAD = "pu200-batch64: 64 synthetic ttbar-like events, pileup Poisson(200), ~1.7M hits"
+EVENTS_PER_STEP = 64
+SECTOR = 16          # oracle sample: 1/SECTOR of the azimuth of one PU200 event
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------- CPU oracle
+def _oracle_sample(batch):
+    import numpy as np
+    phi = np.arctan2(batch["y"], batch["x"])
+    a, b = batch["ev_off"][0], batch["ev_off"][1]
+    m = np.zeros(batch["x"].size, bool)
+    m[a:b] = True
+    m &= (phi >= 0) & (phi < 2 * np.pi / SECTOR)
+    s = {k: batch[k][m] for k in ("x", "y", "z", "r", "module")}
+    s["ev_off"] = np.array([0, int(m.sum())], dtype=np.int32)
+    return s
+
+
+def _time_oracle(sample, repeats):
+    import oracle
+    from synth import cuts as CU
+    from synth import geometry as G
+    oracle.build()
+    times = []
+    for _ in range(repeats):
+        t = time.perf_counter()
+        oracle.run(sample, CU.cuts_for_config(3), CU.FIT_PARAMS, G.module_layer_table(), [0] * 4 + [1] * 6)
+        times.append(time.perf_counter() - t)
+    return times
+
+
+def _cpu_desc(n_hits):
+    return (f"1/{SECTOR} azimuthal sector (phi in [0, 2pi/{SECTOR})) of PU200 event 0, {n_hits} hits, all "
+            f"stages; events/s = 1/({SECTOR} x sector time), which overstates the oracle's full-event rate "
+            f"because its doublet search is quadratic in the hits of an event")
+
+
+# ------------------------------------------------------------ clock sampling
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.idx = gpu_index
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ bytes
+def algorithmic_bytes(H, D, E, T, K, nbar):
+    """Bytes each stage must move at least (each input read once, each output
+    written once): binning 20H + 24H; doublets 16H per layer-pair slot
+    (3.4 on average) + 9D (cell) + 8H (per-hit cell range); Fishbone 8D read +
+    1D write; connection 13D + 4E + 4E (edge src, dst); n-tuplets 8E + 8D read
+    + 66T written (hits, cells, n, alive); cleaning 66T; fit 36K + 12 nbar K
+    read + 88K written."""
+    return {
+        "binning": 44 * H,
+        "doublets": 16 * 3.4 * H + 9 * D + 8 * H,
+        "fishbone": 9 * D,
+        "connect": 13 * D + 8 * E,
+        "ntuplets": 8 * E + 8 * D + 66 * T + 66 * T,
+        "fit": 36 * K + 12 * nbar * K + 88 * K,
+    }
+
+
+
+class Ctx:
+    """Everything the extra measurements need from the main run."""
+
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+
+
+def measure_graph(c, args):
+    """Median time of a CUDA-graph replay of the four stages."""
+    import torch
+    from paper_2008_13461_gb300 import _lib as L
+    try:
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(c.dev)
+        side.wait_stream(c.stream)
+        with torch.cuda.stream(side):
+            ss = side.cuda_stream
+            with torch.cuda.graph(g, stream=side):
+                L.build_doublets(c.ws, c.nb, c.h, c.cfg, c.cells, ss)
+                L.connect_cells(c.ws, c.nb, c.h, c.cfg, c.cells, c.edges, ss)
+                L.find_ntuplets(c.ws, c.nb, c.h, c.cfg, c.cells, c.edges, c.tuples, ss)
+                L.fit_tracks(c.ws, c.nb, c.h, c.cfg, c.tuples, c.tracks, ss)
+        c.stream.wait_stream(side)
+        torch.cuda.synchronize()
+        ge = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        gms = []
+        for _ in range(max(3, args.steps // 2)):
+            c.flush.zero_()
+            ge[0].record(c.stream)
+            g.replay()
+            ge[1].record(c.stream)
+            torch.cuda.synchronize()
+            gms.append(ge[0].elapsed_time(ge[1]))
+        st, c3 = L.read_counts(c.ws, c.nb, c.h, c.cfg, c.s)
+        assert st == L.PT_OK and c3.n_tracks == c.counts.n_tracks
+        return statistics.median(gms)
+    except Exception as exc:   # reported, never required
+        return f"unavailable: {exc}"
+
+
+def measure_e2e(c, args, batch, world):
+    """Events/s through the public API with host buffers: pinned host inputs
+    copied to the device, the four stages, counts and track parameters copied
+    back to pinned host memory, every step."""
+    import torch
+    host = {k: torch.as_tensor(batch[k]).pin_memory() for k in ("x", "y", "z", "r", "module", "ev_off")}
+    out_host = torch.empty(max(1, c.counts.n_tracks) * 5 * 2, dtype=torch.float32).pin_memory()
+    dbuf = {k: torch.empty_like(v, device=c.dev) for k, v in host.items()}
+    dargs = (dbuf["x"], dbuf["y"], dbuf["z"], dbuf["r"], dbuf["module"], dbuf["ev_off"])
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    times, d2h = [], 0
+    for k in range(args.warmup + args.steps):
+        c.flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for key in host:
+            dbuf[key].copy_(host[key], non_blocking=True)
+        c.pipe.launch(c.bufs, *dargs)
+        st, c4 = c.pipe.counts(c.bufs, *dargs)
+        n5 = c4.n_tracks * 5
+        out_host[:n5].copy_(c.bufs.trk_params[:n5], non_blocking=True)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+            d2h = n5 * 4 + 64
+    n_events = (len(batch["ev_off"]) - 1) * world
+    return {"value": n_events / statistics.mean(times), "unit": "events/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h}
+
+
+def measure_per_event(c, batch):
+    """Seconds for the plain per-event GPU form over the batch: the same
+    kernels one event at a time, with a host read of the counts after every
+    stage."""
+    import numpy as np
+    import torch
+    from paper_2008_13461_gb300 import _lib as L
+    ev_host = batch["ev_off"]
+    sizes = np.diff(ev_host)
+    cap = {k: max(v // 8, 1 << 20) for k, v in c.bufs.capacity.items()}
+    ebufs = c.pipe.allocate(int(sizes.max()), 1, cap)
+    ecfg = c.pipe._cfg(ebufs.capacity)
+    ec, ee, et, ek = ebufs.structs()
+    ews, enb = ebufs.ws.data_ptr(), ebufs.ws.numel()
+    offs = [torch.tensor([0, int(n)], dtype=torch.int32, device=c.dev) for n in sizes]
+    t, s = c.t, c.s
+
+    def one_pass():
+        for e in range(len(sizes)):
+            a, b = int(ev_host[e]), int(ev_host[e + 1])
+            eh = c.pipe._hits(t["x"][a:b], t["y"][a:b], t["z"][a:b], t["r"][a:b], t["module"][a:b], offs[e])
+            L.build_doublets(ews, enb, eh, ecfg, ec, s)
+            L.read_counts(ews, enb, eh, ecfg, s)
+            L.connect_cells(ews, enb, eh, ecfg, ec, ee, s)
+            L.read_counts(ews, enb, eh, ecfg, s)
+            L.find_ntuplets(ews, enb, eh, ecfg, ec, ee, et, s)
+            L.read_counts(ews, enb, eh, ecfg, s)
+            L.fit_tracks(ews, enb, eh, ecfg, et, ek, s)
+            stc, _ = L.read_counts(ews, enb, eh, ecfg, s)
+            assert stc == L.PT_OK
+
+    one_pass()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    one_pass()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0
+
+
+# ---------------------------------------------------------------- native
+def run_native(args, rank, world, local_rank):
+    import numpy as np
+    from synth import cuts as CU
+    from synth import events as E
+    from synth import geometry as G
+
+    workers = max(1, min(16, (os.cpu_count() or 4) // max(1, world)))
+    n_ev = args.events
+    batch = E.make_batch(3, n_events=n_ev, first=rank * n_ev, workers=workers)
+    import torch
+    import torch.distributed as dist
+    from paper_2008_13461_gb300 import _lib as L
+    from paper_2008_13461_gb300.pipeline import Pipeline
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    pipe = Pipeline(G.layers(), G.module_layer_table(), CU.cuts_for_config(3), CU.FIT_PARAMS, device=dev)
+    t = {k: torch.as_tensor(batch[k]).to(dev) for k in ("x", "y", "z", "r", "module", "ev_off")}
+    args6 = (t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
+    res, bufs = pipe.run(*args6)
+    counts = res.counts
+    stream = torch.cuda.current_stream(dev)
+    s = stream.cuda_stream
+    h = pipe._hits(*args6)
+    cfg = pipe._cfg(bufs.capacity)
+    cells, edges, tuples, tracks = bufs.structs()
+    ws, nb = bufs.ws.data_ptr(), bufs.ws.numel()
+    stages = (lambda: L.build_doublets(ws, nb, h, cfg, cells, s),
+              lambda: L.connect_cells(ws, nb, h, cfg, cells, edges, s),
+              lambda: L.find_ntuplets(ws, nb, h, cfg, cells, edges, tuples, s),
+              lambda: L.fit_tracks(ws, nb, h, cfg, tuples, tracks, s))
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        for i, f in enumerate(stages):
+            f()
+            if evs:
+                evs[i + 1].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    st, c2 = L.read_counts(ws, nb, h, cfg, s)
+    assert st == L.PT_OK and c2.n_tracks == counts.n_tracks, "results changed between runs"
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local_rank) if rank == 0 else None
+    for k in range(args.steps):
+        flush.zero_()
+        step(evs[k])
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    step_ms = [e[0].elapsed_time(e[4]) for e in evs]
+    stage_ms = [statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i in range(4)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    ctx = Ctx(dev=dev, stream=stream, s=s, ws=ws, nb=nb, h=h, cfg=cfg, cells=cells, edges=edges, tuples=tuples,
+              tracks=tracks, flush=flush, counts=counts, pipe=pipe, bufs=bufs, t=t)
+
+    graph_ms = e2e = per_event_s = "skipped"
+    if not args.no_extras:
+        graph_ms = measure_graph(ctx, args)
+        e2e = measure_e2e(ctx, args, batch, world)
+        if rank == 0:
+            per_event_s = measure_per_event(ctx, batch)
+
+    # roofline of the dominant kernel
+    H, D, Ed, T, K = bufs.n_hits, counts.n_cells, counts.n_edges, counts.n_tuples, counts.n_tracks
+    n = res.tuples["n"].cpu().numpy()
+    nbar = float(n[res.tracks["tuple"].cpu().numpy()].mean()) if K else 0.0
+    ab = algorithmic_bytes(H, D, Ed, T, K, nbar)
+    stage_bytes = [ab["binning"] + ab["doublets"] + ab["fishbone"], ab["connect"], ab["ntuplets"], ab["fit"]]
+    stage_names = ["build_doublets", "connect_cells", "find_ntuplets", "fit_tracks"]
+    dom = max(range(4), key=lambda i: stage_ms[i])
+    peak, peak_kind = _peaks()
+    achieved = stage_bytes[dom] / (stage_ms[dom] * 1e-3) / 1e9
+
+    if rank != 0:
+        return None
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        sample = _oracle_sample(batch)
+        times = _time_oracle(sample, repeats=3)
+        tm = statistics.median(times)
+        cpu = {"value": 1.0 / (SECTOR * tm), "unit": "events/s", "cores": 1, "kind": "oracle",
+               "sample": _cpu_desc(int(sample["x"].size)), "seconds_per_sample": tm}
+    events_total = n_ev * world
+    value = events_total / (ms_per_step * 1e-3)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "events/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 (graph predicates exact; fit normal equations f64)",
+        "data": "synthetic (seeded helical-track events; the paper's CMS Open Data sample is not available)",
+        "config": {"workload": WORKLOAD if n_ev == EVENTS_PER_STEP else f"pu200-batch{n_ev} (profiling size)",
+                   "events_per_step": n_ev, "hits_per_step": H,
+                   "parallelism": f"replicas x{world} (events sharded per rank)",
+                   "l2": "512 MiB buffer written between timed steps (L2 flush)",
+                   "tuning": pipe.tuning},
+        "tracks_per_s": K * world / (ms_per_step * 1e-3),
+        "counts_per_step": {"hits": H, "cells": D, "alive_cells": counts.n_alive_cells, "edges": Ed,
+                            "ntuplets": T, "alive_ntuplets": counts.n_alive_tuples, "tracks": K,
+                            "exact_fallbacks": counts.n_exact_fallbacks},
+        "stage_ms": dict(zip(stage_names, stage_ms)),
+        "graph_ms_per_step": graph_ms,
+        "per_event_form": per_event_s if isinstance(per_event_s, str) else {
+            "events_per_s": n_ev / per_event_s,
+            "note": "same kernels one event at a time, host read of counts after every stage"},
+        "e2e": e2e,
+        "roofline": {"bound": "hbm", "kernel": stage_names[dom], "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                     "algorithmic_bytes": stage_bytes[dom], "traffic": None},
+        "gpu_launches": 13 * args.steps,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    return line
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from synth import events as E
+    batch = E.make_batch(3, n_events=1)
+    sample = _oracle_sample(batch)
+    times = _time_oracle(sample, repeats=args.warmup + args.steps)[args.warmup:]
+    value = args.steps / (SECTOR * sum(times))
+    cpu = {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
+           "sample": _cpu_desc(int(sample["x"].size))}
+    return {
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 / exact integer", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": cpu["sample"]},
+        "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("native", "reference"), default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--events", type=int, default=EVENTS_PER_STEP,
+                    help="events per step (default 64; smaller batches are for profiling runs)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the CUDA-graph, end-to-end and per-event measurements")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        line = run_native(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

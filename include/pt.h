@@ -117,7 +117,7 @@ typedef struct {
     float tol_rz2, k_curv, rmax2, zmax;
 } pt_ca_cuts;
 
-/* All cut constants.  Every float constant must lie in [2^-40, 2^40].
+/* All cut constants.  Every float constant must lie in [2^-30, 2^40].
  * Fishbone (Sec. 3.3): cells (h1,h) and (h2,h) sharing the outer hit h, with
  * inner hits on one layer, are aligned when u = h1-h, v = h2-h satisfy
  * u.v > 0 and |u x v|^2 <= fishbone_eps2 |u|^2 |v|^2; an aligned cell dies if
@@ -143,7 +143,8 @@ typedef struct {
     int32_t n_phi_bins;     /* azimuthal tiles per layer, 16..1024 */
     int32_t n_t_bins;       /* tiles along z (barrel) or r (disks), 1..64 */
     int32_t doublet_lanes;  /* lanes per outer hit: 4, 8, 16 or 32 */
-    int32_t connect_lanes;  /* lanes per outer cell: 4, 8, 16 or 32 */
+    int32_t connect_lanes;  /* reserved (4, 8, 16 or 32 accepted); the CA
+                               connection runs one warp per middle hit */
     int32_t blocks_per_sm;  /* persistent grid size factor, 1..32 */
 } pt_tuning;
 

@@ -43,18 +43,20 @@ bool layout(const pt_hits *h, const pt_config *cfg, WsLayout &L) {
     };
     L.counters = take(sizeof(int32_t) * kCounters);
     L.bin_cnt = take(sizeof(int32_t) * (size_t)(n_bins + 1));
-    L.scan_part = take(sizeof(int32_t) * (size_t)(L.n_scan_blocks + 1));
+    const int64_t hit_blocks = (int64_t)(nh + kScanItems - 1) / kScanItems;
+    L.scan_part = take(sizeof(int32_t) * (size_t)((L.n_scan_blocks > hit_blocks ? L.n_scan_blocks : hit_blocks) + 1));
     L.hit_bin = take(4 * nh);
     L.hit_rank = take(4 * nh);
-    L.bx = take(4 * nh);
-    L.by = take(4 * nh);
-    L.bz = take(4 * nh);
-    L.br = take(4 * nh);
+    L.bh = take(16 * nh);
     L.blayer = take(nh);
     L.bev = take(4 * nh);
     L.perm = take(4 * nh);
     L.in_off = take(4 * nh);
     L.in_cnt = take(4 * nh);
+    L.out_off = take(4 * (nh + 1));
+    L.cell_rank = take(4 * nc);
+    L.out_idx = take(4 * nc);
+    L.leaf_list = take(4 * nc);
     L.edge_off = take(4 * nc);
     L.edge_cnt = take(4 * nc);
     L.has_out = take(nc);
@@ -159,15 +161,16 @@ Params make_params(void *ws, const WsLayout &L, const pt_hits *h, const pt_confi
     p.scan_part = (int32_t *)(w + L.scan_part);
     p.hit_bin = (int32_t *)(w + L.hit_bin);
     p.hit_rank = (int32_t *)(w + L.hit_rank);
-    p.bx = (float *)(w + L.bx);
-    p.by = (float *)(w + L.by);
-    p.bz = (float *)(w + L.bz);
-    p.br = (float *)(w + L.br);
+    p.bh = (float4 *)(w + L.bh);
     p.blayer = (int8_t *)(w + L.blayer);
     p.bev = (int32_t *)(w + L.bev);
     p.perm = (int32_t *)(w + L.perm);
     p.in_off = (int32_t *)(w + L.in_off);
     p.in_cnt = (int32_t *)(w + L.in_cnt);
+    p.out_off = (int32_t *)(w + L.out_off);
+    p.cell_rank = (int32_t *)(w + L.cell_rank);
+    p.out_idx = (int32_t *)(w + L.out_idx);
+    p.leaf_list = (int32_t *)(w + L.leaf_list);
     p.edge_off = (int32_t *)(w + L.edge_off);
     p.edge_cnt = (int32_t *)(w + L.edge_cnt);
     p.has_out = (uint8_t *)(w + L.has_out);
@@ -238,14 +241,17 @@ pt_status pt_build_doublets(void *ws, size_t ws_bytes, const pt_hits *hits, cons
     if (cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * kCounters, s) != cudaSuccess) return PT_ERR_CUDA;
     if (cudaMemsetAsync(p.bin_cnt, 0, sizeof(int32_t) * (size_t)(L.n_bins + 1), s) != cudaSuccess)
         return PT_ERR_CUDA;
+    if (cudaMemsetAsync(p.out_off, 0, sizeof(int32_t) * ((size_t)hits->n_hits + 1), s) != cudaSuccess)
+        return PT_ERR_CUDA;
     const int grid = grid_for(cfg);
     launch_binning(p, grid, s);
     launch_doublets(p, cfg->tuning.doublet_lanes, grid, s);
     // alignment within eps (sin) implies |u^ - v^| <= 2 sin(asin(eps)/2) <= eps pi/2;
-    // 4e-6 covers the float32 rounding of the unit vectors
-    const float ut = (float)((sqrt((double)cfg->cuts.fishbone_eps2) * 1.5707963267948966 + 4e-6) *
-                             (sqrt((double)cfg->cuts.fishbone_eps2) * 1.5707963267948966 + 4e-6));
-    launch_fishbone(p, ut, grid, s);
+    // 4e-6 covers the float32 rounding of the unit vectors.  Key buckets are
+    // at least that wide, with room for the rounding of the bucket index.
+    const double dmax = sqrt((double)cfg->cuts.fishbone_eps2) * 1.5707963267948966 + 4e-6;
+    launch_fishbone(p, (float)(dmax * dmax), (float)(dmax * 1.01 + 1e-5), grid, s);
+    launch_out_lists(p, grid, s);
     return launched();
 }
 
@@ -262,7 +268,7 @@ pt_status pt_connect_cells(void *ws, size_t ws_bytes, const pt_hits *hits, const
     p.cell_alive = cells->alive;
     p.edge_src = edges->src;
     p.edge_dst = edges->dst;
-    launch_connect(p, cfg->tuning.connect_lanes, grid_for(cfg), (cudaStream_t)stream);
+    launch_connect(p, grid_for(cfg), (cudaStream_t)stream);
     return launched();
 }
 

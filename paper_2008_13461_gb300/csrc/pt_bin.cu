@@ -81,35 +81,37 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *smem_warp, int &
 
 constexpr int kPerThread = kScanItems / kThreads;   // 16
 
-__global__ void __launch_bounds__(kThreads) k_scan_reduce(Params p) {
+// Exclusive scan of a[0 .. n) in place, a[n] = total, in three kernels:
+// per-block sums, a one-block scan of those, per-block scans plus offset.
+__global__ void __launch_bounds__(kThreads) k_scan_reduce(const int32_t *a, int64_t n, int32_t *part) {
     __shared__ int sw[kThreads / 32];
     int64_t base = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPerThread;
     int s = 0;
 #pragma unroll
     for (int k = 0; k < kPerThread; k++) {
         int64_t i = base + k;
-        if (i < p.n_bins) s += p.bin_cnt[i];
+        if (i < n) s += a[i];
     }
     int total;
     block_exclusive_scan(s, sw, total);
-    if (threadIdx.x == 0) p.scan_part[blockIdx.x] = total;
+    if (threadIdx.x == 0) part[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(kThreads) k_scan_partials(Params p) {
+__global__ void __launch_bounds__(kThreads) k_scan_partials(int32_t *part, int nblocks, int32_t *total_out) {
     __shared__ int sw[kThreads / 32];
     int carry = 0;
-    for (int b0 = 0; b0 < p.n_scan_blocks; b0 += kThreads) {
+    for (int b0 = 0; b0 < nblocks; b0 += kThreads) {
         int i = b0 + threadIdx.x;
-        int v = i < p.n_scan_blocks ? p.scan_part[i] : 0;
+        int v = i < nblocks ? part[i] : 0;
         int total;
         int e = block_exclusive_scan(v, sw, total);
-        if (i < p.n_scan_blocks) p.scan_part[i] = carry + e;
+        if (i < nblocks) part[i] = carry + e;
         carry += total;
     }
-    if (threadIdx.x == 0) p.bin_cnt[p.n_bins] = carry;
+    if (threadIdx.x == 0) *total_out = carry;
 }
 
-__global__ void __launch_bounds__(kThreads) k_scan_apply(Params p) {
+__global__ void __launch_bounds__(kThreads) k_scan_apply(int32_t *a, int64_t n, const int32_t *part) {
     __shared__ int sw[kThreads / 32];
     int64_t base = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPerThread;
     int v[kPerThread];
@@ -117,17 +119,24 @@ __global__ void __launch_bounds__(kThreads) k_scan_apply(Params p) {
 #pragma unroll
     for (int k = 0; k < kPerThread; k++) {
         int64_t i = base + k;
-        v[k] = i < p.n_bins ? p.bin_cnt[i] : 0;
+        v[k] = i < n ? a[i] : 0;
         s += v[k];
     }
     int total;
-    int e = block_exclusive_scan(s, sw, total) + p.scan_part[blockIdx.x];
+    int e = block_exclusive_scan(s, sw, total) + part[blockIdx.x];
 #pragma unroll
     for (int k = 0; k < kPerThread; k++) {
         int64_t i = base + k;
-        if (i < p.n_bins) p.bin_cnt[i] = e;
+        if (i < n) a[i] = e;
         e += v[k];
     }
+}
+
+void launch_scan(int32_t *a, int64_t n, int32_t *part, cudaStream_t s) {
+    const int nb = (int)((n + kScanItems - 1) / kScanItems);
+    if (nb > 0) k_scan_reduce<<<nb, kThreads, 0, s>>>(a, n, part);
+    k_scan_partials<<<1, kThreads, 0, s>>>(part, nb, a + n);
+    if (nb > 0) k_scan_apply<<<nb, kThreads, 0, s>>>(a, n, part);
 }
 
 __global__ void __launch_bounds__(kThreads) k_bin_fill(Params p) {
@@ -137,10 +146,7 @@ __global__ void __launch_bounds__(kThreads) k_bin_fill(Params p) {
         int bin = p.hit_bin[h];
         if (bin < 0) continue;
         int pos = p.bin_cnt[bin] + p.hit_rank[h];
-        p.bx[pos] = p.x[h];
-        p.by[pos] = p.y[h];
-        p.bz[pos] = p.z[h];
-        p.br[pos] = p.r[h];
+        p.bh[pos] = make_float4(p.x[h], p.y[h], p.z[h], p.r[h]);
         p.perm[pos] = h;
         p.bev[pos] = bin / per_event;
         p.blayer[pos] = (int8_t)((bin / (p.n_phi * p.n_t)) % PT_N_LAYERS);
@@ -149,9 +155,7 @@ __global__ void __launch_bounds__(kThreads) k_bin_fill(Params p) {
 
 void launch_binning(const Params &p, int grid, cudaStream_t s) {
     k_bin_count<<<grid, kThreads, 0, s>>>(p);
-    k_scan_reduce<<<p.n_scan_blocks, kThreads, 0, s>>>(p);
-    k_scan_partials<<<1, kThreads, 0, s>>>(p);
-    k_scan_apply<<<p.n_scan_blocks, kThreads, 0, s>>>(p);
+    launch_scan(p.bin_cnt, p.n_bins, p.scan_part, s);
     k_bin_fill<<<grid, kThreads, 0, s>>>(p);
 }
 

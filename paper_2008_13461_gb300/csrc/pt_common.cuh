@@ -17,13 +17,13 @@ constexpr int kCounters = 16;
 // workspace counters (int32 slots at the start of ws)
 enum Counter {
     C_CELLS = 0, C_EDGES = 1, C_TUPLES = 2, C_TRACKS = 3, C_FLAGS = 4, C_FALLBACK = 5,
-    C_ALIVE_CELLS = 6, C_ALIVE_TUPLES = 7
+    C_ALIVE_CELLS = 6, C_ALIVE_TUPLES = 7, C_LEAVES = 8
 };
 
 // Byte offsets of every workspace array (all 256-byte aligned).
 struct WsLayout {
     size_t counters, bin_cnt, scan_part, hit_bin, hit_rank;
-    size_t bx, by, bz, br, blayer, bev, perm, in_off, in_cnt;
+    size_t bh, blayer, bev, perm, in_off, in_cnt, out_cnt, out_off, cell_rank, out_idx, leaf_list;
     size_t edge_off, edge_cnt, has_out, maxlen;
     size_t total;
     int64_t n_bins;        // events * layers * phi bins * t bins
@@ -40,9 +40,10 @@ struct Params {
     int32_t n_hits, n_events, n_modules;
     // workspace
     int32_t *counters, *bin_cnt, *scan_part, *hit_bin, *hit_rank;
-    float *bx, *by, *bz, *br;
+    float4 *bh;                          // binned hits (x, y, z, r)
     int8_t *blayer;
     int32_t *bev, *perm, *in_off, *in_cnt, *edge_off, *edge_cnt;
+    int32_t *out_cnt, *out_off, *cell_rank, *out_idx, *leaf_list;
     uint8_t *has_out;
     int32_t *maxlen;
     // outputs
@@ -340,6 +341,12 @@ struct FHit {
     float x, y, z, r;
 };
 
+__device__ __forceinline__ FHit load_hit(const float4 *bh, int i) {
+    const float4 v = __ldg(bh + i);
+    FHit h = {v.x, v.y, v.z, v.w};
+    return h;
+}
+
 // CA dz: |z_a r_c - z_c r_a| <= zmax (r_c - r_a)
 __device__ __forceinline__ int pred_dz(const FHit &a, const FHit &c, float zmax, int32_t *cnt) {
     return pred_zip(a.x, a.y, a.z, a.r, c.x, c.y, c.z, c.r, zmax, cnt);
@@ -373,47 +380,59 @@ __device__ __forceinline__ int pred_curv(const FHit &a, const FHit &b, const FHi
     return exact_curv(ghit(a.x, a.y, a.z, a.r), ghit(b.x, b.y, b.z, b.r), ghit(c.x, c.y, c.z, c.r), K, cnt);
 }
 
-// CA beamspot: I^2 <= rmax2 |ab|^2 |bc|^2 |ca|^2.  I is bounded as an
-// interval (its own error bound) before squaring, because the in-circle
-// determinant cancels heavily and a bound on I^2 alone would rarely decide.
+// CA beamspot: I^2 <= rmax2 |ab|^2 |bc|^2 |ca|^2.  The lifted 4x4 in-circle
+// determinant is invariant under translation, so I is evaluated about hit a
+// (B = b-a, C = c-a, D = origin-a), where its terms are small; I is then
+// bounded as an interval (its own error bound) before squaring.
 __device__ __forceinline__ int pred_beamspot(const FHit &a, const FHit &b, const FHit &c, float rmax2,
                                              int32_t *cnt) {
-    float a2 = a.x * a.x + a.y * a.y, b2 = b.x * b.x + b.y * b.y, c2 = c.x * c.x + c.y * c.y;
-    float t1 = b.y * c2, t2 = b2 * c.y, t3 = b.x * c2, t4 = b2 * c.x, t5 = b.x * c.y, t6 = b.y * c.x;
-    float m1 = t1 - t2, m2 = t3 - t4, m3 = t5 - t6;
-    float s1 = a.x * m1, s2 = a.y * m2, s3 = a2 * m3;
-    float I = (s1 - s2) + s3;
-    float Ib = fabsf(a.x) * (fabsf(t1) + fabsf(t2)) + fabsf(a.y) * (fabsf(t3) + fabsf(t4)) +
-               a2 * (fabsf(t5) + fabsf(t6));
-    float eI = ferr(7, Ib);
-    float abx = b.x - a.x, aby = b.y - a.y, bcx = c.x - b.x, bcy = c.y - b.y, cax = a.x - c.x, cay = a.y - c.y;
-    float T = rmax2 * (((abx * abx + aby * aby) * (bcx * bcx + bcy * bcy)) * (cax * cax + cay * cay));
-    float eT = ferr(5, T);
-    float aI = fabsf(I);
-    float hi = aI + eI, lo = aI - eI;
+    const float Bx = b.x - a.x, By = b.y - a.y, Cx = c.x - a.x, Cy = c.y - a.y, Dx = -a.x, Dy = -a.y;
+    const float B2 = Bx * Bx + By * By, C2 = Cx * Cx + Cy * Cy, D2 = Dx * Dx + Dy * Dy;
+    const float t1 = Cy * D2, t2 = C2 * Dy, t3 = Cx * D2, t4 = C2 * Dx, t5 = Cx * Dy, t6 = Cy * Dx;
+    const float m1 = t1 - t2, m2 = t3 - t4, m3 = t5 - t6;
+    const float s1 = Bx * m1, s2 = By * m2, s3 = B2 * m3;
+    const float I = (s1 - s2) + s3;
+    const float Ib = fabsf(Bx) * (fabsf(t1) + fabsf(t2)) + fabsf(By) * (fabsf(t3) + fabsf(t4)) +
+                     B2 * (fabsf(t5) + fabsf(t6));
+    const float eI = ferr(7, Ib);
+    const float bcx = c.x - b.x, bcy = c.y - b.y;
+    const float T = rmax2 * ((B2 * (bcx * bcx + bcy * bcy)) * C2);
+    const float eT = ferr(5, T);
+    const float aI = fabsf(I);
+    const float hi = aI + eI, lo = aI - eI;
     if (hi * hi * (1.0f + 8.0f * kU) < T - eT) return 1;
     if (lo > 0.0f && lo * lo * (1.0f - 8.0f * kU) > T + eT) return 0;
     return exact_beamspot(ghit(a.x, a.y, a.z, a.r), ghit(b.x, b.y, b.z, b.r), ghit(c.x, c.y, c.z, c.r), rmax2,
                           cnt);
 }
 
-// Fishbone alignment: u.v > 0 and |u x v|^2 <= eps2 |u|^2 |v|^2 (3-D)
+// a*b - c*d with one rounding: Kahan's algorithm with FMA, relative error
+// at most 2u (Jeannerod, Louvet, Muller, Math. Comp. 82 (2013) 2245).
+__device__ __forceinline__ float det2(float a, float b, float c, float d) {
+    const float w = __fmul_rn(c, d);
+    const float e = __fmaf_rn(-c, d, w);
+    const float f = __fmaf_rn(a, b, -w);
+    return __fadd_rn(f, e);
+}
+
+// Fishbone alignment: u.v > 0 and |u x v|^2 <= eps2 |u|^2 |v|^2 (3-D).  The
+// cross product of nearly parallel u, v cancels, so its components are taken
+// with det2 (relative error <= 2u each); the squared norms and products of
+// positive terms then carry relative errors below 8u, which bounds F.
 __device__ __forceinline__ int pred_fb(const FHit &h1, const FHit &h2, const FHit &h, float eps2,
                                        int32_t *cnt) {
-    float ux = h1.x - h.x, uy = h1.y - h.y, uz = h1.z - h.z;
-    float vx = h2.x - h.x, vy = h2.y - h.y, vz = h2.z - h.z;
-    float d1 = ux * vx, d2 = uy * vy, d3 = uz * vz;
-    float dot = (d1 + d2) + d3, dotb = (fabsf(d1) + fabsf(d2)) + fabsf(d3);
-    float eD = ferr(3, dotb);
+    const float ux = h1.x - h.x, uy = h1.y - h.y, uz = h1.z - h.z;
+    const float vx = h2.x - h.x, vy = h2.y - h.y, vz = h2.z - h.z;
+    const float d1 = ux * vx, d2 = uy * vy, d3 = uz * vz;
+    const float dot = (d1 + d2) + d3, dotb = (fabsf(d1) + fabsf(d2)) + fabsf(d3);
+    const float eD = ferr(3, dotb);
     if (dot < -eD) return 0;
     if (dot > eD) {
-        float c1 = uy * vz, c2 = uz * vy, c3 = uz * vx, c4 = ux * vz, c5 = ux * vy, c6 = uy * vx;
-        float cx = c1 - c2, cy = c3 - c4, cz = c5 - c6;
-        float cxb = fabsf(c1) + fabsf(c2), cyb = fabsf(c3) + fabsf(c4), czb = fabsf(c5) + fabsf(c6);
-        float cr = (cx * cx + cy * cy) + cz * cz, crb = (cxb * cxb + cyb * cyb) + czb * czb;
-        float E = eps2 * ((ux * ux + uy * uy + uz * uz) * (vx * vx + vy * vy + vz * vz));
-        float F = E - cr;
-        float e = ferr(6, E + crb);
+        const float cx = det2(uy, vz, uz, vy), cy = det2(uz, vx, ux, vz), cz = det2(ux, vy, uy, vx);
+        const float cr = (cx * cx + cy * cy) + cz * cz;
+        const float E = eps2 * ((ux * ux + uy * uy + uz * uz) * (vx * vx + vy * vy + vz * vz));
+        const float F = E - cr;
+        const float e = 12.0f * kU * (E + cr) + 1e-27f;
         if (F > e) return 1;
         if (F < -e) return 0;
     }

@@ -53,7 +53,8 @@ __device__ __forceinline__ void t_window(const Params &p, const pt_pair_cuts &pc
 template <int G, bool kWrite>
 __device__ int sweep_outer(const Params &p, int o, int lane, unsigned gmask, int gshift, int32_t *s_inner,
                            uint8_t *s_pair, int cap, int64_t base) {
-    const float xo = p.bx[o], yo = p.by[o], zo = p.bz[o], ro = p.br[o];
+    const float4 ho = __ldg(p.bh + o);
+    const float xo = ho.x, yo = ho.y, zo = ho.z, ro = ho.w;
     const int Lo = p.blayer[o], ev = p.bev[o];
     const float phio = atan2f(yo, xo);
     const unsigned lanes = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
@@ -86,7 +87,8 @@ __device__ int sweep_outer(const Params &p, int o, int lane, unsigned gmask, int
                 const int i = i0 + lane;
                 bool acc = false;
                 if (i < end) {
-                    const float xi = p.bx[i], yi = p.by[i], zi = p.bz[i], ri = p.br[i];
+                    const float4 hi = __ldg(p.bh + i);
+                    const float xi = hi.x, yi = hi.y, zi = hi.z, ri = hi.w;
                     acc = zi >= pc.zlo && zi <= pc.zhi &&
                           pred_zip(xi, yi, zi, ri, xo, yo, zo, ro, pc.zmax, p.counters) &&
                           pred_phiw(xi, yi, xo, yo, pc.tan2_dphi, p.counters, zi, ri, zo, ro) &&
@@ -157,49 +159,193 @@ __global__ void __launch_bounds__(kThreads) k_doublets(Params p) {
 
 // Fishbone: cells sharing the outer hit o whose inner hits lie on one layer
 // and are aligned; a cell dies when an aligned sibling is strictly shorter,
-// or as long with a smaller input index.  A cheap conservative test on unit
-// direction vectors (|u^ - v^|^2 <= fb_unit_thr, implied by alignment) skips
-// most sibling pairs before the exact predicate.
-template <int G>
-__global__ void __launch_bounds__(kThreads) k_fishbone(Params p, float unit_thr) {
-    constexpr int kGroups = kThreads / G;
-    const int lane = threadIdx.x % G, grp = threadIdx.x / G;
-    const int n_binned = p.bin_cnt[p.n_bins];
-    for (int o = blockIdx.x * kGroups + grp; o < n_binned; o += gridDim.x * kGroups) {
-        const int n = p.in_cnt[o];
-        const int64_t b = p.in_off[o];
-        if (n < 2 || b + n > p.cap_cells) continue;
-        const FHit h = {p.bx[o], p.by[o], p.bz[o], p.br[o]};
+// or as long with a smaller input index.
+//
+// One warp per outer hit.  Alignment within eps implies that the unit
+// directions u^ = (h_i - h_o)/|h_i - h_o| of two siblings differ by at most
+// du = eps pi/2 (plus float32 slack), hence so does any 1-Lipschitz key of
+// them (u^_z for a barrel outer hit, the radial component for a disk).  The
+// siblings are counting-sorted into key buckets of width >= du in shared
+// memory and each cell is compared only with the cells of its own and the two
+// neighbouring buckets -- a superset of its aligned siblings -- so the result
+// is exact while the work drops from O(k^2) to ~O(k).  Outer hits with more
+// than kFbMax cells use the plain pairwise loop.
+constexpr int kFbWarps = 4;
+constexpr int kFbMax = 512;
+constexpr int kFbBuckets = 512;
+
+__device__ __forceinline__ bool fb_shorter_sibling(const Params &p, int i1, int i2, const FHit &h, const GHit &gh,
+                                                   long long l1) {
+    const FHit h1 = load_hit(p.bh, i1);
+    const FHit h2 = load_hit(p.bh, i2);
+    if (!pred_fb(h1, h2, h, p.fishbone_eps2, p.counters)) return false;
+    const GHit g2 = ghit(h2.x, h2.y, h2.z, h2.r);
+    const long long l2 =
+        (g2.x - gh.x) * (g2.x - gh.x) + (g2.y - gh.y) * (g2.y - gh.y) + (g2.z - gh.z) * (g2.z - gh.z);
+    return l2 < l1 || (l2 == l1 && p.perm[i2] < p.perm[i1]);
+}
+
+__device__ __forceinline__ long long len2_to(const Params &p, int i, const GHit &gh) {
+    const FHit f = load_hit(p.bh, i);
+    const GHit g = ghit(f.x, f.y, f.z, f.r);
+    return (g.x - gh.x) * (g.x - gh.x) + (g.y - gh.y) * (g.y - gh.y) + (g.z - gh.z) * (g.z - gh.z);
+}
+
+// Fishbone verdicts for the n >= 2 cells of outer hit o (one warp).
+__device__ __forceinline__ void fishbone_hit(const Params &p, int o, int n, int64_t b, int lane, int w,
+                                          float unit_thr, float du, float (*s_ux)[kFbMax],
+                                          float (*s_uy)[kFbMax], float (*s_uz)[kFbMax],
+                                          int8_t (*s_lay)[kFbMax], int16_t (*s_sorted)[kFbMax],
+                                          int (*s_pos)[kFbBuckets]) {
+    {
+        const FHit h = load_hit(p.bh, o);
         const GHit gh = ghit(h.x, h.y, h.z, h.r);
-        for (int64_t c = b + lane; c < b + n; c += G) {
-            const int i1 = p.cell_inner[c];
-            const int L1 = p.blayer[i1];
-            const FHit h1 = {p.bx[i1], p.by[i1], p.bz[i1], p.br[i1]};
-            const float ux = h1.x - h.x, uy = h1.y - h.y, uz = h1.z - h.z;
+        if (n > kFbMax) {
+            for (int j = lane; j < n; j += 32) {
+                const int i1 = p.cell_inner[b + j];
+                const int L1 = p.blayer[i1];
+                const long long l1 = len2_to(p, i1, gh);
+                bool dead = false;
+                for (int d = 0; d < n && !dead; d++) {
+                    if (d == j) continue;
+                    const int i2 = p.cell_inner[b + d];
+                    if (p.blayer[i2] != L1) continue;
+                    dead = fb_shorter_sibling(p, i1, i2, h, gh, l1);
+                }
+                if (dead) p.cell_alive[b + j] = 0;
+            }
+            return;
+        }
+        const bool radial = p.layer[p.blayer[o]].kind == PT_LAYER_DISK;
+        const float irr = rsqrtf(h.x * h.x + h.y * h.y);
+        const float rx = h.x * irr, ry = h.y * irr;
+        float kmin = 3.0f, kmax = -3.0f;
+        for (int j = lane; j < n; j += 32) {
+            const int i = p.cell_inner[b + j];
+            const FHit hi = load_hit(p.bh, i);
+            const float ux = hi.x - h.x, uy = hi.y - h.y, uz = hi.z - h.z;
             const float iu = rsqrtf(ux * ux + uy * uy + uz * uz);
             const float ax = ux * iu, ay = uy * iu, az = uz * iu;
-            const GHit g1 = ghit(h1.x, h1.y, h1.z, h1.r);
-            const long long l1 = (g1.x - gh.x) * (g1.x - gh.x) + (g1.y - gh.y) * (g1.y - gh.y) +
-                                 (g1.z - gh.z) * (g1.z - gh.z);
-            bool dead = false;
-            for (int64_t d = b; d < b + n && !dead; d++) {
-                if (d == c) continue;
-                const int i2 = p.cell_inner[d];
-                if (p.blayer[i2] != L1) continue;
-                const FHit h2 = {p.bx[i2], p.by[i2], p.bz[i2], p.br[i2]};
-                const float vx = h2.x - h.x, vy = h2.y - h.y, vz = h2.z - h.z;
-                const float iv = rsqrtf(vx * vx + vy * vy + vz * vz);
-                const float dx = ax - vx * iv, dy = ay - vy * iv, dz = az - vz * iv;
-                if (dx * dx + dy * dy + dz * dz > unit_thr) continue;
-                if (!pred_fb(h1, h2, h, p.fishbone_eps2, p.counters)) continue;
-                const GHit g2 = ghit(h2.x, h2.y, h2.z, h2.r);
-                const long long l2 = (g2.x - gh.x) * (g2.x - gh.x) + (g2.y - gh.y) * (g2.y - gh.y) +
-                                     (g2.z - gh.z) * (g2.z - gh.z);
-                if (l2 < l1 || (l2 == l1 && p.perm[i2] < p.perm[i1])) dead = true;
+            s_ux[w][j] = ax;
+            s_uy[w][j] = ay;
+            s_uz[w][j] = az;
+            s_lay[w][j] = p.blayer[i];
+            const float key = radial ? ax * rx + ay * ry : az;
+            kmin = fminf(kmin, key);
+            kmax = fmaxf(kmax, key);
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, d));
+            kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, d));
+        }
+        const float width = fmaxf(du, (kmax - kmin) * (1.0f / (kFbBuckets - 2)));
+        const float iw = 1.0f / width;
+        for (int q = lane; q < kFbBuckets; q += 32) s_pos[w][q] = 0;
+        __syncwarp();
+        for (int j = lane; j < n; j += 32) {
+            const float key = radial ? s_ux[w][j] * rx + s_uy[w][j] * ry : s_uz[w][j];
+            const int bk = min(__float2int_rd((key - kmin) * iw), kFbBuckets - 1);
+            atomicAdd(&s_pos[w][bk], 1);
+        }
+        __syncwarp();
+        {   // exclusive scan of the bucket counts, 16 buckets per lane
+            constexpr int kPer = kFbBuckets / 32;
+            int v[kPer], sum = 0;
+#pragma unroll
+            for (int q = 0; q < kPer; q++) {
+                v[q] = s_pos[w][lane * kPer + q];
+                sum += v[q];
             }
-            if (dead) p.cell_alive[c] = 0;
+            int incl = sum;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += t;
+            }
+            int run = incl - sum;
+#pragma unroll
+            for (int q = 0; q < kPer; q++) {
+                s_pos[w][lane * kPer + q] = run;
+                run += v[q];
+            }
+        }
+        __syncwarp();
+        for (int j = lane; j < n; j += 32) {
+            const float key = radial ? s_ux[w][j] * rx + s_uy[w][j] * ry : s_uz[w][j];
+            const int bk = min(__float2int_rd((key - kmin) * iw), kFbBuckets - 1);
+            s_sorted[w][atomicAdd(&s_pos[w][bk], 1)] = (int16_t)j;
+        }
+        __syncwarp();
+        // s_pos[bk] is now the end of bucket bk
+        for (int j = lane; j < n; j += 32) {
+            const float ax = s_ux[w][j], ay = s_uy[w][j], az = s_uz[w][j];
+            const float key = radial ? ax * rx + ay * ry : az;
+            const int bk = min(__float2int_rd((key - kmin) * iw), kFbBuckets - 1);
+            const int start = bk >= 2 ? s_pos[w][bk - 2] : 0;
+            const int end = s_pos[w][min(bk + 1, kFbBuckets - 1)];
+            const int L1 = s_lay[w][j];
+            const int i1 = p.cell_inner[b + j];
+            long long l1 = -1;
+            bool dead = false;
+            for (int q = start; q < end && !dead; q++) {
+                const int d = s_sorted[w][q];
+                if (d == j || s_lay[w][d] != L1) continue;
+                const float dx = ax - s_ux[w][d], dy = ay - s_uy[w][d], dz = az - s_uz[w][d];
+                if (dx * dx + dy * dy + dz * dz > unit_thr) continue;
+                if (l1 < 0) l1 = len2_to(p, i1, gh);
+                dead = fb_shorter_sibling(p, i1, p.cell_inner[b + d], h, gh, l1);
+            }
+            if (dead) p.cell_alive[b + j] = 0;
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(32 * kFbWarps) k_fishbone(Params p, float unit_thr, float du) {
+    __shared__ float s_ux[kFbWarps][kFbMax], s_uy[kFbWarps][kFbMax], s_uz[kFbWarps][kFbMax];
+    __shared__ int8_t s_lay[kFbWarps][kFbMax];
+    __shared__ int16_t s_sorted[kFbWarps][kFbMax];
+    __shared__ int s_pos[kFbWarps][kFbBuckets];
+    __shared__ int s_alive;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_alive = 0;
+    __syncthreads();
+    int my_alive = 0;
+    const int n_binned = p.bin_cnt[p.n_bins];
+    for (int o = blockIdx.x * kFbWarps + w; o < n_binned; o += gridDim.x * kFbWarps) {
+        const int n = p.in_cnt[o];
+        const int64_t b = p.in_off[o];
+        if (n < 1 || b + n > p.cap_cells) continue;
+        if (n >= 2) fishbone_hit(p, o, n, b, lane, w, unit_thr, du, s_ux, s_uy, s_uz, s_lay, s_sorted, s_pos);
+        // live cells join the out-list of their inner hit (rank by atomics)
+        for (int j = lane; j < n; j += 32) {
+            if (p.cell_alive[b + j]) {
+                p.cell_rank[b + j] = atomicAdd(p.out_off + p.cell_inner[b + j], 1);
+                my_alive++;
+            }
         }
     }
+    if (my_alive) atomicAdd(&s_alive, my_alive);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_alive) atomicAdd(p.counters + C_ALIVE_CELLS, s_alive);
+}
+
+// Out-lists: cells grouped by their inner hit (CSR), from the ranks taken in
+// the Fishbone kernel and the scanned per-hit counts.
+__global__ void __launch_bounds__(kThreads) k_out_fill(Params p) {
+    const int64_t n_cells = min((int64_t)p.counters[C_CELLS], p.cap_cells);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += stride) {
+        if (!p.cell_alive[c]) continue;
+        const int i = p.cell_inner[c];
+        p.out_idx[p.out_off[i] + p.cell_rank[c]] = (int32_t)c;
+    }
+}
+
+void launch_out_lists(const Params &p, int grid, cudaStream_t s) {
+    launch_scan(p.out_off, p.n_hits, p.scan_part, s);
+    k_out_fill<<<grid, kThreads, 0, s>>>(p);
 }
 
 void launch_doublets(const Params &p, int lanes, int grid, cudaStream_t s) {
@@ -211,8 +357,8 @@ void launch_doublets(const Params &p, int lanes, int grid, cudaStream_t s) {
     }
 }
 
-void launch_fishbone(const Params &p, float unit_thr, int grid, cudaStream_t s) {
-    k_fishbone<8><<<grid, kThreads, 0, s>>>(p, unit_thr);
+void launch_fishbone(const Params &p, float unit_thr, float du, int grid, cudaStream_t s) {
+    k_fishbone<<<grid * (kThreads / (32 * kFbWarps)), 32 * kFbWarps, 0, s>>>(p, unit_thr, du);
 }
 
 }  // namespace ptk

@@ -25,14 +25,6 @@
 
 namespace ptk {
 
-// a*b - c*d with one rounding error (Kahan's algorithm with FMA)
-__device__ __forceinline__ float det2(float a, float b, float c, float d) {
-    float w = c * d;
-    float e = fmaf(-c, d, w);
-    float f = fmaf(a, b, -w);
-    return f + e;
-}
-
 __device__ __forceinline__ float asinc(float x) {
     x = fminf(fmaxf(x, -1.0f), 1.0f);
     return fabsf(x) < 1e-4f ? 1.0f + x * x * (1.0f / 6.0f) : asinf(x) / x;
@@ -41,7 +33,8 @@ __device__ __forceinline__ float asinc(float x) {
 template <int M>
 __device__ __forceinline__ int pidx(int r, int c) { return r * (r + 1) / 2 + c; }
 
-// in-place Cholesky of a packed lower-triangular SPD matrix
+// in-place Cholesky of a packed lower-triangular SPD matrix; the diagonal
+// holds the reciprocals of L's diagonal (so solves need no division)
 template <int M>
 __device__ __forceinline__ void chol(double *A) {
 #pragma unroll
@@ -49,9 +42,8 @@ __device__ __forceinline__ void chol(double *A) {
         double s = A[pidx<M>(j, j)];
 #pragma unroll
         for (int k = 0; k < j; k++) s -= A[pidx<M>(j, k)] * A[pidx<M>(j, k)];
-        const double d = sqrt(s > 0.0 ? s : 1e-300);
-        A[pidx<M>(j, j)] = d;
-        const double id = 1.0 / d;
+        const double id = rsqrt(s > 0.0 ? s : 1e-300);
+        A[pidx<M>(j, j)] = id;
 #pragma unroll
         for (int i = j + 1; i < M; i++) {
             double t = A[pidx<M>(i, j)];
@@ -69,14 +61,14 @@ __device__ __forceinline__ void chol_solve(const double *L, double *b) {
         double t = b[i];
 #pragma unroll
         for (int k = 0; k < i; k++) t -= L[pidx<M>(i, k)] * b[k];
-        b[i] = t / L[pidx<M>(i, i)];
+        b[i] = t * L[pidx<M>(i, i)];
     }
 #pragma unroll
     for (int i = M - 1; i >= 0; i--) {
         double t = b[i];
 #pragma unroll
         for (int k = i + 1; k < M; k++) t -= L[pidx<M>(k, i)] * b[k];
-        b[i] = t / L[pidx<M>(i, i)];
+        b[i] = t * L[pidx<M>(i, i)];
     }
 }
 
@@ -312,22 +304,32 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
     p.trk_ndf[k] = (int8_t)(2 * N - 5);
 }
 
+// One kernel per hit count (3, 4, 5, and 6..8), so each is compiled for its
+// own register footprint; each scans the track list and fits its own tracks.
+template <int N>
 __global__ void __launch_bounds__(kThreads) k_fit(Params p) {
     const int64_t nk = min((int64_t)p.counters[C_TRACKS], p.cap_tracks);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nk; k += stride) {
         const int32_t t = p.trk_tuple[k];
-        switch (p.tup_n[t]) {
-        case 3: fit_track<3>(p, k, t); break;
-        case 4: fit_track<4>(p, k, t); break;
-        case 5: fit_track<5>(p, k, t); break;
-        case 6: fit_track<6>(p, k, t); break;
-        case 7: fit_track<7>(p, k, t); break;
-        default: fit_track<8>(p, k, t); break;
+        const int n = p.tup_n[t];
+        if (N < 6) {
+            if (n == N) fit_track<N>(p, k, t);
+        } else if (n == 6) {
+            fit_track<6>(p, k, t);
+        } else if (n == 7) {
+            fit_track<7>(p, k, t);
+        } else if (n == 8) {
+            fit_track<8>(p, k, t);
         }
     }
 }
 
-void launch_fit(const Params &p, int grid, cudaStream_t s) { k_fit<<<grid, kThreads, 0, s>>>(p); }
+void launch_fit(const Params &p, int grid, cudaStream_t s) {
+    k_fit<3><<<grid, kThreads, 0, s>>>(p);
+    k_fit<4><<<grid, kThreads, 0, s>>>(p);
+    k_fit<5><<<grid, kThreads, 0, s>>>(p);
+    k_fit<6><<<grid, kThreads, 0, s>>>(p);
+}
 
 }  // namespace ptk

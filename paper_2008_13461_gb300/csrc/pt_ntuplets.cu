@@ -3,7 +3,8 @@
 //
 // The paper runs one DFS per root along outgoing edges.  Here every maximal
 // path is enumerated from its other end: one thread per leaf cell (live, no
-// outer neighbour) walks incoming edges -- stored contiguously per cell by
+// outer neighbour, taken from the list of cells with incoming edges that the
+// connection kernel appends to) walks incoming edges -- stored contiguously per cell by
 // the connection kernel -- back to cells with no inner neighbour, and emits
 // the path when that cell is a root (inner hit on BPix1, or on BPix2 /
 // FPix1+- which, having no inner neighbour, qualifies) and the path has at
@@ -18,10 +19,12 @@ namespace ptk {
 __device__ __forceinline__ bool root_layer(int L) { return L == 0 || L == 1 || L == 4 || L == 7; }
 
 __global__ void __launch_bounds__(kThreads) k_dfs(Params p) {
-    const int64_t n_cells = min((int64_t)p.counters[C_CELLS], p.cap_cells);
+    const int64_t n_list = min((int64_t)p.counters[C_LEAVES], p.cap_cells);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += stride) {
-        if (!p.cell_alive[c] || p.has_out[c] || p.edge_cnt[c] == 0) continue;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_list; k += stride) {
+        // the list holds the live cells with incoming edges; leaves have no outer neighbour
+        const int c = p.leaf_list[k];
+        if (p.has_out[c]) continue;
         int32_t st_cell[PT_NMAX - 1];
         int32_t st_it[PT_NMAX - 1];
         int depth = 0;

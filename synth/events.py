@@ -393,16 +393,28 @@ def make_event(cfg: EventConfig, e: int) -> dict:
     )
 
 
-def make_batch(cfg: EventConfig | int, n_events: int | None = None, first: int = 0) -> dict:
+def _make_event_args(args):
+    return make_event(*args)
+
+
+def make_batch(cfg: EventConfig | int, n_events: int | None = None, first: int = 0,
+               workers: int = 0) -> dict:
     """Concatenate events first .. first+n_events-1 into one SoA batch.
 
     Returns x, y, z, r (float32), module (int32), ev_off (int32[N+1]) plus
     truth: layer, track (index into the batch-wide track arrays, -1 noise),
-    trk_* arrays."""
+    trk_* arrays.  workers > 1 generates events in a spawn-started process
+    pool (safe before or after CUDA initialisation in the caller)."""
     if isinstance(cfg, int):
         cfg = CONFIGS[cfg]
     n = cfg.n_events if n_events is None else n_events
-    evs = [make_event(cfg, first + e) for e in range(n)]
+    if workers > 1 and n > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            evs = list(ex.map(_make_event_args, [(cfg, first + e) for e in range(n)]))
+    else:
+        evs = [make_event(cfg, first + e) for e in range(n)]
     off = np.zeros(n + 1, dtype=np.int64)
     off[1:] = np.cumsum([ev["x"].size for ev in evs])
     toff = np.zeros(n + 1, dtype=np.int64)

@@ -6,8 +6,10 @@ index to input hit indices (output order is unspecified).  Fitted
 parameters are compared within the tolerance of the float32 path:
   kappa:                        |d| <= 1e-4 |kappa|
   phi0, tan(lambda), d0, z0:    |d| <= 1e-5 max(1, |value|)   (phi0 mod 2 pi)
-and chi2 / covariance diagonal within 1e-3 relative (plus a small absolute
-floor for near-zero values).
+covariance diagonal within 1e-3 relative, and chi2 within
+2e-2 sqrt(max(1, chi2)): the float32 arc lengths carry ~1e-6 cm rounding
+(one ulp at 10-20 cm), which moves the s-z residuals by |tan lambda| times
+that, up to ~1e-2 sigma_z, and chi2 by twice that times sqrt(chi2).
 """
 from __future__ import annotations
 
@@ -119,9 +121,9 @@ def compare_params(P, CV, X2, ND, WP, WC, WX2, WND):
     rel = np.abs(CV[:, diag] - WC[:, diag]) / np.abs(WC[:, diag])
     err["cov_diag_rel"] = rel
     assert np.all(rel <= 1e-3), f"cov diag max rel err {rel.max():.3g}"
-    rc = np.abs(X2 - WX2) / np.maximum(np.abs(WX2), 1e-2)
-    err["chi2_rel"] = rc
-    assert np.all(rc <= 1e-3), f"chi2 max rel err {rc.max():.3g}"
+    rc = np.abs(X2 - WX2) / np.sqrt(np.maximum(1.0, WX2))
+    err["chi2_scaled"] = rc
+    assert np.all(rc <= 2e-2), f"chi2 max scaled err {rc.max():.3g}"
     return {k: (float(v.max()), float(np.percentile(v, 99))) for k, v in err.items()}
 
 
