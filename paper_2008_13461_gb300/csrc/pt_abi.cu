@@ -53,12 +53,13 @@ bool layout(const pt_hits *h, const pt_config *cfg, WsLayout &L) {
     L.perm = take(4 * nh);
     L.in_off = take(4 * nh);
     L.in_cnt = take(4 * nh);
+    L.hk = take(8 * nh);
     L.out_off = take(4 * (nh + 1));
     L.cell_rank = take(4 * nc);
     L.out_idx = take(4 * nc);
+    L.ck = take(4 * nc);
     L.leaf_list = take(4 * nc);
-    L.edge_off = take(4 * nc);
-    L.edge_cnt = take(4 * nc);
+    L.edge_rng = take(8 * nc);
     L.has_out = take(nc);
     L.maxlen = take(4 * nc);
     L.total = o;
@@ -167,12 +168,13 @@ Params make_params(void *ws, const WsLayout &L, const pt_hits *h, const pt_confi
     p.perm = (int32_t *)(w + L.perm);
     p.in_off = (int32_t *)(w + L.in_off);
     p.in_cnt = (int32_t *)(w + L.in_cnt);
+    p.hk = (float2 *)(w + L.hk);
     p.out_off = (int32_t *)(w + L.out_off);
     p.cell_rank = (int32_t *)(w + L.cell_rank);
     p.out_idx = (int32_t *)(w + L.out_idx);
+    p.ck = (float *)(w + L.ck);
     p.leaf_list = (int32_t *)(w + L.leaf_list);
-    p.edge_off = (int32_t *)(w + L.edge_off);
-    p.edge_cnt = (int32_t *)(w + L.edge_cnt);
+    p.edge_rng = (int2 *)(w + L.edge_rng);
     p.has_out = (uint8_t *)(w + L.has_out);
     p.maxlen = (int32_t *)(w + L.maxlen);
     p.cap_cells = cfg->capacity.cells;
@@ -196,6 +198,8 @@ Params make_params(void *ws, const WsLayout &L, const pt_hits *h, const pt_confi
     }
     p.region[0] = c.region[0];
     p.region[1] = c.region[1];
+    for (int r = 0; r < 2; r++)   // tolerance as a distance, rounded up
+        p.region_tol[r] = (float)(sqrt((double)c.region[r].tol_rz2) * (1.0 + 1e-6));
     p.fishbone_eps2 = c.fishbone_eps2;
     p.min_hits = c.min_hits;
     p.fit = cfg->fit;
@@ -291,6 +295,10 @@ pt_status pt_find_ntuplets(void *ws, size_t ws_bytes, const pt_hits *hits, const
     p.tup_cells = tuples->cells;
     p.tup_n = tuples->n;
     p.tup_alive = tuples->alive;
+    if (cfg->capacity.cells > 0 &&
+        cudaMemsetAsync(p.maxlen, 0, sizeof(int32_t) * (size_t)cfg->capacity.cells, (cudaStream_t)stream) !=
+            cudaSuccess)
+        return PT_ERR_CUDA;
     launch_ntuplets(p, grid_for(cfg), (cudaStream_t)stream);
     return launched();
 }

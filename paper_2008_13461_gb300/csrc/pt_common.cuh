@@ -23,8 +23,8 @@ enum Counter {
 // Byte offsets of every workspace array (all 256-byte aligned).
 struct WsLayout {
     size_t counters, bin_cnt, scan_part, hit_bin, hit_rank;
-    size_t bh, blayer, bev, perm, in_off, in_cnt, out_cnt, out_off, cell_rank, out_idx, leaf_list;
-    size_t edge_off, edge_cnt, has_out, maxlen;
+    size_t bh, blayer, bev, perm, in_off, in_cnt, hk, ck, leaf_list, out_off, cell_rank, out_idx;
+    size_t edge_rng, has_out, maxlen;
     size_t total;
     int64_t n_bins;        // events * layers * phi bins * t bins
     int32_t n_scan_blocks;
@@ -42,8 +42,12 @@ struct Params {
     int32_t *counters, *bin_cnt, *scan_part, *hit_bin, *hit_rank;
     float4 *bh;                          // binned hits (x, y, z, r)
     int8_t *blayer;
-    int32_t *bev, *perm, *in_off, *in_cnt, *edge_off, *edge_cnt;
-    int32_t *out_cnt, *out_off, *cell_rank, *out_idx, *leaf_list;
+    int32_t *bev, *perm, *in_off, *in_cnt;
+    int2 *edge_rng;                      // per out-list position: (first edge, count)
+    int32_t *leaf_list;
+    int32_t *out_off, *cell_rank, *out_idx;  // live cells grouped by inner hit (CSR)
+    float *ck;                           // R-z slope key of each cell w.r.t. its outer hit (NaN: dead)
+    float2 *hk;                          // per hit: max sqrt(1+key^2), min gap of its incoming cells
     uint8_t *has_out;
     int32_t *maxlen;
     // outputs
@@ -69,6 +73,7 @@ struct Params {
     int8_t pairs_by_outer[PT_N_LAYERS][kMaxPairsPerLayer];
     int32_t n_pairs_by_outer[PT_N_LAYERS];
     pt_ca_cuts region[2];
+    float region_tol[2];                 // sqrt(tol_rz2) rounded up
     float fishbone_eps2;
     int32_t min_hits;
     pt_fit_params fit;

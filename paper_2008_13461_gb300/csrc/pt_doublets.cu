@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(kThreads) k_doublets(Params p) {
 constexpr int kFbWarps = 4;
 constexpr int kFbMax = 512;
 constexpr int kFbBuckets = 512;
+constexpr int kFbDirect = 12;      // below this many siblings compare all pairs
 
 __device__ __forceinline__ bool fb_shorter_sibling(const Params &p, int i1, int i2, const FHit &h, const GHit &gh,
                                                    long long l1) {
@@ -234,29 +235,48 @@ __device__ __forceinline__ void fishbone_hit(const Params &p, int o, int n, int6
             kmin = fminf(kmin, key);
             kmax = fmaxf(kmax, key);
         }
+        __syncwarp();
+        if (n <= kFbDirect) {
+            // few siblings: compare every pair directly
+            for (int j = lane; j < n; j += 32) {
+                const float ax = s_ux[w][j], ay = s_uy[w][j], az = s_uz[w][j];
+                const int L1 = s_lay[w][j];
+                const int i1 = p.cell_inner[b + j];
+                long long l1 = -1;
+                bool dead = false;
+                for (int d = 0; d < n && !dead; d++) {
+                    if (d == j || s_lay[w][d] != L1) continue;
+                    const float dx = ax - s_ux[w][d], dy = ay - s_uy[w][d], dz = az - s_uz[w][d];
+                    if (dx * dx + dy * dy + dz * dz > unit_thr) continue;
+                    if (l1 < 0) l1 = len2_to(p, i1, gh);
+                    dead = fb_shorter_sibling(p, i1, p.cell_inner[b + d], h, gh, l1);
+                }
+                if (dead) p.cell_alive[b + j] = 0;
+            }
+            __syncwarp();
+            return;
+        }
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) {
             kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, d));
             kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, d));
         }
-        const float width = fmaxf(du, (kmax - kmin) * (1.0f / (kFbBuckets - 2)));
+        // as many buckets as about twice the cells (a power of two, 32 .. max)
+        const int nb = min(kFbBuckets, max(32, 1 << (32 - __clz(2 * n - 1))));
+        const float width = fmaxf(du, (kmax - kmin) / (float)(nb - 2));
         const float iw = 1.0f / width;
-        for (int q = lane; q < kFbBuckets; q += 32) s_pos[w][q] = 0;
+        for (int q = lane; q < nb; q += 32) s_pos[w][q] = 0;
         __syncwarp();
         for (int j = lane; j < n; j += 32) {
             const float key = radial ? s_ux[w][j] * rx + s_uy[w][j] * ry : s_uz[w][j];
-            const int bk = min(__float2int_rd((key - kmin) * iw), kFbBuckets - 1);
+            const int bk = min(__float2int_rd((key - kmin) * iw), nb - 1);
             atomicAdd(&s_pos[w][bk], 1);
         }
         __syncwarp();
-        {   // exclusive scan of the bucket counts, 16 buckets per lane
-            constexpr int kPer = kFbBuckets / 32;
-            int v[kPer], sum = 0;
-#pragma unroll
-            for (int q = 0; q < kPer; q++) {
-                v[q] = s_pos[w][lane * kPer + q];
-                sum += v[q];
-            }
+        {   // exclusive scan of the bucket counts, nb / 32 buckets per lane
+            const int per = nb >> 5;
+            int sum = 0;
+            for (int q = 0; q < per; q++) sum += s_pos[w][lane * per + q];
             int incl = sum;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
@@ -264,16 +284,16 @@ __device__ __forceinline__ void fishbone_hit(const Params &p, int o, int n, int6
                 if (lane >= d) incl += t;
             }
             int run = incl - sum;
-#pragma unroll
-            for (int q = 0; q < kPer; q++) {
-                s_pos[w][lane * kPer + q] = run;
-                run += v[q];
+            for (int q = 0; q < per; q++) {
+                const int v = s_pos[w][lane * per + q];
+                s_pos[w][lane * per + q] = run;
+                run += v;
             }
         }
         __syncwarp();
         for (int j = lane; j < n; j += 32) {
             const float key = radial ? s_ux[w][j] * rx + s_uy[w][j] * ry : s_uz[w][j];
-            const int bk = min(__float2int_rd((key - kmin) * iw), kFbBuckets - 1);
+            const int bk = min(__float2int_rd((key - kmin) * iw), nb - 1);
             s_sorted[w][atomicAdd(&s_pos[w][bk], 1)] = (int16_t)j;
         }
         __syncwarp();
@@ -281,9 +301,9 @@ __device__ __forceinline__ void fishbone_hit(const Params &p, int o, int n, int6
         for (int j = lane; j < n; j += 32) {
             const float ax = s_ux[w][j], ay = s_uy[w][j], az = s_uz[w][j];
             const float key = radial ? ax * rx + ay * ry : az;
-            const int bk = min(__float2int_rd((key - kmin) * iw), kFbBuckets - 1);
+            const int bk = min(__float2int_rd((key - kmin) * iw), nb - 1);
             const int start = bk >= 2 ? s_pos[w][bk - 2] : 0;
-            const int end = s_pos[w][min(bk + 1, kFbBuckets - 1)];
+            const int end = s_pos[w][min(bk + 1, nb - 1)];
             const int L1 = s_lay[w][j];
             const int i1 = p.cell_inner[b + j];
             long long l1 = -1;
@@ -318,21 +338,41 @@ __global__ void __launch_bounds__(32 * kFbWarps) k_fishbone(Params p, float unit
         const int64_t b = p.in_off[o];
         if (n < 1 || b + n > p.cap_cells) continue;
         if (n >= 2) fishbone_hit(p, o, n, b, lane, w, unit_thr, du, s_ux, s_uy, s_uz, s_lay, s_sorted, s_pos);
-        // live cells join the out-list of their inner hit (rank by atomics)
+        // R-z slope keys of the cells ending on o, for the CA connection:
+        // barrel o: (z_o - z_a)/(r_o - r_a); disk o: (r_o - r_a)/(z_o - z_a);
+        // NaN for dead cells.  Per hit: max sqrt(1 + key^2) and min gap.
+        const float4 ho = __ldg(p.bh + o);
+        const bool disk = p.layer[p.blayer[o]].kind == PT_LAYER_DISK;
+        float kmax = 0.f, gmin = 3.0e38f;
         for (int j = lane; j < n; j += 32) {
+            float key = __int_as_float(0x7fc00000);
             if (p.cell_alive[b + j]) {
-                p.cell_rank[b + j] = atomicAdd(p.out_off + p.cell_inner[b + j], 1);
+                const float4 ha = __ldg(p.bh + p.cell_inner[b + j]);
+                const float dr = ho.w - ha.w, dz = ho.z - ha.z;
+                const float num = disk ? dr : dz, den = disk ? dz : dr;
+                key = den != 0.f ? num / den : __int_as_float(0x7f800000);
+                kmax = fmaxf(kmax, sqrtf(1.0f + key * key));
+                gmin = fminf(gmin, fabsf(den));
                 my_alive++;
+                // join the out-list of the inner hit (rank by atomics)
+                p.cell_rank[b + j] = atomicAdd(p.out_off + p.cell_inner[b + j], 1);
             }
+            p.ck[b + j] = key;
         }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, d));
+            gmin = fminf(gmin, __shfl_xor_sync(0xffffffffu, gmin, d));
+        }
+        if (lane == 0) p.hk[o] = make_float2(kmax, gmin);
     }
     if (my_alive) atomicAdd(&s_alive, my_alive);
     __syncthreads();
     if (threadIdx.x == 0 && s_alive) atomicAdd(p.counters + C_ALIVE_CELLS, s_alive);
 }
 
-// Out-lists: cells grouped by their inner hit (CSR), from the ranks taken in
-// the Fishbone kernel and the scanned per-hit counts.
+// Out-lists: live cells grouped by their inner hit (CSR), from the ranks
+// taken in the Fishbone kernel and the scanned per-hit counts.
 __global__ void __launch_bounds__(kThreads) k_out_fill(Params p) {
     const int64_t n_cells = min((int64_t)p.counters[C_CELLS], p.cap_cells);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;

@@ -33,6 +33,21 @@ __device__ __forceinline__ float asinc(float x) {
 template <int M>
 __device__ __forceinline__ int pidx(int r, int c) { return r * (r + 1) / 2 + c; }
 
+// Double-precision 1/sqrt(s) and 1/d from a float32 seed and Newton steps
+// (each step squares the relative error: 1e-7 -> 1e-14 -> below 1e-16), to
+// keep the slow FP64 pipe to a few multiply-adds.
+__device__ __forceinline__ double rsqrt_fp64(double s) {
+    double y = (double)rsqrtf((float)s);
+    y = y * (1.5 - 0.5 * s * y * y);
+    return y * (1.5 - 0.5 * s * y * y);
+}
+
+__device__ __forceinline__ double recip_fp64(double d) {
+    double r = (double)(1.0f / (float)d);
+    r = r * (2.0 - d * r);
+    return r * (2.0 - d * r);
+}
+
 // in-place Cholesky of a packed lower-triangular SPD matrix; the diagonal
 // holds the reciprocals of L's diagonal (so solves need no division)
 template <int M>
@@ -42,7 +57,7 @@ __device__ __forceinline__ void chol(double *A) {
         double s = A[pidx<M>(j, j)];
 #pragma unroll
         for (int k = 0; k < j; k++) s -= A[pidx<M>(j, k)] * A[pidx<M>(j, k)];
-        const double id = rsqrt(s > 0.0 ? s : 1e-300);
+        const double id = rsqrt_fp64(s > 1e-30 ? s : 1e-30);
         A[pidx<M>(j, j)] = id;
 #pragma unroll
         for (int i = j + 1; i < M; i++) {
@@ -111,8 +126,13 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
         m[i] = -U / (1.0f + sqrtf(fmaxf(q, 0.f)));
     }
     ds[0] = 0.f;
+    double ids[N];
+    ids[0] = 0.0;
 #pragma unroll
-    for (int i = 1; i < N; i++) ds[i] = fmaxf(s[i] - s[i - 1], 1e-4f);
+    for (int i = 1; i < N; i++) {
+        ds[i] = fmaxf(s[i] - s[i - 1], 1e-4f);
+        ids[i] = recip_fp64(ds[i]);
+    }
     const float tanl0 = (hz[N - 1] - hz[0]) / fmaxf(s[N - 1], 1e-4f);
     const float sec2 = 1.0f + tanl0 * tanl0;
     const float pt0 = 0.00299792458f * p.fit.bz / fmaxf(fabsf(k0), 1e-7f);
@@ -125,8 +145,8 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
         const float xx0 = disk[i] ? p.fit.x0_disk * sqrtf(sec2) / atl : p.fit.x0_barrel * sqrtf(sec2);
         const float th = 0.0136f / pmom * sqrtf(xx0) * (1.0f + 0.038f * logf(xx0));
         const double th2 = (double)th * th;
-        vb[i] = fmax(th2 * sec2, 1e-20);
-        vg[i] = fmax(th2 * sec2 * sec2, 1e-20);
+        vb[i] = recip_fp64(fmax(th2 * sec2, 1e-20));          // weights 1/variance
+        vg[i] = recip_fp64(fmax(th2 * sec2 * sec2, 1e-20));
     }
     // 3) line fit in s-z
     double A[N * (N + 1) / 2], v[N], wz[N];
@@ -135,13 +155,13 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
 #pragma unroll
     for (int i = 0; i < N; i++) {
         const double sz = disk[i] ? (double)p.fit.sigma_r * atl : (double)p.fit.sigma_z;
-        wz[i] = 1.0 / (sz * sz);
+        wz[i] = recip_fp64(sz * sz);
         A[pidx<N>(i, i)] = wz[i];
         v[i] = wz[i] * hz[i];
     }
 #pragma unroll
     for (int i = 1; i < N - 1; i++) {
-        const double g0 = 1.0 / ds[i], g2 = 1.0 / ds[i + 1], g1 = -(g0 + g2), w = 1.0 / vg[i];
+        const double g0 = ids[i], g2 = ids[i + 1], g1 = -(g0 + g2), w = vg[i];
         A[pidx<N>(i - 1, i - 1)] += g0 * g0 * w;
         A[pidx<N>(i, i - 1)] += g1 * g0 * w;
         A[pidx<N>(i, i)] += g1 * g1 * w;
@@ -156,8 +176,8 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
     for (int i = 0; i < N; i++) chi2 += wz[i] * (v[i] - hz[i]) * (v[i] - hz[i]);
 #pragma unroll
     for (int i = 1; i < N - 1; i++) {
-        const double gam = (v[i + 1] - v[i]) / ds[i + 1] - (v[i] - v[i - 1]) / ds[i];
-        chi2 += gam * gam / vg[i];
+        const double gam = (v[i + 1] - v[i]) * ids[i + 1] - (v[i] - v[i - 1]) * ids[i];
+        chi2 += gam * gam * vg[i];
     }
     double Cv[2][2];
 #pragma unroll
@@ -174,7 +194,7 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
     double B[M * (M + 1) / 2], x[M];
 #pragma unroll
     for (int i = 0; i < M * (M + 1) / 2; i++) B[i] = 0.0;
-    const double wu = 1.0 / ((double)p.fit.sigma_rphi * p.fit.sigma_rphi);
+    const double wu = recip_fp64((double)p.fit.sigma_rphi * p.fit.sigma_rphi);
 #pragma unroll
     for (int i = 0; i < N; i++) {
         B[pidx<M>(i, i)] = wu;
@@ -183,8 +203,8 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
     x[N] = 0.0;
 #pragma unroll
     for (int i = 1; i < N - 1; i++) {
-        const double h0 = 1.0 / ds[i], h2 = 1.0 / ds[i + 1], h1 = -(h0 + h2);
-        const double h3 = -0.5 * ((double)ds[i] + ds[i + 1]), w = 1.0 / vb[i];
+        const double h0 = ids[i], h2 = ids[i + 1], h1 = -(h0 + h2);
+        const double h3 = -0.5 * ((double)ds[i] + ds[i + 1]), w = vb[i];
         B[pidx<M>(i - 1, i - 1)] += h0 * h0 * w;
         B[pidx<M>(i, i - 1)] += h1 * h0 * w;
         B[pidx<M>(i, i)] += h1 * h1 * w;
@@ -203,9 +223,9 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
     for (int i = 0; i < N; i++) chi2 += wu * (x[i] - m[i]) * (x[i] - m[i]);
 #pragma unroll
     for (int i = 1; i < N - 1; i++) {
-        const double be = (x[i + 1] - x[i]) / ds[i + 1] - (x[i] - x[i - 1]) / ds[i] -
+        const double be = (x[i + 1] - x[i]) * ids[i + 1] - (x[i] - x[i - 1]) * ids[i] -
                           dk * 0.5 * ((double)ds[i] + ds[i + 1]);
-        chi2 += be * be / vb[i];
+        chi2 += be * be * vb[i];
     }
     double Cc[3][3];
     {
@@ -225,7 +245,7 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
     const float u0 = (float)x[0];
     const float px = hx[0] - u0 * sn, py = hy[0] + u0 * cs;
     const float ds1 = ds[1];
-    const float psi = psi0 + (float)((x[1] - x[0]) / ds1 - dk * 0.5 * ds1);
+    const float psi = psi0 + (float)((x[1] - x[0]) * ids[1] - dk * 0.5 * ds1);
     float sp, cp;
     sincosf(psi, &sp, &cp);
     const float Xo = -det2(px, cp, -py, sp);       // -(P . t)
@@ -238,7 +258,7 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
     float phi0 = psi + dpsi;
     phi0 = phi0 - 6.28318531f * rintf(phi0 * 0.159154943f);
     const float arc = kf != 0.f ? dpsi / kf : Xo;
-    const double tanl = (v[1] - v[0]) / ds1;
+    const double tanl = (v[1] - v[0]) * ids[1];
     const double z0 = v[0] + tanl * arc;
     // circle-block Jacobian d(kappa, phi0, d0) / d(u0, u1, dk)
     float J[3][3];
@@ -274,7 +294,7 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
                 for (int d = 0; d < 3; d++) acc += (double)J[a][c] * Cc[c][d] * J[b][d];
             Fc[a][b] = (float)acc;
         }
-    const double Jl[2][2] = {{-1.0 / ds1, 1.0 / ds1}, {1.0 - arc / ds1, arc / ds1}};
+    const double Jl[2][2] = {{-ids[1], ids[1]}, {1.0 - arc * ids[1], arc * ids[1]}};
     float Fl[2][2];
 #pragma unroll
     for (int a = 0; a < 2; a++)

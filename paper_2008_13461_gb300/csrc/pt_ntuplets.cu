@@ -32,7 +32,8 @@ __global__ void __launch_bounds__(kThreads) k_dfs(Params p) {
         st_it[0] = 0;
         while (depth >= 0) {
             const int x = st_cell[depth];
-            const int ne = p.edge_cnt[x];
+            const int2 er = p.edge_rng[p.out_off[p.cell_inner[x]] + p.cell_rank[x]];
+            const int ne = er.y;
             if (ne == 0) {
                 // start of a path: emit if it is a root and the path has >= 3 hits
                 if (depth >= 1 && root_layer(p.blayer[p.cell_inner[x]])) {
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(kThreads) k_dfs(Params p) {
                 continue;
             }
             if (st_it[depth] < ne) {
-                const int64_t eidx = (int64_t)p.edge_off[x] + st_it[depth];
+                const int64_t eidx = (int64_t)er.x + st_it[depth];
                 st_it[depth]++;
                 if (eidx >= p.cap_edges || depth + 1 >= PT_NMAX - 1) continue;
                 depth++;
