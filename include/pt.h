@@ -65,7 +65,8 @@ typedef enum {
     PT_ERR_INVALID_ARG = 1, /* NULL pointer, bad size, bad tuning, small ws */
     PT_ERR_CAPACITY = 2,    /* a device buffer overflowed (pt_read_counts) */
     PT_ERR_INPUT = 3,       /* input violates the contract (pt_read_counts) */
-    PT_ERR_CUDA = 4         /* a CUDA runtime call failed */
+    PT_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    PT_ERR_TOO_LARGE = 5    /* beyond the fixed scratch of pt_bin_hits_noalloc */
 } pt_status;
 
 /* bits of pt_counts.flags */
@@ -242,6 +243,35 @@ const int32_t *pt_hit_order(const void *ws, size_t ws_bytes, const pt_hits *hits
                             const pt_config *cfg);
 
 const char *pt_status_string(pt_status s);
+
+/* Allocation-free hit binning, for callers that cannot allocate device
+ * memory -- for instance code running where cudaMalloc is not allowed, or a
+ * host program whose device memory is fully budgeted up front.  The paper
+ * has no counterpart: this is the binning step of pt_build_doublets (hits
+ * tiled per event, layer, phi tile and z|r tile) with its scratch kept in a
+ * fixed array inside the library (about 14 MB held on every GPU that loads
+ * the library, until the process exits) instead of a workspace.
+ *
+ * Inputs: hits and geometry as for pt_build_doublets (device arrays), tile
+ * counts n_phi_bins in 16..1024 and n_t_bins in 1..64.  Outputs (device,
+ * caller-allocated): binned[n_hits*4] float x, y, z, r in binned order,
+ * 16-byte aligned; hit_order[n_hits] binned position -> input index;
+ * tile_off[T+1] exclusive offsets of the T = n_events*10*n_phi_bins*n_t_bins
+ * tiles (tile_off[T] = number of binned hits); flags[1] receives
+ * PT_FLAG_INPUT when a hit violates the input contract (such hits are left
+ * out).  The tile order and the offsets equal those of pt_build_doublets for
+ * the same tuning; the order of hits inside a tile is unspecified.
+ *
+ * Limits: at most 2^20 hits and 2^22 tiles, else PT_ERR_TOO_LARGE.  The
+ * library allocates nothing (no cudaMalloc / cudaFree); it only enqueues
+ * memsets, kernels and one 4-byte device copy on `stream`.  The first call on
+ * each device looks up the address of the fixed array with
+ * cudaGetSymbolAddress, so make that first call before any stream capture.
+ * All calls share the one array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller. */
+pt_status pt_bin_hits_noalloc(const pt_hits *hits, const pt_geometry *geometry, int32_t n_phi_bins,
+                              int32_t n_t_bins, float *binned, int32_t *hit_order, int32_t *tile_off,
+                              int32_t *flags, void *stream);
 
 #ifdef __cplusplus
 }

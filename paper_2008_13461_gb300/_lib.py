@@ -15,7 +15,7 @@ N_LAYERS = 10
 MAX_PAIRS = 32
 NMAX = 8
 
-PT_OK, PT_ERR_INVALID_ARG, PT_ERR_CAPACITY, PT_ERR_INPUT, PT_ERR_CUDA = range(5)
+PT_OK, PT_ERR_INVALID_ARG, PT_ERR_CAPACITY, PT_ERR_INPUT, PT_ERR_CUDA, PT_ERR_TOO_LARGE = range(6)
 FLAG_CELLS, FLAG_EDGES, FLAG_TUPLES, FLAG_TRACKS, FLAG_INPUT = 1, 2, 4, 8, 16
 
 
@@ -93,7 +93,7 @@ class Counts(C.Structure):
 
 # every symbol declared in include/pt.h
 EXPORTS = ("pt_workspace_size", "pt_build_doublets", "pt_connect_cells", "pt_find_ntuplets",
-           "pt_fit_tracks", "pt_read_counts", "pt_hit_order", "pt_status_string")
+           "pt_fit_tracks", "pt_read_counts", "pt_hit_order", "pt_status_string", "pt_bin_hits_noalloc")
 
 _lib = None
 
@@ -127,6 +127,9 @@ def lib(build_if_missing: bool = True):
     L.pt_hit_order.argtypes = common
     L.pt_status_string.restype = C.c_char_p
     L.pt_status_string.argtypes = [C.c_int]
+    L.pt_bin_hits_noalloc.restype = C.c_int
+    L.pt_bin_hits_noalloc.argtypes = [P(Hits), P(Geometry), C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p]
     _lib = L
     return L
 
@@ -176,3 +179,9 @@ def read_counts(ws, ws_bytes, hits, cfg, stream) -> tuple[int, Counts]:
 
 def hit_order(ws, ws_bytes, hits, cfg) -> int:
     return lib().pt_hit_order(ws, ws_bytes, C.byref(hits), C.byref(cfg))
+
+
+def bin_hits_noalloc(hits, geometry, n_phi_bins, n_t_bins, binned, hit_order_out, tile_off, flags, stream) -> None:
+    """Allocation-free binning (see pt_bin_hits_noalloc in pt.h)."""
+    check(lib().pt_bin_hits_noalloc(C.byref(hits), C.byref(geometry), n_phi_bins, n_t_bins, binned, hit_order_out,
+                                    tile_off, flags, stream), "pt_bin_hits_noalloc")

@@ -363,6 +363,7 @@ const char *pt_status_string(pt_status s) {
     case PT_ERR_CAPACITY: return "output capacity exceeded";
     case PT_ERR_INPUT: return "input violates the contract";
     case PT_ERR_CUDA: return "CUDA error";
+    case PT_ERR_TOO_LARGE: return "problem larger than the fixed scratch of the allocation-free entry point";
     }
     return "unknown status";
 }
