@@ -162,6 +162,7 @@ Params make_params(void *ws, const WsLayout &L, const pt_hits *h, const pt_confi
     p.scan_part = (int32_t *)(w + L.scan_part);
     p.hit_bin = (int32_t *)(w + L.hit_bin);
     p.hit_rank = (int32_t *)(w + L.hit_rank);
+    p.fb_big = p.hit_rank;     // free once the hits are binned
     p.bh = (float4 *)(w + L.bh);
     p.blayer = (int8_t *)(w + L.blayer);
     p.bev = (int32_t *)(w + L.bev);

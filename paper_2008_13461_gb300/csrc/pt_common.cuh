@@ -6,7 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/pt.h"
+#include "pt.h"
 
 namespace ptk {
 
@@ -17,7 +17,10 @@ constexpr int kCounters = 16;
 // workspace counters (int32 slots at the start of ws)
 enum Counter {
     C_CELLS = 0, C_EDGES = 1, C_TUPLES = 2, C_TRACKS = 3, C_FLAGS = 4, C_FALLBACK = 5,
-    C_ALIVE_CELLS = 6, C_ALIVE_TUPLES = 7, C_LEAVES = 8
+    C_ALIVE_CELLS = 6, C_ALIVE_TUPLES = 7, C_LEAVES = 8,
+    C_FB_NEXT = 9,        // Fishbone: next chunk of outer hits to take
+    C_FB_BIG = 10,        // Fishbone: outer hits listed for the large warps
+    C_FB_BIG_NEXT = 11    // Fishbone: next listed outer hit to take
 };
 
 // Byte offsets of every workspace array (all 256-byte aligned).
@@ -43,6 +46,7 @@ struct Params {
     float4 *bh;                          // binned hits (x, y, z, r)
     int8_t *blayer;
     int32_t *bev, *perm, *in_off, *in_cnt;
+    int32_t *fb_big;                     // outer hits with many cells (reuses hit_rank after binning)
     int2 *edge_rng;                      // per out-list position: (first edge, count)
     int32_t *leaf_list;
     int32_t *out_off, *cell_rank, *out_idx;  // live cells grouped by inner hit (CSR)
@@ -420,14 +424,15 @@ __device__ __forceinline__ float det2(float a, float b, float c, float d) {
     return __fadd_rn(f, e);
 }
 
-// Fishbone alignment: u.v > 0 and |u x v|^2 <= eps2 |u|^2 |v|^2 (3-D).  The
-// cross product of nearly parallel u, v cancels, so its components are taken
-// with det2 (relative error <= 2u each); the squared norms and products of
-// positive terms then carry relative errors below 8u, which bounds F.
-__device__ __forceinline__ int pred_fb(const FHit &h1, const FHit &h2, const FHit &h, float eps2,
-                                       int32_t *cnt) {
-    const float ux = h1.x - h.x, uy = h1.y - h.y, uz = h1.z - h.z;
-    const float vx = h2.x - h.x, vy = h2.y - h.y, vz = h2.z - h.z;
+// Fishbone alignment: u.v > 0 and |u x v|^2 <= eps2 |u|^2 |v|^2 (3-D), for
+// u = h1 - h and v = h2 - h.  Hits are multiples of 2^-14 below 64 in
+// magnitude, so these differences are exact in float32 and the test can be
+// given them directly.  The cross product of nearly parallel u, v cancels,
+// so its components are taken with det2 (relative error <= 2u each); the
+// squared norms and products of positive terms then carry relative errors
+// below 8u, which bounds F.
+__device__ __forceinline__ int pred_fb_d(float ux, float uy, float uz, float vx, float vy, float vz, float eps2,
+                                         int32_t *cnt) {
     const float d1 = ux * vx, d2 = uy * vy, d3 = uz * vz;
     const float dot = (d1 + d2) + d3, dotb = (fabsf(d1) + fabsf(d2)) + fabsf(d3);
     const float eD = ferr(3, dotb);
@@ -441,8 +446,12 @@ __device__ __forceinline__ int pred_fb(const FHit &h1, const FHit &h2, const FHi
         if (F > e) return 1;
         if (F < -e) return 0;
     }
-    return exact_fb(ghit(h1.x, h1.y, h1.z, h1.r), ghit(h2.x, h2.y, h2.z, h2.r), ghit(h.x, h.y, h.z, h.r), eps2,
-                    cnt);
+    const GHit o = {0, 0, 0, 0};
+    return exact_fb(ghit(ux, uy, uz, 0.f), ghit(vx, vy, vz, 0.f), o, eps2, cnt);
+}
+
+__device__ __forceinline__ int pred_fb(const FHit &h1, const FHit &h2, const FHit &h, float eps2, int32_t *cnt) {
+    return pred_fb_d(h1.x - h.x, h1.y - h.y, h1.z - h.z, h2.x - h.x, h2.y - h.y, h2.z - h.z, eps2, cnt);
 }
 
 }  // namespace ptk

@@ -14,8 +14,9 @@
 // and |X| <= tol |ac| <= tol (|ab| + |bc|) give
 //     |key_c - key_a| <= tol (sqrt(1+key_a^2)/dr_bc + sqrt(1+key_c^2)/dr_ab);
 // for a disk b the same holds with r and z exchanged.  With sqrt(1+key_a^2)
-// and 1/dr_ab bounded by their per-hit maximum (both computed with the keys
-// in the Fishbone kernel), every aligned candidate falls in the window; the
+// and 1/dr_ab bounded by their maximum over the cells ending on b (both
+// computed with the keys in the Fishbone kernel), every aligned candidate
+// falls in the window; the
 // few inside it take a float32 R-z test with an error bound and then the
 // exact predicate chain.
 //

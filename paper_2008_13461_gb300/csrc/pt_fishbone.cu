@@ -1,0 +1,326 @@
+// Step a2: the Fishbone (Sec. 3.3), and the per-cell data the CA connection
+// needs from it.
+//
+// Cells sharing an outer hit o whose inner hits lie on one layer and are
+// aligned as seen from o form a fishbone; every cell of it dies except the
+// shortest (equal lengths: the smaller input index of the inner hit wins).
+//
+// One warp per outer hit.  The warp keeps, per cell, the difference vector
+// u = h_inner - h_o in shared memory; hits are multiples of 2^-14 below 64 in
+// magnitude, so u is exact in float32 and the alignment test and the squared
+// length (an integer in grid units) are evaluated from it with no further
+// memory traffic.  Alignment within eps implies that the unit directions of
+// two siblings differ by at most du = eps pi/2 (plus float32 slack), hence
+// so does any 1-Lipschitz key of them (u^_z for a barrel o, the radial
+// component for a disk o).  The siblings are counting-sorted into key
+// buckets of width >= du, and each cell is compared only with the cells of
+// its own and the two neighbouring buckets: a superset of its aligned
+// siblings, so the result is exact at ~O(k) work per outer hit.
+//
+// Shared memory per warp bounds the siblings it can hold, and the warps an
+// SM can keep resident bound how well the gathers of the inner hits are
+// hidden.  Most outer hits have fewer than ~200 cells, so two launches share
+// the work: many small warps take chunks of 32 outer hits from a queue and
+// list the outer hits with more cells, which few large warps then take one
+// at a time; beyond the large warps' capacity a plain pairwise loop over
+// global memory is used.
+//
+// The same pass writes, for the CA connection, each cell's R-z slope key
+// relative to o (NaN for dead cells) and per hit the bounds the slope window
+// needs (taken over all cells of o, a superset of the live ones, so the
+// window only widens), and ranks every live cell in the out-list of its
+// inner hit.
+#include "pt_common.cuh"
+#include "pt_kernels.cuh"
+
+namespace ptk {
+
+constexpr int kFbDirect = 12;        // up to this many siblings: compare all pairs
+
+// Per warp and cell: u = h_inner - h_o (exact) and 1/|u| in w; the cell's
+// position (bits 0-9), its inner layer (10-14) and key bucket (15-24).
+template <int W, int M, int NB>
+struct FbSmem {
+    float4 rec[W][M];
+    int meta[W][M];
+    int16_t idx[W][M];               // cell positions sorted by bucket
+    uint8_t dead[W][M];
+    int pos[W][NB];
+};
+
+__device__ __forceinline__ int rec_cell(int m) { return m & 1023; }
+__device__ __forceinline__ int rec_bucket(int m) { return (m >> 15) & 1023; }
+constexpr int kRecLayerMask = 31 << 10;
+
+// Bucket key of a record: u^_z (barrel o) or the radial component of u^
+// (disk o; (rx, ry) is o's radial direction).  Explicit roundings, so every
+// evaluation gives the same bits.
+__device__ __forceinline__ float fb_key(const float4 &r, bool disk, float rx, float ry) {
+    const float k = disk ? __fmul_rn(__fmaf_rn(r.x, rx, __fmul_rn(r.y, ry)), r.w) : __fmul_rn(r.z, r.w);
+    return k == k ? k : 0.f;
+}
+
+// squared length of a difference vector, in grid units (exact)
+__device__ __forceinline__ long long len2u(float ux, float uy, float uz) {
+    const long long x = grid_int(ux), y = grid_int(uy), z = grid_int(uz);
+    return x * x + y * y + z * z;
+}
+
+__device__ __forceinline__ int cell_layer(const Params &p, int64_t c) { return p.pair[p.cell_pair[c]].inner; }
+
+// Does sibling d (record r2, meta m2) kill cell j (record r1, unit vector
+// v1, meta m1)?  Same inner layer, unit directions close (a necessary
+// condition of alignment), aligned, and strictly shorter or as long with a
+// smaller input index of the inner hit.
+__device__ __forceinline__ bool fb_kills(const Params &p, int64_t b, int j, const float4 &r1, const float3 &v1,
+                                         int m1, int d, int m2, const float4 &r2, float unit_thr) {
+    if (d == j || ((m1 ^ m2) & kRecLayerMask)) return false;
+    const float dx = v1.x - r2.x * r2.w, dy = v1.y - r2.y * r2.w, dz = v1.z - r2.z * r2.w;
+    if (dx * dx + dy * dy + dz * dz > unit_thr) return false;
+    if (!pred_fb_d(r1.x, r1.y, r1.z, r2.x, r2.y, r2.z, p.fishbone_eps2, p.counters)) return false;
+    const long long l1 = len2u(r1.x, r1.y, r1.z), l2 = len2u(r2.x, r2.y, r2.z);
+    return l2 < l1 || (l2 == l1 && p.perm[p.cell_inner[b + d]] < p.perm[p.cell_inner[b + j]]);
+}
+
+// Verdicts of the n cells of outer hit o (one warp); returns the lane's
+// count of live cells.  kGlobal: n may exceed M (pairwise loop compiled in).
+template <int W, int M, int NB, bool kGlobal>
+__device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64_t b, int lane, int w,
+                                            float unit_thr, float du, FbSmem<W, M, NB> &sm) {
+    const float4 ho = __ldg(p.bh + o);
+    const bool disk = p.layer[p.blayer[o]].kind == PT_LAYER_DISK;
+    const bool in_smem = !kGlobal || n <= M;
+    const float irr = rsqrtf(ho.x * ho.x + ho.y * ho.y);
+    const float rx = ho.x * irr, ry = ho.y * irr;
+    // pass 1: R-z slope keys (barrel o: (z_o - z_a)/(r_o - r_a); disk o:
+    // (r_o - r_a)/(z_o - z_a)) with the per-hit bounds; records and the
+    // range of the bucket keys
+    float kmax = 0.f, gmin = 3.0e38f, bmin = 3.0f, bmax = -3.0f;
+    for (int j = lane; j < n; j += 32) {
+        const int i = p.cell_inner[b + j];
+        const int L = cell_layer(p, b + j);
+        const float4 a = __ldg(p.bh + i);
+        const float dr = ho.w - a.w, dz = ho.z - a.z;
+        const float num = disk ? dr : dz, den = disk ? dz : dr;
+        const float ck = den != 0.f ? num / den : __int_as_float(0x7f800000);
+        kmax = fmaxf(kmax, sqrtf(1.0f + ck * ck));
+        gmin = fminf(gmin, fabsf(den));
+        p.ck[b + j] = ck;
+        if (in_smem) {
+            const float ux = a.x - ho.x, uy = a.y - ho.y, uz = a.z - ho.z;
+            const float4 r = make_float4(ux, uy, uz, rsqrtf(ux * ux + uy * uy + uz * uz));
+            sm.rec[w][j] = r;
+            sm.meta[w][j] = j | (L << 10);
+            sm.dead[w][j] = 0;
+            const float key = fb_key(r, disk, rx, ry);
+            bmin = fminf(bmin, key);
+            bmax = fmaxf(bmax, key);
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, d));
+        gmin = fminf(gmin, __shfl_xor_sync(0xffffffffu, gmin, d));
+    }
+    if (lane == 0) p.hk[o] = make_float2(kmax, gmin);
+    __syncwarp();
+
+    if (kGlobal && !in_smem) {
+        // more siblings than the warp holds: plain pairwise loop
+        const GHit gh = ghit(ho.x, ho.y, ho.z, ho.w);
+        const FHit h = {ho.x, ho.y, ho.z, ho.w};
+        for (int j = lane; j < n; j += 32) {
+            const int i1 = p.cell_inner[b + j];
+            const int L1 = cell_layer(p, b + j);
+            const FHit h1 = load_hit(p.bh, i1);
+            const GHit g1 = ghit(h1.x, h1.y, h1.z, h1.r);
+            const long long l1 = (g1.x - gh.x) * (g1.x - gh.x) + (g1.y - gh.y) * (g1.y - gh.y) +
+                                 (g1.z - gh.z) * (g1.z - gh.z);
+            bool dead = false;
+            for (int d = 0; d < n && !dead; d++) {
+                if (d == j || cell_layer(p, b + d) != L1) continue;
+                const int i2 = p.cell_inner[b + d];
+                const FHit h2 = load_hit(p.bh, i2);
+                if (!pred_fb(h1, h2, h, p.fishbone_eps2, p.counters)) continue;
+                const GHit g2 = ghit(h2.x, h2.y, h2.z, h2.r);
+                const long long l2 = (g2.x - gh.x) * (g2.x - gh.x) + (g2.y - gh.y) * (g2.y - gh.y) +
+                                     (g2.z - gh.z) * (g2.z - gh.z);
+                dead = l2 < l1 || (l2 == l1 && p.perm[i2] < p.perm[i1]);
+            }
+            if (dead) p.cell_alive[b + j] = 0;
+        }
+    } else if (n <= kFbDirect) {
+        for (int j = lane; j < n; j += 32) {
+            const float4 r1 = sm.rec[w][j];
+            const float3 v1 = make_float3(r1.x * r1.w, r1.y * r1.w, r1.z * r1.w);
+            const int m1 = sm.meta[w][j];
+            bool dead = false;
+            for (int d = 0; d < n && !dead; d++)
+                dead = fb_kills(p, b, j, r1, v1, m1, d, sm.meta[w][d], sm.rec[w][d], unit_thr);
+            if (dead) sm.dead[w][j] = 1;
+        }
+    } else {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            bmin = fminf(bmin, __shfl_xor_sync(0xffffffffu, bmin, d));
+            bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, d));
+        }
+        // about two buckets per cell (a power of two, 32 .. NB)
+        const int nb = min(NB, max(32, 1 << (32 - __clz(2 * n - 1))));
+        const float iw = 1.0f / fmaxf(du, (bmax - bmin) / (float)(nb - 2));
+        for (int q = lane; q < nb; q += 32) sm.pos[w][q] = 0;
+        __syncwarp();
+        for (int j = lane; j < n; j += 32) {
+            const float key = fb_key(sm.rec[w][j], disk, rx, ry);
+            const int bk = min(max(__float2int_rd((key - bmin) * iw), 0), nb - 1);
+            sm.meta[w][j] |= bk << 15;
+            atomicAdd(&sm.pos[w][bk], 1);
+        }
+        __syncwarp();
+        {   // exclusive scan of the bucket counts, nb / 32 buckets per lane
+            const int per = nb >> 5;
+            int sum = 0;
+            for (int q = 0; q < per; q++) sum += sm.pos[w][lane * per + q];
+            int incl = sum;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += t;
+            }
+            int run = incl - sum;
+            for (int q = 0; q < per; q++) {
+                const int v = sm.pos[w][lane * per + q];
+                sm.pos[w][lane * per + q] = run;
+                run += v;
+            }
+        }
+        __syncwarp();
+        for (int j = lane; j < n; j += 32) sm.idx[w][atomicAdd(&sm.pos[w][rec_bucket(sm.meta[w][j])], 1)] = (int16_t)j;
+        __syncwarp();
+        // sm.pos[bk] is now the end of bucket bk; each lane takes sorted
+        // positions and scans the cells of buckets bk-1 .. bk+1
+        for (int q0 = lane; q0 < n; q0 += 32) {
+            const int j = sm.idx[w][q0];
+            const float4 r1 = sm.rec[w][j];
+            const float3 v1 = make_float3(r1.x * r1.w, r1.y * r1.w, r1.z * r1.w);
+            const int m1 = sm.meta[w][j];
+            const int bk = rec_bucket(m1);
+            const int start = bk >= 2 ? sm.pos[w][bk - 2] : 0;
+            const int end = sm.pos[w][min(bk + 1, nb - 1)];
+            bool dead = false;
+            for (int q = start; q < end && !dead; q++) {
+                const int d = sm.idx[w][q];
+                dead = fb_kills(p, b, j, r1, v1, m1, d, sm.meta[w][d], sm.rec[w][d], unit_thr);
+            }
+            if (dead) sm.dead[w][j] = 1;
+        }
+    }
+    __syncwarp();
+
+    // pass 2: dead cells get a NaN key; live cells join the out-list of
+    // their inner hit (rank by atomics)
+    int alive = 0;
+    for (int j = lane; j < n; j += 32) {
+        const bool dead = in_smem ? sm.dead[w][j] != 0 : p.cell_alive[b + j] == 0;
+        if (dead) {
+            if (in_smem) p.cell_alive[b + j] = 0;
+            p.ck[b + j] = __int_as_float(0x7fc00000);
+        } else {
+            alive++;
+            p.cell_rank[b + j] = atomicAdd(p.out_off + p.cell_inner[b + j], 1);
+        }
+    }
+    __syncwarp();
+    return alive;
+}
+
+__device__ __forceinline__ void add_alive(const Params &p, int v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(p.counters + C_ALIVE_CELLS, v);
+}
+
+// Small warps: take chunks of 32 consecutive binned hits from a queue, load
+// their cell counts together, work through those with 1..M cells and list
+// the ones with more.
+template <int W, int M, int NB, int kMinBlocks>
+__global__ void __launch_bounds__(32 * W, kMinBlocks) k_fishbone_small(Params p, float unit_thr, float du) {
+    __shared__ FbSmem<W, M, NB> sm;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int my_alive = 0;
+    const int n_binned = p.bin_cnt[p.n_bins];
+    const int n_chunks = (n_binned + 31) >> 5;
+    for (;;) {
+        int ch = 0;
+        if (lane == 0) ch = atomicAdd(p.counters + C_FB_NEXT, 1);
+        ch = __shfl_sync(0xffffffffu, ch, 0);
+        if (ch >= n_chunks) break;
+        const int ol = (ch << 5) + lane;
+        int nl = 0, bl = 0;
+        if (ol < n_binned) {
+            nl = p.in_cnt[ol];
+            bl = p.in_off[ol];
+        }
+        const bool ok = nl >= 1 && (int64_t)bl + nl <= p.cap_cells;
+        const unsigned big = __ballot_sync(0xffffffffu, ok && nl > M);
+        if (big) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(p.counters + C_FB_BIG, __popc(big));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (ok && nl > M) p.fb_big[base + __popc(big & ((1u << lane) - 1u))] = ol;
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, ok && nl <= M);
+        while (todo) {
+            const int t = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int n = __shfl_sync(0xffffffffu, nl, t);
+            const int b = __shfl_sync(0xffffffffu, bl, t);
+            my_alive += fishbone_hit<W, M, NB, false>(p, (ch << 5) + t, n, b, lane, w, unit_thr, du, sm);
+        }
+    }
+    add_alive(p, my_alive);
+}
+
+// Large warps: the listed outer hits, one at a time from a queue.
+template <int W, int M, int NB>
+__global__ void __launch_bounds__(32 * W) k_fishbone_large(Params p, float unit_thr, float du) {
+    __shared__ FbSmem<W, M, NB> sm;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int my_alive = 0;
+    const int n_list = p.counters[C_FB_BIG];
+    for (;;) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(p.counters + C_FB_BIG_NEXT, 1);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= n_list) break;
+        const int o = p.fb_big[k];
+        my_alive += fishbone_hit<W, M, NB, true>(p, o, p.in_cnt[o], p.in_off[o], lane, w, unit_thr, du, sm);
+    }
+    add_alive(p, my_alive);
+}
+
+constexpr int kFbSmallMax = 192;
+
+void launch_fishbone(const Params &p, float unit_thr, float du, int grid, cudaStream_t s) {
+    k_fishbone_small<8, kFbSmallMax, 256, 3><<<grid, 256, 0, s>>>(p, unit_thr, du);
+    k_fishbone_large<2, 512, 1024><<<grid, 64, 0, s>>>(p, unit_thr, du);
+}
+
+// Out-lists: live cells grouped by their inner hit (CSR), from the ranks
+// taken in the Fishbone kernel and the scanned per-hit counts.
+__global__ void __launch_bounds__(kThreads) k_out_fill(Params p) {
+    const int64_t n_cells = min((int64_t)p.counters[C_CELLS], p.cap_cells);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += stride) {
+        if (!p.cell_alive[c]) continue;
+        const int i = p.cell_inner[c];
+        p.out_idx[p.out_off[i] + p.cell_rank[c]] = (int32_t)c;
+    }
+}
+
+void launch_out_lists(const Params &p, int grid, cudaStream_t s) {
+    launch_scan(p.out_off, p.n_hits, p.scan_part, s);
+    k_out_fill<<<grid, kThreads, 0, s>>>(p);
+}
+
+}  // namespace ptk
