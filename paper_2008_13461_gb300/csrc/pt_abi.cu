@@ -53,11 +53,14 @@ bool layout(const pt_hits *h, const pt_config *cfg, WsLayout &L) {
     L.perm = take(4 * nh);
     L.in_off = take(4 * nh);
     L.in_cnt = take(4 * nh);
+    L.in_live = take(4 * nh);
     L.hk = take(8 * nh);
     L.out_off = take(4 * (nh + 1));
     L.cell_rank = take(4 * nc);
-    L.out_idx = take(4 * nc);
+    L.out_ent = take(8 * nc);
     L.ck = take(4 * nc);
+    L.sk = take(8 * nc);
+    L.sci = take(4 * nc);
     L.leaf_list = take(4 * nc);
     L.edge_rng = take(8 * nc);
     L.has_out = take(nc);
@@ -172,8 +175,11 @@ Params make_params(void *ws, const WsLayout &L, const pt_hits *h, const pt_confi
     p.hk = (float2 *)(w + L.hk);
     p.out_off = (int32_t *)(w + L.out_off);
     p.cell_rank = (int32_t *)(w + L.cell_rank);
-    p.out_idx = (int32_t *)(w + L.out_idx);
+    p.out_ent = (int2 *)(w + L.out_ent);
     p.ck = (float *)(w + L.ck);
+    p.sk = (float2 *)(w + L.sk);
+    p.sci = (int32_t *)(w + L.sci);
+    p.in_live = (int32_t *)(w + L.in_live);
     p.leaf_list = (int32_t *)(w + L.leaf_list);
     p.edge_rng = (int2 *)(w + L.edge_rng);
     p.has_out = (uint8_t *)(w + L.has_out);
@@ -248,6 +254,7 @@ pt_status pt_build_doublets(void *ws, size_t ws_bytes, const pt_hits *hits, cons
         return PT_ERR_CUDA;
     if (cudaMemsetAsync(p.out_off, 0, sizeof(int32_t) * ((size_t)hits->n_hits + 1), s) != cudaSuccess)
         return PT_ERR_CUDA;
+    if (cudaMemsetAsync(p.in_live, 0, sizeof(int32_t) * (size_t)hits->n_hits, s) != cudaSuccess) return PT_ERR_CUDA;
     const int grid = grid_for(cfg);
     launch_binning(p, grid, s);
     launch_doublets(p, cfg->tuning.doublet_lanes, grid, s);

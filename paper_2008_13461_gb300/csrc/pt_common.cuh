@@ -26,7 +26,7 @@ enum Counter {
 // Byte offsets of every workspace array (all 256-byte aligned).
 struct WsLayout {
     size_t counters, bin_cnt, scan_part, hit_bin, hit_rank;
-    size_t bh, blayer, bev, perm, in_off, in_cnt, hk, ck, leaf_list, out_off, cell_rank, out_idx;
+    size_t bh, blayer, bev, perm, in_off, in_cnt, in_live, hk, ck, sk, sci, leaf_list, out_off, cell_rank, out_ent;
     size_t edge_rng, has_out, maxlen;
     size_t total;
     int64_t n_bins;        // events * layers * phi bins * t bins
@@ -49,9 +49,13 @@ struct Params {
     int32_t *fb_big;                     // outer hits with many cells (reuses hit_rank after binning)
     int2 *edge_rng;                      // per out-list position: (first edge, count)
     int32_t *leaf_list;
-    int32_t *out_off, *cell_rank, *out_idx;  // live cells grouped by inner hit (CSR)
-    float *ck;                           // R-z slope key of each cell w.r.t. its outer hit (NaN: dead)
+    int32_t *out_off, *cell_rank;        // live cells grouped by inner hit (CSR) ...
+    int2 *out_ent;                       // ... as (cell, outer hit of the cell)
+    float *ck;                           // R-z slope key of each cell w.r.t. its outer hit (scratch)
     float2 *hk;                          // per hit: max sqrt(1+key^2), min gap of its incoming cells
+    int32_t *in_live;                    // per hit: live incoming cells
+    float2 *sk;                          // live incoming cells of each hit sorted by slope key:
+    int32_t *sci;                        //   (key, inner hit as int bits) and the cell index
     uint8_t *has_out;
     int32_t *maxlen;
     // outputs
@@ -86,6 +90,13 @@ struct Params {
 // ---------------------------------------------------------------- utilities
 __device__ __forceinline__ void set_flag(int32_t *counters, uint32_t f) {
     atomicOr(reinterpret_cast<unsigned int *>(counters + C_FLAGS), f);
+}
+
+// True when an earlier stage ran out of capacity in one of the mask's
+// outputs: this stage's inputs are incomplete, and it does nothing (the
+// caller reads the flags and reruns with larger buffers).
+__device__ __forceinline__ bool upstream_overflow(const Params &p, uint32_t mask) {
+    return (p.counters[C_FLAGS] & mask) != 0;
 }
 
 __device__ __forceinline__ long long grid_int(float v) {

@@ -2,11 +2,12 @@
 // sharing hit b are linked when the R-z alignment, dz, curvature and
 // beamspot predicates of b's region (barrel or endcap, Sec. 4.2) pass.
 //
-// One warp owns one middle hit b.  It stages the live cells ending on b in
-// shared memory once -- inner hit a, cell index and slope key -- and each
-// lane takes one live cell (b,c) starting on b (from the out-lists built
-// after the Fishbone) and scans the staged cells; the staged data are
-// shared-memory broadcasts reused by every outer cell of b.
+// One warp owns one middle hit b and each lane one live cell (b,c) starting
+// on b, taken from the out-list of b (with the outer hit c).  The live cells
+// ending on b were written by the Fishbone kernel sorted by their R-z slope
+// key relative to b, with their inner hits, so the candidates of a lane are a
+// contiguous run of that array, found by binary search (the warp's lanes
+// share the array through L1).
 //
 // The R-z cut is very tight, so it is first used as a window on the slope
 // key.  For a barrel b, with key = dz/dr of a segment,
@@ -14,26 +15,24 @@
 // and |X| <= tol |ac| <= tol (|ab| + |bc|) give
 //     |key_c - key_a| <= tol (sqrt(1+key_a^2)/dr_bc + sqrt(1+key_c^2)/dr_ab);
 // for a disk b the same holds with r and z exchanged.  With sqrt(1+key_a^2)
-// and 1/dr_ab bounded by their maximum over the cells ending on b (both
-// computed with the keys in the Fishbone kernel), every aligned candidate
-// falls in the window; the
-// few inside it take a float32 R-z test with an error bound and then the
-// exact predicate chain.
+// and 1/dr_ab bounded by their maximum over the cells ending on b, every
+// aligned candidate falls in the window; the run searched is the window
+// widened far beyond the rounding of the key differences, and inside it the
+// window test itself, a float32 R-z test with an error bound and then the
+// exact predicate chain decide.
 //
 // Each lane counts its accepted candidates and remembers the first few in a
 // small shared-memory queue, so the incoming edges of a cell are reserved
 // together and written contiguously (the depth-first search walks them
 // backwards); the edge range of a cell is stored at its out-list position.
-// Cells with incoming edges join the list the search starts from.  Hits with
-// more than kCaMax live incoming cells scan them in global memory.
+// Cells with incoming edges join the list the search starts from.
 #include "pt_common.cuh"
 #include "pt_kernels.cuh"
 
 namespace ptk {
 
 constexpr int kCaWarps = 4;
-constexpr int kCaWords = 8;
-constexpr int kCaMax = 32 * kCaWords;    // staged incoming cells per hit
+constexpr int kCaQueue = 8;         // accepted candidates remembered per lane
 
 // The full chain runs for the few candidates that pass the window and the
 // float R-z test; out of line so that the scan loop stays small.
@@ -73,54 +72,45 @@ __device__ __forceinline__ int warp_excl(int v, int lane, int &total) {
     return incl - v;
 }
 
-constexpr int kCaQueue = 8;     // accepted candidates remembered per lane
+// first position of s[0, n) whose key is >= lo (keys ascending)
+__device__ __forceinline__ int lower_key(const float2 *s, int n, float lo) {
+    int l = 0, h = n;
+    while (l < h) {
+        const int m = (l + h) >> 1;
+        if (__ldg(s + m).x < lo) l = m + 1;
+        else h = m;
+    }
+    return l;
+}
 
-__global__ void __launch_bounds__(32 * kCaWarps) k_connect(Params p) {
-    __shared__ float4 s_a[kCaWarps][kCaMax];
-    __shared__ float s_k[kCaWarps][kCaMax];
-    __shared__ int32_t s_c[kCaWarps][kCaMax];
-    __shared__ int16_t s_q[kCaWarps][kCaQueue][32];
+__global__ void __launch_bounds__(32 * kCaWarps, 6) k_connect(Params p) {
+    __shared__ int32_t s_q[kCaWarps][kCaQueue][32];
+    if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
     const int n_binned = p.bin_cnt[p.n_bins];
     for (int b = blockIdx.x * kCaWarps + w; b < n_binned; b += gridDim.x * kCaWarps) {
         const int o0 = p.out_off[b], nout = p.out_off[b + 1] - o0;
         if (nout == 0) continue;
-        int nin = p.in_cnt[b];
         const int64_t b0 = p.in_off[b];
-        if (b0 + nin > p.cap_cells) nin = 0;
+        int ns = p.in_live[b];
+        if (b0 + ns > p.cap_cells) ns = 0;
         const FHit B = load_hit(p.bh, b);
         const bool disk = p.layer[p.blayer[b]].kind == PT_LAYER_DISK;
         const pt_ca_cuts rg = p.region[disk ? 1 : 0];
         const float tol = p.region_tol[disk ? 1 : 0];
         const float2 hk = p.hk[b];
-        // stage the live incoming cells of b (dead cells carry a NaN key)
-        int ns = 0;
-        for (int j0 = 0; j0 < nin; j0 += 32) {
-            const int j = j0 + lane;
-            const float key = j < nin ? p.ck[b0 + j] : 0.f;
-            const bool live = j < nin && key == key;
-            const unsigned m = __ballot_sync(0xffffffffu, live);
-            if (live) {
-                const int slot = ns + __popc(m & ((1u << lane) - 1u));
-                if (slot < kCaMax) {
-                    s_c[w][slot] = (int32_t)(b0 + j);
-                    s_k[w][slot] = key;
-                    s_a[w][slot] = __ldg(p.bh + p.cell_inner[b0 + j]);
-                }
-            }
-            ns += __popc(m);
-        }
-        __syncwarp();
-        const bool staged = ns <= kCaMax;
+        const float2 *S = p.sk + b0;
         for (int q0 = 0; q0 < nout; q0 += 32) {
             const int q = q0 + lane;
             const bool act = q < nout;
-            int co = 0;
+            int co = 0, r0 = 0, r1 = 0;
             FHit C = B;
-            float key_c = 0.f, wdt = -1.f;
+            float key_c = 0.f, wdt = -1.f, hi = 0.f;
             if (act) {
-                co = p.out_idx[o0 + q];
-                C = load_hit(p.bh, p.cell_outer[co]);
+                const int2 ent = p.out_ent[o0 + q];
+                co = ent.x;
+                C = load_hit(p.bh, ent.y);
                 const float dr = C.r - B.r, dz = C.z - B.z;
                 const float num = disk ? dr : dz, den = disk ? dz : dr;
                 key_c = den != 0.f ? num / den : __int_as_float(0x7f800000);
@@ -128,16 +118,22 @@ __global__ void __launch_bounds__(32 * kCaWarps) k_connect(Params p) {
                 wdt = tol * (hk.x / fabsf(den) + sqrtf(1.0f + key_c * key_c) / hk.y);
                 wdt = wdt * (1.0f + 1e-5f) + 1e-5f * (1.0f + fabsf(key_c) + hk.x);
                 if (!(wdt == wdt) || den == 0.f) wdt = __int_as_float(0x7f800000);
+                // keys passing the window test lie in [lo, hi]
+                const float sl = (fabsf(key_c) + wdt) * 9.5367431640625e-7f;
+                const float lo = key_c - wdt - sl;
+                hi = key_c + wdt + sl;
+                if (!(hi == hi)) hi = __int_as_float(0x7f800000);
+                r0 = lo > -3.4e38f ? lower_key(S, ns, lo) : 0;
+                r1 = ns;
             }
             // count accepted candidates; remember the first kCaQueue
             int mine = 0;
-            const int nc = act ? (staged ? ns : nin) : 0;
-            for (int k = 0; k < nc; k++) {
-                const float key = staged ? s_k[w][k] : p.ck[b0 + k];
-                if (!(fabsf(key - key_c) <= wdt)) continue;
-                const float4 a = staged ? s_a[w][k] : __ldg(p.bh + p.cell_inner[b0 + k]);
-                if (connects(p, a, B, C, rg)) {
-                    if (mine < kCaQueue) s_q[w][mine][lane] = (int16_t)k;
+            for (int r = r0; r < r1; r++) {
+                const float2 e = __ldg(S + r);
+                if (e.x > hi) break;
+                if (!(fabsf(e.x - key_c) <= wdt)) continue;
+                if (connects(p, __ldg(p.bh + __float_as_int(e.y)), B, C, rg)) {
+                    if (mine < kCaQueue) s_q[w][mine][lane] = r;
                     mine++;
                 }
             }
@@ -148,8 +144,7 @@ __global__ void __launch_bounds__(32 * kCaWarps) k_connect(Params p) {
             base = __shfl_sync(0xffffffffu, base, 0) + excl;
             if (mine > 0 && mine <= kCaQueue) {
                 for (int t = 0; t < mine; t++) {
-                    const int k = s_q[w][t][lane];
-                    const int ci = staged ? s_c[w][k] : (int32_t)(b0 + k);
+                    const int ci = p.sci[b0 + s_q[w][t][lane]];
                     if (base + t < p.cap_edges) {
                         p.edge_src[base + t] = ci;
                         p.edge_dst[base + t] = co;
@@ -158,12 +153,12 @@ __global__ void __launch_bounds__(32 * kCaWarps) k_connect(Params p) {
                 }
             } else if (mine > kCaQueue) {   // rare: scan again to write all
                 int64_t e = base;
-                for (int k = 0; k < nc; k++) {
-                    const float key = staged ? s_k[w][k] : p.ck[b0 + k];
-                    if (!(fabsf(key - key_c) <= wdt)) continue;
-                    const float4 a = staged ? s_a[w][k] : __ldg(p.bh + p.cell_inner[b0 + k]);
-                    if (connects(p, a, B, C, rg)) {
-                        const int ci = staged ? s_c[w][k] : (int32_t)(b0 + k);
+                for (int r = r0; r < r1; r++) {
+                    const float2 v = __ldg(S + r);
+                    if (v.x > hi) break;
+                    if (!(fabsf(v.x - key_c) <= wdt)) continue;
+                    if (connects(p, __ldg(p.bh + __float_as_int(v.y)), B, C, rg)) {
+                        const int ci = p.sci[b0 + r];
                         if (e < p.cap_edges) {
                             p.edge_src[e] = ci;
                             p.edge_dst[e] = co;
@@ -177,7 +172,7 @@ __global__ void __launch_bounds__(32 * kCaWarps) k_connect(Params p) {
             const unsigned lm = __ballot_sync(0xffffffffu, mine > 0);
             int lb = 0;
             if (lane == 0 && lm) lb = atomicAdd(p.counters + C_LEAVES, __popc(lm));
-            lb = __shfl_sync(0xffffffffu, lb, 0) + __popc(lm & ((1u << lane) - 1u));
+            lb = __shfl_sync(0xffffffffu, lb, 0) + __popc(lm & below);
             if (act) {
                 // incoming-edge range, stored at the cell's out-list position
                 // (coalesced); the search finds it through the cell's rank
@@ -187,7 +182,6 @@ __global__ void __launch_bounds__(32 * kCaWarps) k_connect(Params p) {
             }
             __syncwarp();
         }
-        __syncwarp();
     }
 }
 

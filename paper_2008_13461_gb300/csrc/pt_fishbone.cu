@@ -25,11 +25,11 @@
 // at a time; beyond the large warps' capacity a plain pairwise loop over
 // global memory is used.
 //
-// The same pass writes, for the CA connection, each cell's R-z slope key
-// relative to o (NaN for dead cells) and per hit the bounds the slope window
-// needs (taken over all cells of o, a superset of the live ones, so the
-// window only widens), and ranks every live cell in the out-list of its
-// inner hit.
+// The same pass prepares the CA connection: it writes the live cells of o
+// sorted by their R-z slope key relative to o (with the inner hit and the
+// cell index), per hit the bounds the slope window needs (taken over all
+// cells of o, a superset of the live ones, so the window only widens), and
+// ranks every live cell in the out-list of its inner hit.
 #include "pt_common.cuh"
 #include "pt_kernels.cuh"
 
@@ -217,18 +217,106 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
     }
     __syncwarp();
 
-    // pass 2: dead cells get a NaN key; live cells join the out-list of
-    // their inner hit (rank by atomics)
+    // pass 2: live cells join the out-list of their inner hit (rank by
+    // atomics) and are written sorted by slope key for the CA connection
     int alive = 0;
-    for (int j = lane; j < n; j += 32) {
-        const bool dead = in_smem ? sm.dead[w][j] != 0 : p.cell_alive[b + j] == 0;
-        if (dead) {
-            if (in_smem) p.cell_alive[b + j] = 0;
-            p.ck[b + j] = __int_as_float(0x7fc00000);
-        } else {
+    if (in_smem) {
+        // slope key and inner hit of each live cell (the records are free)
+        float smin = __int_as_float(0x7f800000), smax = -smin;
+        for (int j = lane; j < n; j += 32) {
+            if (sm.dead[w][j]) {
+                p.cell_alive[b + j] = 0;
+                continue;
+            }
+            const float key = p.ck[b + j];
+            const int ii = p.cell_inner[b + j];
+            sm.rec[w][j] = make_float4(key, __int_as_float(ii), 0.f, 0.f);
+            if (fabsf(key) <= 3.4e38f) {
+                smin = fminf(smin, key);
+                smax = fmaxf(smax, key);
+            }
             alive++;
-            p.cell_rank[b + j] = atomicAdd(p.out_off + p.cell_inner[b + j], 1);
+            p.cell_rank[b + j] = atomicAdd(p.out_off + ii, 1);
         }
+        int nl = alive;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            nl += __shfl_xor_sync(0xffffffffu, nl, d);
+            smin = fminf(smin, __shfl_xor_sync(0xffffffffu, smin, d));
+            smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, d));
+        }
+        // counting sort into about one bucket per cell, then the exact rank
+        // inside the bucket: key, ties by position
+        const int nb = min(NB, max(32, 1 << (32 - __clz(max(nl, 1) - 1))));
+        const float span = fmaxf(smax - smin, fmaxf(fabsf(smin), fabsf(smax)) * 1e-6f);
+        const float iw = span > 0.f && span <= 3.4e38f ? (float)nb / span : 0.f;
+        for (int q = lane; q < nb; q += 32) sm.pos[w][q] = 0;
+        __syncwarp();
+        for (int j = lane; j < n; j += 32) {
+            if (sm.dead[w][j]) continue;
+            const int bk = min(max((int)((sm.rec[w][j].x - smin) * iw), 0), nb - 1);
+            sm.meta[w][j] = bk;
+            atomicAdd(&sm.pos[w][bk], 1);
+        }
+        __syncwarp();
+        {
+            const int per = nb >> 5;
+            int sum = 0;
+            for (int q = 0; q < per; q++) sum += sm.pos[w][lane * per + q];
+            int incl = sum;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += t;
+            }
+            int run = incl - sum;
+            for (int q = 0; q < per; q++) {
+                const int v = sm.pos[w][lane * per + q];
+                sm.pos[w][lane * per + q] = run;
+                run += v;
+            }
+        }
+        __syncwarp();
+        for (int j = lane; j < n; j += 32)
+            if (!sm.dead[w][j]) sm.idx[w][atomicAdd(&sm.pos[w][sm.meta[w][j]], 1)] = (int16_t)j;
+        __syncwarp();
+        for (int j = lane; j < n; j += 32) {
+            if (sm.dead[w][j]) continue;
+            const float4 r = sm.rec[w][j];
+            const int bk = sm.meta[w][j];
+            const int e = sm.pos[w][bk];
+            int rank = bk > 0 ? sm.pos[w][bk - 1] : 0;
+            for (int q = rank; q < e; q++) {
+                const int i = sm.idx[w][q];
+                const float ki = sm.rec[w][i].x;
+                rank += ki < r.x || (ki == r.x && i < j);
+            }
+            p.sk[b + rank] = make_float2(r.x, r.y);
+            p.sci[b + rank] = (int32_t)(b + j);
+        }
+        if (lane == 0) p.in_live[o] = nl;
+    } else {
+        // (only outer hits with very many cells) rank by direct comparison
+        int nl = 0;
+        for (int j = lane; j < n; j += 32) {
+            if (!p.cell_alive[b + j]) continue;
+            const float key = p.ck[b + j];
+            const int ii = p.cell_inner[b + j];
+            int rank = 0;
+            for (int i = 0; i < n; i++) {
+                if (!p.cell_alive[b + i]) continue;
+                const float ki = p.ck[b + i];
+                rank += ki < key || (ki == key && i < j);
+            }
+            p.sk[b + rank] = make_float2(key, __int_as_float(ii));
+            p.sci[b + rank] = (int32_t)(b + j);
+            alive++;
+            p.cell_rank[b + j] = atomicAdd(p.out_off + ii, 1);
+        }
+        nl = alive;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) nl += __shfl_xor_sync(0xffffffffu, nl, d);
+        if (lane == 0) p.in_live[o] = nl;
     }
     __syncwarp();
     return alive;
@@ -246,6 +334,7 @@ __device__ __forceinline__ void add_alive(const Params &p, int v) {
 template <int W, int M, int NB, int kMinBlocks>
 __global__ void __launch_bounds__(32 * W, kMinBlocks) k_fishbone_small(Params p, float unit_thr, float du) {
     __shared__ FbSmem<W, M, NB> sm;
+    if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int my_alive = 0;
     const int n_binned = p.bin_cnt[p.n_bins];
@@ -285,6 +374,7 @@ __global__ void __launch_bounds__(32 * W, kMinBlocks) k_fishbone_small(Params p,
 template <int W, int M, int NB>
 __global__ void __launch_bounds__(32 * W) k_fishbone_large(Params p, float unit_thr, float du) {
     __shared__ FbSmem<W, M, NB> sm;
+    if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int my_alive = 0;
     const int n_list = p.counters[C_FB_BIG];
@@ -309,12 +399,13 @@ void launch_fishbone(const Params &p, float unit_thr, float du, int grid, cudaSt
 // Out-lists: live cells grouped by their inner hit (CSR), from the ranks
 // taken in the Fishbone kernel and the scanned per-hit counts.
 __global__ void __launch_bounds__(kThreads) k_out_fill(Params p) {
+    if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int64_t n_cells = min((int64_t)p.counters[C_CELLS], p.cap_cells);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += stride) {
         if (!p.cell_alive[c]) continue;
         const int i = p.cell_inner[c];
-        p.out_idx[p.out_off[i] + p.cell_rank[c]] = (int32_t)c;
+        p.out_ent[p.out_off[i] + p.cell_rank[c]] = make_int2((int32_t)c, p.cell_outer[c]);
     }
 }
 

@@ -19,6 +19,7 @@ namespace ptk {
 __device__ __forceinline__ bool root_layer(int L) { return L == 0 || L == 1 || L == 4 || L == 7; }
 
 __global__ void __launch_bounds__(kThreads) k_dfs(Params p) {
+    if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int64_t n_list = min((int64_t)p.counters[C_LEAVES], p.cap_cells);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_list; k += stride) {
