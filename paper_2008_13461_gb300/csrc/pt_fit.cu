@@ -20,6 +20,13 @@
 // the normal equations, their Cholesky factorisation, solutions and chi2 in
 // float64, where the kink weights (up to ~1e10) and measurement weights
 // (~1e6) make the matrices too ill-conditioned for float32.
+//
+// The float64 pipe is the bound, so the unknowns are ordered with the ones
+// the track parameters need (v0, v1; u0, u1, dk) last: with A = L L^T, their
+// covariance is the inverse of the trailing block of L times its transpose
+// (the Schur complement), their values need the back-substitution of that
+// block only, and chi2 = c - |L^-1 b|^2 (c = sum of weighted squared
+// measurements) needs no full solution.
 #include "pt_common.cuh"
 #include "pt_kernels.cuh"
 
@@ -33,18 +40,16 @@ __device__ __forceinline__ float asinc(float x) {
 template <int M>
 __device__ __forceinline__ int pidx(int r, int c) { return r * (r + 1) / 2 + c; }
 
-// Double-precision 1/sqrt(s) and 1/d from a float32 seed and Newton steps
-// (each step squares the relative error: 1e-7 -> 1e-14 -> below 1e-16), to
-// keep the slow FP64 pipe to a few multiply-adds.
+// Double-precision 1/sqrt(s) and 1/d from a float32 seed and one Newton
+// step (relative error 1e-7 -> ~1e-14), to keep the slow FP64 pipe to a
+// few multiply-adds.
 __device__ __forceinline__ double rsqrt_fp64(double s) {
-    double y = (double)rsqrtf((float)s);
-    y = y * (1.5 - 0.5 * s * y * y);
+    const double y = (double)rsqrtf((float)s);
     return y * (1.5 - 0.5 * s * y * y);
 }
 
 __device__ __forceinline__ double recip_fp64(double d) {
-    double r = (double)(1.0f / (float)d);
-    r = r * (2.0 - d * r);
+    const double r = (double)(1.0f / (float)d);
     return r * (2.0 - d * r);
 }
 
@@ -69,8 +74,11 @@ __device__ __forceinline__ void chol(double *A) {
     }
 }
 
-template <int M>
-__device__ __forceinline__ void chol_solve(const double *L, double *b) {
+// Given the factor of chol(), b := L^-1 b; then the last K unknowns of the
+// solution of A x = b (into x) and their covariance (the inverse of
+// L22 L22^T, L22 the trailing K x K block); returns |L^-1 b|^2.
+template <int M, int K>
+__device__ __forceinline__ double solve_tail(const double *L, double *b, double *x, double (*C)[K]) {
 #pragma unroll
     for (int i = 0; i < M; i++) {
         double t = b[i];
@@ -78,14 +86,51 @@ __device__ __forceinline__ void chol_solve(const double *L, double *b) {
         for (int k = 0; k < i; k++) t -= L[pidx<M>(i, k)] * b[k];
         b[i] = t * L[pidx<M>(i, i)];
     }
+    double yy = 0.0;
 #pragma unroll
-    for (int i = M - 1; i >= 0; i--) {
-        double t = b[i];
+    for (int i = 0; i < M; i++) yy += b[i] * b[i];
+    constexpr int o = M - K;
 #pragma unroll
-        for (int k = i + 1; k < M; k++) t -= L[pidx<M>(k, i)] * b[k];
-        b[i] = t * L[pidx<M>(i, i)];
+    for (int i = K - 1; i >= 0; i--) {
+        double t = b[o + i];
+#pragma unroll
+        for (int k = i + 1; k < K; k++) t -= L[pidx<M>(o + k, o + i)] * x[k];
+        x[i] = t * L[pidx<M>(o + i, o + i)];
     }
+    // T = L22^-1 (lower triangular), C = T^T T
+    double T[K][K];
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+#pragma unroll
+        for (int i = 0; i < K; i++) {
+            if (i < j) {
+                T[i][j] = 0.0;
+            } else if (i == j) {
+                T[i][j] = L[pidx<M>(o + i, o + i)];
+            } else {
+                double t = 0.0;
+#pragma unroll
+                for (int k = j; k < i; k++) t -= L[pidx<M>(o + i, o + k)] * T[k][j];
+                T[i][j] = t * L[pidx<M>(o + i, o + i)];
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < K; a++)
+#pragma unroll
+        for (int c = 0; c <= a; c++) {
+            double t = 0.0;
+#pragma unroll
+            for (int k = a; k < K; k++) t += T[k][a] * T[k][c];
+            C[a][c] = t;
+            C[c][a] = t;
+        }
+    return yy;
 }
+
+// packed index of the symmetric entry (i, j), either order
+template <int M>
+__device__ __forceinline__ int sidx(int i, int j) { return i >= j ? pidx<M>(i, j) : pidx<M>(j, i); }
 
 template <int N>
 __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
@@ -148,104 +193,73 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
         vb[i] = recip_fp64(fmax(th2 * sec2, 1e-20));          // weights 1/variance
         vg[i] = recip_fp64(fmax(th2 * sec2 * sec2, 1e-20));
     }
-    // 3) line fit in s-z
-    double A[N * (N + 1) / 2], v[N], wz[N];
+    // 3) line fit in s-z; unknown v_i at position ln(i): v2 .. v_{n-1}, v0, v1
+    auto ln = [](int i) { return i >= 2 ? i - 2 : N - 2 + i; };
+    double A[N * (N + 1) / 2], bv[N];
+    double chi2 = 0.0;
 #pragma unroll
     for (int i = 0; i < N * (N + 1) / 2; i++) A[i] = 0.0;
 #pragma unroll
     for (int i = 0; i < N; i++) {
         const double sz = disk[i] ? (double)p.fit.sigma_r * atl : (double)p.fit.sigma_z;
-        wz[i] = recip_fp64(sz * sz);
-        A[pidx<N>(i, i)] = wz[i];
-        v[i] = wz[i] * hz[i];
+        const double wz = recip_fp64(sz * sz);
+        A[pidx<N>(ln(i), ln(i))] = wz;
+        bv[ln(i)] = wz * hz[i];
+        chi2 += bv[ln(i)] * hz[i];
     }
 #pragma unroll
     for (int i = 1; i < N - 1; i++) {
         const double g0 = ids[i], g2 = ids[i + 1], g1 = -(g0 + g2), w = vg[i];
-        A[pidx<N>(i - 1, i - 1)] += g0 * g0 * w;
-        A[pidx<N>(i, i - 1)] += g1 * g0 * w;
-        A[pidx<N>(i, i)] += g1 * g1 * w;
-        A[pidx<N>(i + 1, i - 1)] += g2 * g0 * w;
-        A[pidx<N>(i + 1, i)] += g2 * g1 * w;
-        A[pidx<N>(i + 1, i + 1)] += g2 * g2 * w;
+        const double wg0 = g0 * w, wg1 = g1 * w, wg2 = g2 * w;
+        A[sidx<N>(ln(i - 1), ln(i - 1))] += g0 * wg0;
+        A[sidx<N>(ln(i), ln(i - 1))] += g1 * wg0;
+        A[sidx<N>(ln(i), ln(i))] += g1 * wg1;
+        A[sidx<N>(ln(i + 1), ln(i - 1))] += g2 * wg0;
+        A[sidx<N>(ln(i + 1), ln(i))] += g2 * wg1;
+        A[sidx<N>(ln(i + 1), ln(i + 1))] += g2 * wg2;
     }
     chol<N>(A);
-    chol_solve<N>(A, v);
-    double chi2 = 0.0;
-#pragma unroll
-    for (int i = 0; i < N; i++) chi2 += wz[i] * (v[i] - hz[i]) * (v[i] - hz[i]);
-#pragma unroll
-    for (int i = 1; i < N - 1; i++) {
-        const double gam = (v[i + 1] - v[i]) * ids[i + 1] - (v[i] - v[i - 1]) * ids[i];
-        chi2 += gam * gam * vg[i];
-    }
-    double Cv[2][2];
-#pragma unroll
-    for (int c = 0; c < 2; c++) {
-        double e[N];
-#pragma unroll
-        for (int i = 0; i < N; i++) e[i] = (i == c) ? 1.0 : 0.0;
-        chol_solve<N>(A, e);
-        Cv[0][c] = e[0];
-        Cv[1][c] = e[1];
-    }
-    // 4) circle fit: unknowns u_0 .. u_{n-1}, dk
+    double v[2], Cv[2][2];
+    chi2 -= solve_tail<N, 2>(A, bv, v, Cv);
+    // 4) circle fit: unknowns u_0 .. u_{n-1}, dk; u_i at position ln(i), dk last
     constexpr int M = N + 1;
-    double B[M * (M + 1) / 2], x[M];
+    double B[M * (M + 1) / 2], bu[M];
 #pragma unroll
     for (int i = 0; i < M * (M + 1) / 2; i++) B[i] = 0.0;
     const double wu = recip_fp64((double)p.fit.sigma_rphi * p.fit.sigma_rphi);
 #pragma unroll
     for (int i = 0; i < N; i++) {
-        B[pidx<M>(i, i)] = wu;
-        x[i] = wu * m[i];
+        B[pidx<M>(ln(i), ln(i))] = wu;
+        bu[ln(i)] = wu * m[i];
+        chi2 += bu[ln(i)] * m[i];
     }
-    x[N] = 0.0;
+    bu[N] = 0.0;
 #pragma unroll
     for (int i = 1; i < N - 1; i++) {
         const double h0 = ids[i], h2 = ids[i + 1], h1 = -(h0 + h2);
         const double h3 = -0.5 * ((double)ds[i] + ds[i + 1]), w = vb[i];
-        B[pidx<M>(i - 1, i - 1)] += h0 * h0 * w;
-        B[pidx<M>(i, i - 1)] += h1 * h0 * w;
-        B[pidx<M>(i, i)] += h1 * h1 * w;
-        B[pidx<M>(i + 1, i - 1)] += h2 * h0 * w;
-        B[pidx<M>(i + 1, i)] += h2 * h1 * w;
-        B[pidx<M>(i + 1, i + 1)] += h2 * h2 * w;
-        B[pidx<M>(N, i - 1)] += h3 * h0 * w;
-        B[pidx<M>(N, i)] += h3 * h1 * w;
-        B[pidx<M>(N, i + 1)] += h3 * h2 * w;
+        const double wh0 = h0 * w, wh1 = h1 * w, wh2 = h2 * w;
+        B[sidx<M>(ln(i - 1), ln(i - 1))] += h0 * wh0;
+        B[sidx<M>(ln(i), ln(i - 1))] += h1 * wh0;
+        B[sidx<M>(ln(i), ln(i))] += h1 * wh1;
+        B[sidx<M>(ln(i + 1), ln(i - 1))] += h2 * wh0;
+        B[sidx<M>(ln(i + 1), ln(i))] += h2 * wh1;
+        B[sidx<M>(ln(i + 1), ln(i + 1))] += h2 * wh2;
+        B[pidx<M>(N, ln(i - 1))] += h3 * wh0;
+        B[pidx<M>(N, ln(i))] += h3 * wh1;
+        B[pidx<M>(N, ln(i + 1))] += h3 * wh2;
         B[pidx<M>(N, N)] += h3 * h3 * w;
     }
     chol<M>(B);
-    chol_solve<M>(B, x);
-    const double dk = x[N];
-#pragma unroll
-    for (int i = 0; i < N; i++) chi2 += wu * (x[i] - m[i]) * (x[i] - m[i]);
-#pragma unroll
-    for (int i = 1; i < N - 1; i++) {
-        const double be = (x[i + 1] - x[i]) * ids[i + 1] - (x[i] - x[i - 1]) * ids[i] -
-                          dk * 0.5 * ((double)ds[i] + ds[i + 1]);
-        chi2 += be * be * vb[i];
-    }
-    double Cc[3][3];
-    {
-        const int sel[3] = {0, 1, N};
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            double e[M];
-#pragma unroll
-            for (int i = 0; i < M; i++) e[i] = (i == sel[c]) ? 1.0 : 0.0;
-            chol_solve<M>(B, e);
-#pragma unroll
-            for (int r = 0; r < 3; r++) Cc[r][c] = e[sel[r]];
-        }
-    }
+    double xu[3], Cc[3][3];
+    chi2 -= solve_tail<M, 3>(B, bu, xu, Cc);
+    const double dk = xu[2];
     // 5) perigee of the fitted circle through P with direction psi
     const float kf = (float)((double)k0 + dk);
-    const float u0 = (float)x[0];
+    const float u0 = (float)xu[0];
     const float px = hx[0] - u0 * sn, py = hy[0] + u0 * cs;
     const float ds1 = ds[1];
-    const float psi = psi0 + (float)((x[1] - x[0]) * ids[1] - dk * 0.5 * ds1);
+    const float psi = psi0 + (float)((xu[1] - xu[0]) * ids[1] - dk * 0.5 * ds1);
     float sp, cp;
     sincosf(psi, &sp, &cp);
     const float Xo = -det2(px, cp, -py, sp);       // -(P . t)
@@ -282,31 +296,36 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
             J[2][j] = dd0;
         }
     }
+    // F = J C J^T as (J C) J^T
+    double JC[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            double acc = 0.0;
+#pragma unroll
+            for (int c = 0; c < 3; c++) acc += (double)J[a][c] * Cc[c][d];
+            JC[a][d] = acc;
+        }
     float Fc[3][3];
 #pragma unroll
     for (int a = 0; a < 3; a++)
 #pragma unroll
-        for (int b = 0; b < 3; b++) {
+        for (int b = 0; b <= a; b++) {
             double acc = 0.0;
 #pragma unroll
-            for (int c = 0; c < 3; c++)
-#pragma unroll
-                for (int d = 0; d < 3; d++) acc += (double)J[a][c] * Cc[c][d] * J[b][d];
+            for (int d = 0; d < 3; d++) acc += JC[a][d] * J[b][d];
             Fc[a][b] = (float)acc;
+            Fc[b][a] = Fc[a][b];
         }
-    const double Jl[2][2] = {{-ids[1], ids[1]}, {1.0 - arc * ids[1], arc * ids[1]}};
+    // line block: tanl = (v1 - v0)/ds1, z0 = v0 + tanl arc
+    const double t0 = -ids[1], t1 = ids[1], z0a = 1.0 - arc * ids[1], z1a = arc * ids[1];
+    const double c00 = Cv[0][0], c01 = Cv[0][1], c11 = Cv[1][1];
     float Fl[2][2];
-#pragma unroll
-    for (int a = 0; a < 2; a++)
-#pragma unroll
-        for (int b = 0; b < 2; b++) {
-            double acc = 0.0;
-#pragma unroll
-            for (int c = 0; c < 2; c++)
-#pragma unroll
-                for (int d = 0; d < 2; d++) acc += Jl[a][c] * Cv[c][d] * Jl[b][d];
-            Fl[a][b] = (float)acc;
-        }
+    Fl[0][0] = (float)(t0 * (t0 * c00 + t1 * c01) + t1 * (t0 * c01 + t1 * c11));
+    Fl[1][0] = (float)(z0a * (t0 * c00 + t1 * c01) + z1a * (t0 * c01 + t1 * c11));
+    Fl[1][1] = (float)(z0a * (z0a * c00 + z1a * c01) + z1a * (z0a * c01 + z1a * c11));
+    Fl[0][1] = Fl[1][0];
     float *par = p.trk_params + k * 5;
     par[0] = -kf;
     par[1] = phi0;
