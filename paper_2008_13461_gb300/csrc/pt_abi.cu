@@ -55,9 +55,6 @@ bool layout(const pt_hits *h, const pt_config *cfg, WsLayout &L) {
     L.in_cnt = take(4 * nh);
     L.in_live = take(4 * nh);
     L.hk = take(8 * nh);
-    L.out_off = take(4 * (nh + 1));
-    L.cell_rank = take(4 * nc);
-    L.out_ent = take(8 * nc);
     L.ck = take(4 * nc);
     L.sk = take(8 * nc);
     L.sci = take(4 * nc);
@@ -173,9 +170,6 @@ Params make_params(void *ws, const WsLayout &L, const pt_hits *h, const pt_confi
     p.in_off = (int32_t *)(w + L.in_off);
     p.in_cnt = (int32_t *)(w + L.in_cnt);
     p.hk = (float2 *)(w + L.hk);
-    p.out_off = (int32_t *)(w + L.out_off);
-    p.cell_rank = (int32_t *)(w + L.cell_rank);
-    p.out_ent = (int2 *)(w + L.out_ent);
     p.ck = (float *)(w + L.ck);
     p.sk = (float2 *)(w + L.sk);
     p.sci = (int32_t *)(w + L.sci);
@@ -252,8 +246,6 @@ pt_status pt_build_doublets(void *ws, size_t ws_bytes, const pt_hits *hits, cons
     if (cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * kCounters, s) != cudaSuccess) return PT_ERR_CUDA;
     if (cudaMemsetAsync(p.bin_cnt, 0, sizeof(int32_t) * (size_t)(L.n_bins + 1), s) != cudaSuccess)
         return PT_ERR_CUDA;
-    if (cudaMemsetAsync(p.out_off, 0, sizeof(int32_t) * ((size_t)hits->n_hits + 1), s) != cudaSuccess)
-        return PT_ERR_CUDA;
     if (cudaMemsetAsync(p.in_live, 0, sizeof(int32_t) * (size_t)hits->n_hits, s) != cudaSuccess) return PT_ERR_CUDA;
     const int grid = grid_for(cfg);
     launch_binning(p, grid, s);
@@ -263,7 +255,6 @@ pt_status pt_build_doublets(void *ws, size_t ws_bytes, const pt_hits *hits, cons
     // at least that wide, with room for the rounding of the bucket index.
     const double dmax = sqrt((double)cfg->cuts.fishbone_eps2) * 1.5707963267948966 + 4e-6;
     launch_fishbone(p, (float)(dmax * dmax), (float)(dmax * 1.01 + 1e-5), grid, s);
-    launch_out_lists(p, grid, s);
     return launched();
 }
 

@@ -26,7 +26,7 @@ enum Counter {
 // Byte offsets of every workspace array (all 256-byte aligned).
 struct WsLayout {
     size_t counters, bin_cnt, scan_part, hit_bin, hit_rank;
-    size_t bh, blayer, bev, perm, in_off, in_cnt, in_live, hk, ck, sk, sci, leaf_list, out_off, cell_rank, out_ent;
+    size_t bh, blayer, bev, perm, in_off, in_cnt, in_live, hk, ck, sk, sci, leaf_list;
     size_t edge_rng, has_out, maxlen;
     size_t total;
     int64_t n_bins;        // events * layers * phi bins * t bins
@@ -47,10 +47,8 @@ struct Params {
     int8_t *blayer;
     int32_t *bev, *perm, *in_off, *in_cnt;
     int32_t *fb_big;                     // outer hits with many cells (reuses hit_rank after binning)
-    int2 *edge_rng;                      // per out-list position: (first edge, count)
+    int2 *edge_rng;                      // per cell: (first incoming edge, count)
     int32_t *leaf_list;
-    int32_t *out_off, *cell_rank;        // live cells grouped by inner hit (CSR) ...
-    int2 *out_ent;                       // ... as (cell, outer hit of the cell)
     float *ck;                           // R-z slope key of each cell w.r.t. its outer hit (scratch)
     float2 *hk;                          // per hit: max sqrt(1+key^2), min gap of its incoming cells
     int32_t *in_live;                    // per hit: live incoming cells

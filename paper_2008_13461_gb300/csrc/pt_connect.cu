@@ -2,12 +2,12 @@
 // sharing hit b are linked when the R-z alignment, dz, curvature and
 // beamspot predicates of b's region (barrel or endcap, Sec. 4.2) pass.
 //
-// One warp owns one middle hit b and each lane one live cell (b,c) starting
-// on b, taken from the out-list of b (with the outer hit c).  The live cells
-// ending on b were written by the Fishbone kernel sorted by their R-z slope
-// key relative to b, with their inner hits, so the candidates of a lane are a
-// contiguous run of that array, found by binary search (the warp's lanes
-// share the array through L1).
+// One thread per live cell (b,c), in cell order (cells are grouped by their
+// outer hit c, so the threads of a warp work on neighbouring middle hits).
+// The live cells ending on b were written by the Fishbone kernel sorted by
+// their R-z slope key relative to b, with their inner hits, so the
+// candidates (a,b) of a cell are a contiguous run of that array, found by
+// binary search (the runs of neighbouring hits stay in L2).
 //
 // The R-z cut is very tight, so it is first used as a window on the slope
 // key.  For a barrel b, with key = dz/dr of a segment,
@@ -21,18 +21,20 @@
 // window test itself, a float32 R-z test with an error bound and then the
 // exact predicate chain decide.
 //
-// Each lane counts its accepted candidates and remembers the first few in a
-// small shared-memory queue, so the incoming edges of a cell are reserved
-// together and written contiguously (the depth-first search walks them
-// backwards); the edge range of a cell is stored at its out-list position.
-// Cells with incoming edges join the list the search starts from.
+// The incoming edges of a cell are written contiguously (the depth-first
+// search walks them backwards from the cell's edge range).  A warp reserves
+// the edges of 128 consecutive cells with one atomic; each cell remembers
+// its first few accepted candidates in shared memory, and a cell with more
+// (rare) scans again to write them all.  Cells with incoming edges join the
+// list the search starts from.
 #include "pt_common.cuh"
 #include "pt_kernels.cuh"
 
 namespace ptk {
 
 constexpr int kCaWarps = 4;
-constexpr int kCaQueue = 8;         // accepted candidates remembered per lane
+constexpr int kCaQueue = 8;         // accepted candidates remembered per cell
+constexpr int kCaChunk = 4;         // rounds of 32 cells per edge reservation
 
 // The full chain runs for the few candidates that pass the window and the
 // float R-z test; out of line so that the scan loop stays small.
@@ -83,105 +85,110 @@ __device__ __forceinline__ int lower_key(const float2 *s, int n, float lo) {
     return l;
 }
 
+// Every inner cell (a,b) connecting to the live cell x = (b,c), in key
+// order: emit(t, i) for the t-th one, i its index in the sorted arrays.
+// Returns their number.
+template <class Emit>
+__device__ __forceinline__ int scan_cell(const Params &p, int x, Emit &&emit) {
+    const int b = p.cell_inner[x], c = p.cell_outer[x];
+    const int64_t b0 = p.in_off[b];
+    int ns = p.in_live[b];
+    if (b0 + ns > p.cap_cells) ns = 0;
+    if (ns == 0) return 0;
+    const FHit B = load_hit(p.bh, b), C = load_hit(p.bh, c);
+    const bool disk = p.layer[p.blayer[b]].kind == PT_LAYER_DISK;
+    const pt_ca_cuts rg = p.region[disk ? 1 : 0];
+    const float tol = p.region_tol[disk ? 1 : 0];
+    const float2 hk = p.hk[b];
+    const float dr = C.r - B.r, dz = C.z - B.z;
+    const float num = disk ? dr : dz, den = disk ? dz : dr;
+    const float key_c = den != 0.f ? num / den : __int_as_float(0x7f800000);
+    // window half-width, widened for float32 rounding of the keys
+    float wdt = tol * (hk.x / fabsf(den) + sqrtf(1.0f + key_c * key_c) / hk.y);
+    wdt = wdt * (1.0f + 1e-5f) + 1e-5f * (1.0f + fabsf(key_c) + hk.x);
+    if (!(wdt == wdt) || den == 0.f) wdt = __int_as_float(0x7f800000);
+    // keys passing the window test lie in [lo, hi]
+    const float sl = (fabsf(key_c) + wdt) * 9.5367431640625e-7f;
+    const float lo = key_c - wdt - sl;
+    float hi = key_c + wdt + sl;
+    if (!(hi == hi)) hi = __int_as_float(0x7f800000);
+    const float2 *S = p.sk + b0;
+    int n = 0;
+    for (int r = lo > -3.4e38f ? lower_key(S, ns, lo) : 0; r < ns; r++) {
+        const float2 e = __ldg(S + r);
+        if (e.x > hi) break;
+        if (!(fabsf(e.x - key_c) <= wdt)) continue;
+        if (connects(p, __ldg(p.bh + __float_as_int(e.y)), B, C, rg)) emit(n++, b0 + r);
+    }
+    return n;
+}
+
 __global__ void __launch_bounds__(32 * kCaWarps, 6) k_connect(Params p) {
-    __shared__ int32_t s_q[kCaWarps][kCaQueue][32];
+    __shared__ int32_t s_q[kCaWarps][kCaChunk][kCaQueue][32];
+    __shared__ int32_t s_m[kCaWarps][kCaChunk][32];
     if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned below = (1u << lane) - 1u;
-    const int n_binned = p.bin_cnt[p.n_bins];
-    for (int b = blockIdx.x * kCaWarps + w; b < n_binned; b += gridDim.x * kCaWarps) {
-        const int o0 = p.out_off[b], nout = p.out_off[b + 1] - o0;
-        if (nout == 0) continue;
-        const int64_t b0 = p.in_off[b];
-        int ns = p.in_live[b];
-        if (b0 + ns > p.cap_cells) ns = 0;
-        const FHit B = load_hit(p.bh, b);
-        const bool disk = p.layer[p.blayer[b]].kind == PT_LAYER_DISK;
-        const pt_ca_cuts rg = p.region[disk ? 1 : 0];
-        const float tol = p.region_tol[disk ? 1 : 0];
-        const float2 hk = p.hk[b];
-        const float2 *S = p.sk + b0;
-        for (int q0 = 0; q0 < nout; q0 += 32) {
-            const int q = q0 + lane;
-            const bool act = q < nout;
-            int co = 0, r0 = 0, r1 = 0;
-            FHit C = B;
-            float key_c = 0.f, wdt = -1.f, hi = 0.f;
-            if (act) {
-                const int2 ent = p.out_ent[o0 + q];
-                co = ent.x;
-                C = load_hit(p.bh, ent.y);
-                const float dr = C.r - B.r, dz = C.z - B.z;
-                const float num = disk ? dr : dz, den = disk ? dz : dr;
-                key_c = den != 0.f ? num / den : __int_as_float(0x7f800000);
-                // window half-width, widened for float32 rounding of the keys
-                wdt = tol * (hk.x / fabsf(den) + sqrtf(1.0f + key_c * key_c) / hk.y);
-                wdt = wdt * (1.0f + 1e-5f) + 1e-5f * (1.0f + fabsf(key_c) + hk.x);
-                if (!(wdt == wdt) || den == 0.f) wdt = __int_as_float(0x7f800000);
-                // keys passing the window test lie in [lo, hi]
-                const float sl = (fabsf(key_c) + wdt) * 9.5367431640625e-7f;
-                const float lo = key_c - wdt - sl;
-                hi = key_c + wdt + sl;
-                if (!(hi == hi)) hi = __int_as_float(0x7f800000);
-                r0 = lo > -3.4e38f ? lower_key(S, ns, lo) : 0;
-                r1 = ns;
-            }
-            // count accepted candidates; remember the first kCaQueue
-            int mine = 0;
-            for (int r = r0; r < r1; r++) {
-                const float2 e = __ldg(S + r);
-                if (e.x > hi) break;
-                if (!(fabsf(e.x - key_c) <= wdt)) continue;
-                if (connects(p, __ldg(p.bh + __float_as_int(e.y)), B, C, rg)) {
-                    if (mine < kCaQueue) s_q[w][mine][lane] = r;
-                    mine++;
-                }
-            }
-            int total;
-            const int excl = warp_excl(mine, lane, total);
-            int64_t base = 0;
-            if (lane == 0 && total > 0) base = atomicAdd(p.counters + C_EDGES, total);
-            base = __shfl_sync(0xffffffffu, base, 0) + excl;
-            if (mine > 0 && mine <= kCaQueue) {
-                for (int t = 0; t < mine; t++) {
-                    const int ci = p.sci[b0 + s_q[w][t][lane]];
-                    if (base + t < p.cap_edges) {
-                        p.edge_src[base + t] = ci;
-                        p.edge_dst[base + t] = co;
-                    }
-                    p.has_out[ci] = 1;
-                }
-            } else if (mine > kCaQueue) {   // rare: scan again to write all
-                int64_t e = base;
-                for (int r = r0; r < r1; r++) {
-                    const float2 v = __ldg(S + r);
-                    if (v.x > hi) break;
-                    if (!(fabsf(v.x - key_c) <= wdt)) continue;
-                    if (connects(p, __ldg(p.bh + __float_as_int(v.y)), B, C, rg)) {
-                        const int ci = p.sci[b0 + r];
-                        if (e < p.cap_edges) {
-                            p.edge_src[e] = ci;
-                            p.edge_dst[e] = co;
+    const int64_t n_cells = min((int64_t)p.counters[C_CELLS], p.cap_cells);
+    constexpr int64_t kPer = 32 * kCaChunk;
+    const int64_t n_chunks = (n_cells + kPer - 1) / kPer;
+    for (int64_t ch = (int64_t)blockIdx.x * kCaWarps + w; ch < n_chunks; ch += (int64_t)gridDim.x * kCaWarps) {
+        int tot = 0, nleaf = 0;
+#pragma unroll 1
+        for (int it = 0; it < kCaChunk; it++) {
+            const int64_t x = ch * kPer + it * 32 + lane;
+            int m = -1;    // -1: no live cell
+            if (x < n_cells && p.cell_alive[x])
+                m = scan_cell(p, (int)x, [&](int t, int64_t i) {
+                    if (t < kCaQueue) s_q[w][it][t][lane] = p.sci[i];
+                });
+            s_m[w][it][lane] = m;
+            tot += max(m, 0);
+            nleaf += m > 0;
+        }
+        int total;
+        const int excl = warp_excl(tot, lane, total);
+        int64_t base = 0;
+        if (lane == 0 && total > 0) base = atomicAdd(p.counters + C_EDGES, total);
+        base = __shfl_sync(0xffffffffu, base, 0) + excl;
+        int ltot;
+        const int lexcl = warp_excl(nleaf, lane, ltot);
+        int64_t lb = 0;
+        if (lane == 0 && ltot > 0) lb = atomicAdd(p.counters + C_LEAVES, ltot);
+        lb = __shfl_sync(0xffffffffu, lb, 0) + lexcl;
+#pragma unroll 1
+        for (int it = 0; it < kCaChunk; it++) {
+            const int64_t x = ch * kPer + it * 32 + lane;
+            const int m = s_m[w][it][lane];
+            if (m < 0) continue;
+            if (m > 0) {
+                if (m <= kCaQueue) {
+                    for (int t = 0; t < m; t++) {
+                        const int ci = s_q[w][it][t][lane];
+                        if (base + t < p.cap_edges) {
+                            p.edge_src[base + t] = ci;
+                            p.edge_dst[base + t] = (int32_t)x;
                         }
                         p.has_out[ci] = 1;
-                        e++;
                     }
+                } else {   // rare: scan again to write them all
+                    const int64_t e0 = base;
+                    scan_cell(p, (int)x, [&](int t, int64_t i) {
+                        const int ci = p.sci[i];
+                        if (e0 + t < p.cap_edges) {
+                            p.edge_src[e0 + t] = ci;
+                            p.edge_dst[e0 + t] = (int32_t)x;
+                        }
+                        p.has_out[ci] = 1;
+                    });
                 }
+                if (base + m > p.cap_edges) set_flag(p.counters, PT_FLAG_EDGES);
+                if (lb < p.cap_cells) p.leaf_list[lb] = (int32_t)x;
+                lb++;
             }
-            // list of cells with incoming edges (one atomic per warp)
-            const unsigned lm = __ballot_sync(0xffffffffu, mine > 0);
-            int lb = 0;
-            if (lane == 0 && lm) lb = atomicAdd(p.counters + C_LEAVES, __popc(lm));
-            lb = __shfl_sync(0xffffffffu, lb, 0) + __popc(lm & below);
-            if (act) {
-                // incoming-edge range, stored at the cell's out-list position
-                // (coalesced); the search finds it through the cell's rank
-                p.edge_rng[o0 + q] = make_int2((int32_t)base, mine);
-                if (base + mine > p.cap_edges) set_flag(p.counters, PT_FLAG_EDGES);
-                if (mine > 0 && lb < p.cap_cells) p.leaf_list[lb] = co;
-            }
-            __syncwarp();
+            p.edge_rng[x] = make_int2((int32_t)base, m);
+            base += m;
         }
+        __syncwarp();
     }
 }
 

@@ -27,9 +27,8 @@
 //
 // The same pass prepares the CA connection: it writes the live cells of o
 // sorted by their R-z slope key relative to o (with the inner hit and the
-// cell index), per hit the bounds the slope window needs (taken over all
-// cells of o, a superset of the live ones, so the window only widens), and
-// ranks every live cell in the out-list of its inner hit.
+// cell index), and per hit the bounds the slope window needs (taken over
+// all cells of o, a superset of the live ones, so the window only widens).
 #include "pt_common.cuh"
 #include "pt_kernels.cuh"
 
@@ -217,8 +216,7 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
     }
     __syncwarp();
 
-    // pass 2: live cells join the out-list of their inner hit (rank by
-    // atomics) and are written sorted by slope key for the CA connection
+    // pass 2: the live cells, sorted by slope key for the CA connection
     int alive = 0;
     if (in_smem) {
         // slope key and inner hit of each live cell (the records are free)
@@ -236,7 +234,6 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
                 smax = fmaxf(smax, key);
             }
             alive++;
-            p.cell_rank[b + j] = atomicAdd(p.out_off + ii, 1);
         }
         int nl = alive;
 #pragma unroll
@@ -311,7 +308,6 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
             p.sk[b + rank] = make_float2(key, __int_as_float(ii));
             p.sci[b + rank] = (int32_t)(b + j);
             alive++;
-            p.cell_rank[b + j] = atomicAdd(p.out_off + ii, 1);
         }
         nl = alive;
 #pragma unroll
@@ -394,24 +390,6 @@ constexpr int kFbSmallMax = 192;
 void launch_fishbone(const Params &p, float unit_thr, float du, int grid, cudaStream_t s) {
     k_fishbone_small<8, kFbSmallMax, 256, 3><<<grid, 256, 0, s>>>(p, unit_thr, du);
     k_fishbone_large<2, 512, 1024><<<grid, 64, 0, s>>>(p, unit_thr, du);
-}
-
-// Out-lists: live cells grouped by their inner hit (CSR), from the ranks
-// taken in the Fishbone kernel and the scanned per-hit counts.
-__global__ void __launch_bounds__(kThreads) k_out_fill(Params p) {
-    if (upstream_overflow(p, PT_FLAG_CELLS)) return;
-    const int64_t n_cells = min((int64_t)p.counters[C_CELLS], p.cap_cells);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += stride) {
-        if (!p.cell_alive[c]) continue;
-        const int i = p.cell_inner[c];
-        p.out_ent[p.out_off[i] + p.cell_rank[c]] = make_int2((int32_t)c, p.cell_outer[c]);
-    }
-}
-
-void launch_out_lists(const Params &p, int grid, cudaStream_t s) {
-    launch_scan(p.out_off, p.n_hits, p.scan_part, s);
-    k_out_fill<<<grid, kThreads, 0, s>>>(p);
 }
 
 }  // namespace ptk

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kThreads) k_dfs(Params p) {
         st_it[0] = 0;
         while (depth >= 0) {
             const int x = st_cell[depth];
-            const int2 er = p.edge_rng[p.out_off[p.cell_inner[x]] + p.cell_rank[x]];
+            const int2 er = p.edge_rng[x];
             const int ne = er.y;
             if (ne == 0) {
                 // start of a path: emit if it is a root and the path has >= 3 hits
