@@ -306,7 +306,19 @@ static __device__ __noinline__ int exact_fb(GHit h1, GHit h2, GHit h, float eps2
     return big_cmp_scaled(cr, eps2, 0, uv) <= 0;
 }
 
+// a*b - c*d with one rounding: Kahan's algorithm with FMA, relative error
+// at most 2u (Jeannerod, Louvet, Muller, Math. Comp. 82 (2013) 2245).
+__device__ __forceinline__ float det2(float a, float b, float c, float d) {
+    const float w = __fmul_rn(c, d);
+    const float e = __fmaf_rn(-c, d, w);
+    const float f = __fmaf_rn(a, b, -w);
+    return __fadd_rn(f, e);
+}
+
 // ---- filtered predicates (float32 with proven bound; exact when undecided)
+// Cross-product-like differences a*b - c*d that cancel for the accepted
+// configurations are taken with det2 (relative error <= 2u), so the bounds
+// scale with the result rather than with the products.
 // i = inner, o = outer.
 
 // PhiW: Dt > 0 and C^2 <= T Dt^2
@@ -316,11 +328,10 @@ __device__ __forceinline__ int pred_phiw(float xi, float yi, float xo, float yo,
     float Dt = p1 + p2, Dtb = fabsf(p1) + fabsf(p2);
     float eD = ferr(2, Dtb);
     if (Dt < -eD) return 0;
-    float q1 = xi * yo, q2 = yi * xo;
-    float C = q1 - q2, Cb = fabsf(q1) + fabsf(q2);
+    const float C = det2(xi, yo, yi, xo);
     if (Dt > eD) {
         float F = T * (Dt * Dt) - C * C;
-        float e = ferr(5, T * (Dtb * Dtb) + Cb * Cb);
+        float e = ferr(5, T * (Dtb * Dtb) + C * C);
         if (F > e) return 1;
         if (F < -e) return 0;
     }
@@ -346,10 +357,9 @@ __device__ __forceinline__ int pred_pt(float xi, float yi, float zi, float ri, f
                                        float ro, float K, int32_t *cnt) {
     float dx = xo - xi, dy = yo - yi;
     float P = ((dx * dx + dy * dy) * (xi * xi + yi * yi)) * (xo * xo + yo * yo);
-    float q1 = xi * yo, q2 = yi * xo;
-    float C = q1 - q2, Cb = fabsf(q1) + fabsf(q2);
+    const float C = det2(xi, yo, yi, xo);
     float F = P - K * (C * C);
-    float e = ferr(5, P + K * (Cb * Cb));
+    float e = ferr(5, P + K * (C * C));
     if (F > e) return 1;
     if (F < -e) return 0;
     return exact_pt(ghit(xi, yi, zi, ri), ghit(xo, yo, zo, ro), K, cnt);
@@ -372,13 +382,11 @@ __device__ __forceinline__ int pred_dz(const FHit &a, const FHit &c, float zmax,
 
 // CA R-z: X^2 <= tol2 ((r_c-r_a)^2 + (z_c-z_a)^2)
 __device__ __forceinline__ int pred_rz(const FHit &a, const FHit &b, const FHit &c, float tol2, int32_t *cnt) {
-    float d1 = b.r - a.r, d2 = c.z - b.z, d3 = b.z - a.z, d4 = c.r - b.r;
-    float p = d1 * d2, q = d3 * d4;
-    float X = p - q, Xb = fabsf(p) + fabsf(q);
+    const float X = det2(b.r - a.r, c.z - b.z, b.z - a.z, c.r - b.r);
     float e1 = c.r - a.r, e2 = c.z - a.z;
     float T = tol2 * (e1 * e1 + e2 * e2);
     float F = T - X * X;
-    float e = ferr(4, T + Xb * Xb);
+    float e = ferr(4, T + X * X);
     if (F > e) return 1;
     if (F < -e) return 0;
     return exact_rz(ghit(a.x, a.y, a.z, a.r), ghit(b.x, b.y, b.z, b.r), ghit(c.x, c.y, c.z, c.r), tol2, cnt);
@@ -388,11 +396,10 @@ __device__ __forceinline__ int pred_rz(const FHit &a, const FHit &b, const FHit 
 __device__ __forceinline__ int pred_curv(const FHit &a, const FHit &b, const FHit &c, float K, int32_t *cnt) {
     float abx = b.x - a.x, aby = b.y - a.y, acx = c.x - a.x, acy = c.y - a.y;
     float bcx = c.x - b.x, bcy = c.y - b.y;
-    float p = abx * acy, q = aby * acx;
-    float O = p - q, Ob = fabsf(p) + fabsf(q);
+    const float O = det2(abx, acy, aby, acx);
     float P = ((abx * abx + aby * aby) * (bcx * bcx + bcy * bcy)) * (acx * acx + acy * acy);
     float F = P - K * (O * O);
-    float e = ferr(5, P + K * (Ob * Ob));
+    float e = ferr(5, P + K * (O * O));
     if (F > e) return 1;
     if (F < -e) return 0;
     return exact_curv(ghit(a.x, a.y, a.z, a.r), ghit(b.x, b.y, b.z, b.r), ghit(c.x, c.y, c.z, c.r), K, cnt);
@@ -424,14 +431,6 @@ __device__ __forceinline__ int pred_beamspot(const FHit &a, const FHit &b, const
                           cnt);
 }
 
-// a*b - c*d with one rounding: Kahan's algorithm with FMA, relative error
-// at most 2u (Jeannerod, Louvet, Muller, Math. Comp. 82 (2013) 2245).
-__device__ __forceinline__ float det2(float a, float b, float c, float d) {
-    const float w = __fmul_rn(c, d);
-    const float e = __fmaf_rn(-c, d, w);
-    const float f = __fmaf_rn(a, b, -w);
-    return __fadd_rn(f, e);
-}
 
 // Fishbone alignment: u.v > 0 and |u x v|^2 <= eps2 |u|^2 |v|^2 (3-D), for
 // u = h1 - h and v = h2 - h.  Hits are multiples of 2^-14 below 64 in

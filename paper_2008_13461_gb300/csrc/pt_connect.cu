@@ -2,8 +2,8 @@
 // sharing hit b are linked when the R-z alignment, dz, curvature and
 // beamspot predicates of b's region (barrel or endcap, Sec. 4.2) pass.
 //
-// One thread per live cell (b,c), in cell order (cells are grouped by their
-// outer hit c, so the threads of a warp work on neighbouring middle hits).
+// Cells (b,c) are taken in cell order (cells are grouped by their outer hit
+// c, so neighbouring threads work on neighbouring middle hits).
 // The live cells ending on b were written by the Fishbone kernel sorted by
 // their R-z slope key relative to b, with their inner hits, so the
 // candidates (a,b) of a cell are a contiguous run of that array, found by
@@ -21,9 +21,12 @@
 // window test itself, a float32 R-z test with an error bound and then the
 // exact predicate chain decide.
 //
+// A warp takes 128 consecutive cells at a time.  Only cells whose inner hit
+// has live cells ending on it have candidates at all (about a quarter), so
+// the warp first lists those and then runs their searches on full lanes.
 // The incoming edges of a cell are written contiguously (the depth-first
-// search walks them backwards from the cell's edge range).  A warp reserves
-// the edges of 128 consecutive cells with one atomic; each cell remembers
+// search walks them backwards from the cell's edge range); the warp
+// reserves the edges of its 128 cells with one atomic, each cell remembers
 // its first few accepted candidates in shared memory, and a cell with more
 // (rare) scans again to write them all.  Cells with incoming edges join the
 // list the search starts from.
@@ -47,12 +50,10 @@ static __device__ __noinline__ bool ca_test(const FHit A, const FHit B, const FH
 // Branch-free part of the R-z test: false only when the float32 evaluation
 // with its error bound proves the alignment cut fails.
 __device__ __forceinline__ bool rz_maybe(const float4 &a, const FHit &b, const FHit &c, float tol2) {
-    const float d1 = b.r - a.w, d2 = c.z - b.z, d3 = b.z - a.z, d4 = c.r - b.r;
-    const float p = d1 * d2, q = d3 * d4;
-    const float X = p - q, Xb = fabsf(p) + fabsf(q);
+    const float X = det2(b.r - a.w, c.z - b.z, b.z - a.z, c.r - b.r);
     const float e1 = c.r - a.w, e2 = c.z - a.z;
     const float T = tol2 * (e1 * e1 + e2 * e2);
-    return T - X * X >= -ferr(4, T + Xb * Xb);
+    return T - X * X >= -ferr(4, T + X * X);
 }
 
 __device__ __forceinline__ bool connects(const Params &p, const float4 &a, const FHit &B, const FHit &C,
@@ -124,24 +125,52 @@ __device__ __forceinline__ int scan_cell(const Params &p, int x, Emit &&emit) {
 }
 
 __global__ void __launch_bounds__(32 * kCaWarps, 6) k_connect(Params p) {
-    __shared__ int32_t s_q[kCaWarps][kCaChunk][kCaQueue][32];
-    __shared__ int32_t s_m[kCaWarps][kCaChunk][32];
+    constexpr int kPer = 32 * kCaChunk;
+    __shared__ int32_t s_q[kCaWarps][kCaQueue][kPer];   // accepted inner cells per chunk position
+    __shared__ int32_t s_m[kCaWarps][kPer];             // edges per chunk position (-1: no live cell)
+    __shared__ int16_t s_list[kCaWarps][kPer];          // positions whose inner hit has live cells
     if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
     const int64_t n_cells = min((int64_t)p.counters[C_CELLS], p.cap_cells);
-    constexpr int64_t kPer = 32 * kCaChunk;
     const int64_t n_chunks = (n_cells + kPer - 1) / kPer;
     for (int64_t ch = (int64_t)blockIdx.x * kCaWarps + w; ch < n_chunks; ch += (int64_t)gridDim.x * kCaWarps) {
-        int tot = 0, nleaf = 0;
-#pragma unroll 1
+        const int64_t x0 = ch * kPer;
+        // 1) live cells, and a list of those with candidates at all (the
+        //    inner hit has live cells ending on it), so that the searches
+        //    run on full warps
+        int nlist = 0;
+#pragma unroll
         for (int it = 0; it < kCaChunk; it++) {
-            const int64_t x = ch * kPer + it * 32 + lane;
-            int m = -1;    // -1: no live cell
-            if (x < n_cells && p.cell_alive[x])
-                m = scan_cell(p, (int)x, [&](int t, int64_t i) {
-                    if (t < kCaQueue) s_q[w][it][t][lane] = p.sci[i];
-                });
-            s_m[w][it][lane] = m;
+            const int pos = it * 32 + lane;
+            const int64_t x = x0 + pos;
+            int st = -1;
+            bool need = false;
+            if (x < n_cells && p.cell_alive[x]) {
+                st = 0;
+                const int b = p.cell_inner[x];
+                need = p.in_live[b] > 0;
+            }
+            s_m[w][pos] = st;
+            const unsigned m = __ballot_sync(0xffffffffu, need);
+            if (need) s_list[w][nlist + __popc(m & below)] = (int16_t)pos;
+            nlist += __popc(m);
+        }
+        __syncwarp();
+        // 2) the searches
+        for (int i = lane; i < nlist; i += 32) {
+            const int pos = s_list[w][i];
+            s_m[w][pos] = scan_cell(p, (int)(x0 + pos), [&](int t, int64_t k) {
+                if (t < kCaQueue) s_q[w][t][pos] = p.sci[k];
+            });
+        }
+        __syncwarp();
+        // 3) edges of the chunk: one reservation, then each cell's edges
+        //    contiguously and its edge range
+        int tot = 0, nleaf = 0;
+#pragma unroll
+        for (int it = 0; it < kCaChunk; it++) {
+            const int m = s_m[w][it * 32 + lane];
             tot += max(m, 0);
             nleaf += m > 0;
         }
@@ -157,13 +186,14 @@ __global__ void __launch_bounds__(32 * kCaWarps, 6) k_connect(Params p) {
         lb = __shfl_sync(0xffffffffu, lb, 0) + lexcl;
 #pragma unroll 1
         for (int it = 0; it < kCaChunk; it++) {
-            const int64_t x = ch * kPer + it * 32 + lane;
-            const int m = s_m[w][it][lane];
+            const int pos = it * 32 + lane;
+            const int64_t x = x0 + pos;
+            const int m = s_m[w][pos];
             if (m < 0) continue;
             if (m > 0) {
                 if (m <= kCaQueue) {
                     for (int t = 0; t < m; t++) {
-                        const int ci = s_q[w][it][t][lane];
+                        const int ci = s_q[w][t][pos];
                         if (base + t < p.cap_edges) {
                             p.edge_src[base + t] = ci;
                             p.edge_dst[base + t] = (int32_t)x;
@@ -172,8 +202,8 @@ __global__ void __launch_bounds__(32 * kCaWarps, 6) k_connect(Params p) {
                     }
                 } else {   // rare: scan again to write them all
                     const int64_t e0 = base;
-                    scan_cell(p, (int)x, [&](int t, int64_t i) {
-                        const int ci = p.sci[i];
+                    scan_cell(p, (int)x, [&](int t, int64_t k) {
+                        const int ci = p.sci[k];
                         if (e0 + t < p.cap_edges) {
                             p.edge_src[e0 + t] = ci;
                             p.edge_dst[e0 + t] = (int32_t)x;
