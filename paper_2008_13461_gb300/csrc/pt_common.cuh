@@ -20,7 +20,8 @@ enum Counter {
     C_ALIVE_CELLS = 6, C_ALIVE_TUPLES = 7, C_LEAVES = 8,
     C_FB_NEXT = 9,        // Fishbone: next chunk of outer hits to take
     C_FB_BIG = 10,        // Fishbone: outer hits listed for the large warps
-    C_FB_BIG_NEXT = 11    // Fishbone: next listed outer hit to take
+    C_FB_BIG_NEXT = 11,   // Fishbone: next listed outer hit to take
+    C_CA_PENDING = 12     // CA connection: cells left to the exact pass
 };
 
 // Byte offsets of every workspace array (all 256-byte aligned).
@@ -316,12 +317,17 @@ __device__ __forceinline__ float det2(float a, float b, float c, float d) {
 }
 
 // ---- filtered predicates (float32 with proven bound; exact when undecided)
+// Each returns 1 (holds) or 0 (fails).  With kExact = false an undecided
+// float32 evaluation returns 2 instead of calling the exact form, so that
+// hot kernels carry no big-integer code and can defer the rare undecided
+// unit to a kernel that has it.
 // Cross-product-like differences a*b - c*d that cancel for the accepted
 // configurations are taken with det2 (relative error <= 2u), so the bounds
 // scale with the result rather than with the products.
 // i = inner, o = outer.
 
 // PhiW: Dt > 0 and C^2 <= T Dt^2
+template <bool kExact = true>
 __device__ __forceinline__ int pred_phiw(float xi, float yi, float xo, float yo, float T, int32_t *cnt,
                                          float zi, float ri, float zo, float ro) {
     float p1 = xi * xo, p2 = yi * yo;
@@ -335,10 +341,12 @@ __device__ __forceinline__ int pred_phiw(float xi, float yi, float xo, float yo,
         if (F > e) return 1;
         if (F < -e) return 0;
     }
+    if (!kExact) return 2;
     return exact_phiw(ghit(xi, yi, zi, ri), ghit(xo, yo, zo, ro), T, cnt);
 }
 
 // ZIP: r_o > r_i and |z_i r_o - z_o r_i| <= zmax (r_o - r_i)
+template <bool kExact = true>
 __device__ __forceinline__ int pred_zip(float xi, float yi, float zi, float ri, float xo, float yo, float zo,
                                         float ro, float zmax, int32_t *cnt) {
     if (!(ro > ri)) return 0;
@@ -349,10 +357,12 @@ __device__ __forceinline__ int pred_zip(float xi, float yi, float zi, float ri, 
     float e = ferr(3, R + Lb);
     if (F > e) return 1;
     if (F < -e) return 0;
+    if (!kExact) return 2;
     return exact_zip(ghit(xi, yi, zi, ri), ghit(xo, yo, zo, ro), zmax, cnt);
 }
 
 // PT: K C^2 <= |o-i|^2 |i|^2 |o|^2
+template <bool kExact = true>
 __device__ __forceinline__ int pred_pt(float xi, float yi, float zi, float ri, float xo, float yo, float zo,
                                        float ro, float K, int32_t *cnt) {
     float dx = xo - xi, dy = yo - yi;
@@ -362,6 +372,7 @@ __device__ __forceinline__ int pred_pt(float xi, float yi, float zi, float ri, f
     float e = ferr(5, P + K * (C * C));
     if (F > e) return 1;
     if (F < -e) return 0;
+    if (!kExact) return 2;
     return exact_pt(ghit(xi, yi, zi, ri), ghit(xo, yo, zo, ro), K, cnt);
 }
 
@@ -376,11 +387,13 @@ __device__ __forceinline__ FHit load_hit(const float4 *bh, int i) {
 }
 
 // CA dz: |z_a r_c - z_c r_a| <= zmax (r_c - r_a)
+template <bool kExact = true>
 __device__ __forceinline__ int pred_dz(const FHit &a, const FHit &c, float zmax, int32_t *cnt) {
-    return pred_zip(a.x, a.y, a.z, a.r, c.x, c.y, c.z, c.r, zmax, cnt);
+    return pred_zip<kExact>(a.x, a.y, a.z, a.r, c.x, c.y, c.z, c.r, zmax, cnt);
 }
 
 // CA R-z: X^2 <= tol2 ((r_c-r_a)^2 + (z_c-z_a)^2)
+template <bool kExact = true>
 __device__ __forceinline__ int pred_rz(const FHit &a, const FHit &b, const FHit &c, float tol2, int32_t *cnt) {
     const float X = det2(b.r - a.r, c.z - b.z, b.z - a.z, c.r - b.r);
     float e1 = c.r - a.r, e2 = c.z - a.z;
@@ -389,10 +402,12 @@ __device__ __forceinline__ int pred_rz(const FHit &a, const FHit &b, const FHit 
     float e = ferr(4, T + X * X);
     if (F > e) return 1;
     if (F < -e) return 0;
+    if (!kExact) return 2;
     return exact_rz(ghit(a.x, a.y, a.z, a.r), ghit(b.x, b.y, b.z, b.r), ghit(c.x, c.y, c.z, c.r), tol2, cnt);
 }
 
 // CA curvature: |ab|^2 |bc|^2 |ca|^2 >= K O^2
+template <bool kExact = true>
 __device__ __forceinline__ int pred_curv(const FHit &a, const FHit &b, const FHit &c, float K, int32_t *cnt) {
     float abx = b.x - a.x, aby = b.y - a.y, acx = c.x - a.x, acy = c.y - a.y;
     float bcx = c.x - b.x, bcy = c.y - b.y;
@@ -402,6 +417,7 @@ __device__ __forceinline__ int pred_curv(const FHit &a, const FHit &b, const FHi
     float e = ferr(5, P + K * (O * O));
     if (F > e) return 1;
     if (F < -e) return 0;
+    if (!kExact) return 2;
     return exact_curv(ghit(a.x, a.y, a.z, a.r), ghit(b.x, b.y, b.z, b.r), ghit(c.x, c.y, c.z, c.r), K, cnt);
 }
 
@@ -409,6 +425,7 @@ __device__ __forceinline__ int pred_curv(const FHit &a, const FHit &b, const FHi
 // determinant is invariant under translation, so I is evaluated about hit a
 // (B = b-a, C = c-a, D = origin-a), where its terms are small; I is then
 // bounded as an interval (its own error bound) before squaring.
+template <bool kExact = true>
 __device__ __forceinline__ int pred_beamspot(const FHit &a, const FHit &b, const FHit &c, float rmax2,
                                              int32_t *cnt) {
     const float Bx = b.x - a.x, By = b.y - a.y, Cx = c.x - a.x, Cy = c.y - a.y, Dx = -a.x, Dy = -a.y;
@@ -427,6 +444,7 @@ __device__ __forceinline__ int pred_beamspot(const FHit &a, const FHit &b, const
     const float hi = aI + eI, lo = aI - eI;
     if (hi * hi * (1.0f + 8.0f * kU) < T - eT) return 1;
     if (lo > 0.0f && lo * lo * (1.0f - 8.0f * kU) > T + eT) return 0;
+    if (!kExact) return 2;
     return exact_beamspot(ghit(a.x, a.y, a.z, a.r), ghit(b.x, b.y, b.z, b.r), ghit(c.x, c.y, c.z, c.r), rmax2,
                           cnt);
 }

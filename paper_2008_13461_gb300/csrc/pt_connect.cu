@@ -30,6 +30,11 @@
 // its first few accepted candidates in shared memory, and a cell with more
 // (rare) scans again to write them all.  Cells with incoming edges join the
 // list the search starts from.
+//
+// The predicates run as float32 filters only; a cell with a candidate they
+// cannot decide (about one in 10^5) is left to a second pass that has the
+// exact forms, which keeps the big-integer code and its registers out of
+// the main kernel.
 #include "pt_common.cuh"
 #include "pt_kernels.cuh"
 
@@ -39,12 +44,26 @@ constexpr int kCaWarps = 4;
 constexpr int kCaQueue = 8;         // accepted candidates remembered per cell
 constexpr int kCaChunk = 4;         // rounds of 32 cells per edge reservation
 
-// The full chain runs for the few candidates that pass the window and the
-// float R-z test; out of line so that the scan loop stays small.
-static __device__ __noinline__ bool ca_test(const FHit A, const FHit B, const FHit C, const pt_ca_cuts rg,
-                                            int32_t *cnt) {
-    return pred_rz(A, B, C, rg.tol_rz2, cnt) && pred_dz(A, C, rg.zmax, cnt) && pred_curv(A, B, C, rg.k_curv, cnt) &&
-           pred_beamspot(A, B, C, rg.rmax2, cnt);
+// The predicate chain: 1 connects, 0 does not; with kExact = false, 2 when
+// a float32 filter cannot decide and none fails.
+template <bool kExact>
+__device__ __forceinline__ int ca_chain(const FHit &A, const FHit &B, const FHit &C, const pt_ca_cuts &rg,
+                                        int32_t *cnt) {
+    const int r1 = pred_rz<kExact>(A, B, C, rg.tol_rz2, cnt);
+    if (!r1) return 0;
+    const int r2 = pred_dz<kExact>(A, C, rg.zmax, cnt);
+    if (!r2) return 0;
+    const int r3 = pred_curv<kExact>(A, B, C, rg.k_curv, cnt);
+    if (!r3) return 0;
+    const int r4 = pred_beamspot<kExact>(A, B, C, rg.rmax2, cnt);
+    if (!r4) return 0;
+    return (r1 | r2 | r3 | r4) == 1 ? 1 : 2;
+}
+
+// the exact chain, out of line (only the pass over undecided cells uses it)
+static __device__ __noinline__ int ca_test(const FHit A, const FHit B, const FHit C, const pt_ca_cuts rg,
+                                           int32_t *cnt) {
+    return ca_chain<true>(A, B, C, rg, cnt);
 }
 
 // Branch-free part of the R-z test: false only when the float32 evaluation
@@ -56,11 +75,13 @@ __device__ __forceinline__ bool rz_maybe(const float4 &a, const FHit &b, const F
     return T - X * X >= -ferr(4, T + X * X);
 }
 
-__device__ __forceinline__ bool connects(const Params &p, const float4 &a, const FHit &B, const FHit &C,
-                                         const pt_ca_cuts &rg) {
-    if (!rz_maybe(a, B, C, rg.tol_rz2)) return false;
+template <bool kExact>
+__device__ __forceinline__ int connects(const Params &p, const float4 &a, const FHit &B, const FHit &C,
+                                        const pt_ca_cuts &rg) {
+    if (!rz_maybe(a, B, C, rg.tol_rz2)) return 0;
     const FHit A = {a.x, a.y, a.z, a.w};
-    return ca_test(A, B, C, rg, p.counters);
+    if (kExact) return ca_test(A, B, C, rg, p.counters);
+    return ca_chain<false>(A, B, C, rg, p.counters);
 }
 
 // exclusive prefix of v over the warp, and the warp total
@@ -88,8 +109,9 @@ __device__ __forceinline__ int lower_key(const float2 *s, int n, float lo) {
 
 // Every inner cell (a,b) connecting to the live cell x = (b,c), in key
 // order: emit(t, i) for the t-th one, i its index in the sorted arrays.
-// Returns their number.
-template <class Emit>
+// Returns their number, or -2 (kExact = false) when a candidate is
+// undecided.
+template <bool kExact, class Emit>
 __device__ __forceinline__ int scan_cell(const Params &p, int x, Emit &&emit) {
     const int b = p.cell_inner[x], c = p.cell_outer[x];
     const int64_t b0 = p.in_off[b];
@@ -119,12 +141,14 @@ __device__ __forceinline__ int scan_cell(const Params &p, int x, Emit &&emit) {
         const float2 e = __ldg(S + r);
         if (e.x > hi) break;
         if (!(fabsf(e.x - key_c) <= wdt)) continue;
-        if (connects(p, __ldg(p.bh + __float_as_int(e.y)), B, C, rg)) emit(n++, b0 + r);
+        const int v = connects<kExact>(p, __ldg(p.bh + __float_as_int(e.y)), B, C, rg);
+        if (v == 2) return -2;
+        if (v) emit(n++, b0 + r);
     }
     return n;
 }
 
-__global__ void __launch_bounds__(32 * kCaWarps, 6) k_connect(Params p) {
+__global__ void __launch_bounds__(32 * kCaWarps, 8) k_connect(Params p) {
     constexpr int kPer = 32 * kCaChunk;
     __shared__ int32_t s_q[kCaWarps][kCaQueue][kPer];   // accepted inner cells per chunk position
     __shared__ int32_t s_m[kCaWarps][kPer];             // edges per chunk position (-1: no live cell)
@@ -160,9 +184,16 @@ __global__ void __launch_bounds__(32 * kCaWarps, 6) k_connect(Params p) {
         // 2) the searches
         for (int i = lane; i < nlist; i += 32) {
             const int pos = s_list[w][i];
-            s_m[w][pos] = scan_cell(p, (int)(x0 + pos), [&](int t, int64_t k) {
+            int m = scan_cell<false>(p, (int)(x0 + pos), [&](int t, int64_t k) {
                 if (t < kCaQueue) s_q[w][t][pos] = p.sci[k];
             });
+            if (m == -2) {   // undecided: left to the exact pass
+                const int k = atomicAdd(p.counters + C_CA_PENDING, 1);
+                if (k < p.cap_cells) reinterpret_cast<int32_t *>(p.ck)[k] = (int32_t)(x0 + pos);
+                else set_flag(p.counters, PT_FLAG_CELLS);
+                m = -1;
+            }
+            s_m[w][pos] = m;
         }
         __syncwarp();
         // 3) edges of the chunk: one reservation, then each cell's edges
@@ -202,7 +233,7 @@ __global__ void __launch_bounds__(32 * kCaWarps, 6) k_connect(Params p) {
                     }
                 } else {   // rare: scan again to write them all
                     const int64_t e0 = base;
-                    scan_cell(p, (int)x, [&](int t, int64_t k) {
+                    scan_cell<false>(p, (int)x, [&](int t, int64_t k) {
                         const int ci = p.sci[k];
                         if (e0 + t < p.cap_edges) {
                             p.edge_src[e0 + t] = ci;
@@ -222,8 +253,36 @@ __global__ void __launch_bounds__(32 * kCaWarps, 6) k_connect(Params p) {
     }
 }
 
+// The cells with an undecided candidate, one thread each, with the exact
+// predicates; each reserves its own edges.
+__global__ void __launch_bounds__(128) k_connect_exact(Params p) {
+    if (upstream_overflow(p, PT_FLAG_CELLS)) return;
+    const int n = (int)min((int64_t)p.counters[C_CA_PENDING], p.cap_cells);
+    const int32_t *list = reinterpret_cast<const int32_t *>(p.ck);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int x = list[k];
+        const int m = scan_cell<true>(p, x, [](int, int64_t) {});
+        const int64_t base = m > 0 ? atomicAdd(p.counters + C_EDGES, m) : 0;
+        scan_cell<true>(p, x, [&](int t, int64_t i) {
+            const int ci = p.sci[i];
+            if (base + t < p.cap_edges) {
+                p.edge_src[base + t] = ci;
+                p.edge_dst[base + t] = x;
+            }
+            p.has_out[ci] = 1;
+        });
+        if (base + m > p.cap_edges) set_flag(p.counters, PT_FLAG_EDGES);
+        p.edge_rng[x] = make_int2((int32_t)base, m);
+        if (m > 0) {
+            const int lb = atomicAdd(p.counters + C_LEAVES, 1);
+            if (lb < p.cap_cells) p.leaf_list[lb] = x;
+        }
+    }
+}
+
 void launch_connect(const Params &p, int grid, cudaStream_t s) {
     k_connect<<<grid * (kThreads / (32 * kCaWarps)), 32 * kCaWarps, 0, s>>>(p);
+    k_connect_exact<<<grid / 8 + 1, 128, 0, s>>>(p);
 }
 
 }  // namespace ptk
