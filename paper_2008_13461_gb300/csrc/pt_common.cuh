@@ -21,7 +21,8 @@ enum Counter {
     C_FB_NEXT = 9,        // Fishbone: next chunk of outer hits to take
     C_FB_BIG = 10,        // Fishbone: outer hits listed for the large warps
     C_FB_BIG_NEXT = 11,   // Fishbone: next listed outer hit to take
-    C_CA_PENDING = 12     // CA connection: cells left to the exact pass
+    C_CA_PENDING = 12,    // CA connection: cells left to the exact pass
+    C_DB_PENDING = 13     // doublets: outer hits left to the exact pass
 };
 
 // Byte offsets of every workspace array (all 256-byte aligned).

@@ -48,10 +48,12 @@ __device__ __forceinline__ void t_window(const Params &p, const pt_pair_cuts &pc
 
 // Sweep all candidate inner hits of outer hit o.  kWrite = false: fill the
 // group's shared buffer (up to cap entries) and count; kWrite = true: write
-// cells directly at global index base + slot.
-template <int G, bool kWrite>
+// cells directly at global index base + slot.  kExact = false: the
+// predicates are float32 filters only, and *undecided is set on the lanes
+// that met a candidate they cannot decide.
+template <int G, bool kWrite, bool kExact>
 __device__ int sweep_outer(const Params &p, int o, int lane, unsigned gmask, int gshift, int32_t *s_inner,
-                           uint8_t *s_pair, int cap, int64_t base) {
+                           uint8_t *s_pair, int cap, int64_t base, bool *undecided) {
     const float4 ho = __ldg(p.bh + o);
     const float xo = ho.x, yo = ho.y, zo = ho.z, ro = ho.w;
     const int Lo = p.blayer[o], ev = p.bev[o];
@@ -84,15 +86,24 @@ __device__ int sweep_outer(const Params &p, int o, int lane, unsigned gmask, int
             const int beg = p.bin_cnt[tile + tb0], end = p.bin_cnt[tile + tb1 + 1];
             for (int i0 = beg; i0 < end; i0 += G) {
                 const int i = i0 + lane;
-                bool acc = false;
+                int v = 0;     // 1 accepted, 0 rejected, 2|3 undecided (kExact = false)
                 if (i < end) {
                     const float4 hi = __ldg(p.bh + i);
                     const float xi = hi.x, yi = hi.y, zi = hi.z, ri = hi.w;
-                    acc = zi >= pc.zlo && zi <= pc.zhi &&
-                          pred_zip(xi, yi, zi, ri, xo, yo, zo, ro, pc.zmax, p.counters) &&
-                          pred_phiw(xi, yi, xo, yo, pc.tan2_dphi, p.counters, zi, ri, zo, ro) &&
-                          pred_pt(xi, yi, zi, ri, xo, yo, zo, ro, pc.k_pt, p.counters);
+                    if (zi >= pc.zlo && zi <= pc.zhi) {
+                        v = pred_zip<kExact>(xi, yi, zi, ri, xo, yo, zo, ro, pc.zmax, p.counters);
+                        if (v) {
+                            const int v2 = pred_phiw<kExact>(xi, yi, xo, yo, pc.tan2_dphi, p.counters, zi, ri, zo, ro);
+                            v = v2 ? (v | v2) : 0;
+                        }
+                        if (v) {
+                            const int v3 = pred_pt<kExact>(xi, yi, zi, ri, xo, yo, zo, ro, pc.k_pt, p.counters);
+                            v = v3 ? (v | v3) : 0;
+                        }
+                    }
                 }
+                const bool acc = v == 1;
+                if (!kExact && v > 1) *undecided = true;
                 const unsigned m = (__ballot_sync(gmask, acc) >> gshift) & lanes;
                 if (acc) {
                     const int slot = count + __popc(m & below);
@@ -117,6 +128,44 @@ __device__ int sweep_outer(const Params &p, int o, int lane, unsigned gmask, int
     return count;
 }
 
+// Cells of outer hit o (one group of G lanes).  kExact = false: returns
+// false without writing anything when a candidate is undecided.
+template <int G, bool kExact>
+__device__ __forceinline__ bool doublets_hit(const Params &p, int o, int lane, unsigned gmask, int gshift,
+                                             int32_t *s_inner, uint8_t *s_pair, int cap) {
+    bool und = false;
+    const int n = sweep_outer<G, false, kExact>(p, o, lane, gmask, gshift, s_inner, s_pair, cap, 0, &und);
+    if (!kExact && __ballot_sync(gmask, und)) return false;
+    int64_t base = 0;
+    if (lane == 0 && n > 0) base = atomicAdd(p.counters + C_CELLS, n);
+    base = __shfl_sync(gmask, base, gshift);
+    if (n <= cap) {
+        __syncwarp(gmask);
+        for (int k = lane; k < n; k += G) {
+            const int64_t c = base + k;
+            if (c < p.cap_cells) {
+                p.cell_inner[c] = s_inner[k];
+                p.cell_outer[c] = o;
+                p.cell_pair[c] = s_pair[k];
+                p.cell_alive[c] = 1;
+                p.has_out[c] = 0;
+            }
+        }
+    } else {
+        sweep_outer<G, true, kExact>(p, o, lane, gmask, gshift, nullptr, nullptr, 0, base, &und);
+    }
+    if (lane == 0) {
+        p.in_off[o] = (int32_t)base;
+        p.in_cnt[o] = n;
+        if (base + n > p.cap_cells) set_flag(p.counters, PT_FLAG_CELLS);
+    }
+    __syncwarp(gmask);
+    return true;
+}
+
+// Main pass: float32 filters only (no big-integer code, so far fewer
+// registers); an outer hit with an undecided candidate (about one in 10^3)
+// is listed for the exact pass.
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_doublets(Params p) {
     constexpr int kGroups = kThreads / G;
@@ -128,32 +177,24 @@ __global__ void __launch_bounds__(kThreads) k_doublets(Params p) {
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << gshift);
     const int n_binned = p.bin_cnt[p.n_bins];
     for (int o = blockIdx.x * kGroups + grp; o < n_binned; o += gridDim.x * kGroups) {
-        const int n = sweep_outer<G, false>(p, o, lane, gmask, gshift, s_inner[grp], s_pair[grp], kBuf, 0);
-        int64_t base = 0;
-        if (lane == 0 && n > 0) base = atomicAdd(p.counters + C_CELLS, n);
-        base = __shfl_sync(gmask, base, gshift);
-        if (n <= kBuf) {
-            __syncwarp(gmask);
-            for (int k = lane; k < n; k += G) {
-                const int64_t c = base + k;
-                if (c < p.cap_cells) {
-                    p.cell_inner[c] = s_inner[grp][k];
-                    p.cell_outer[c] = o;
-                    p.cell_pair[c] = s_pair[grp][k];
-                    p.cell_alive[c] = 1;
-                    p.has_out[c] = 0;
-                }
-            }
-        } else {
-            sweep_outer<G, true>(p, o, lane, gmask, gshift, nullptr, nullptr, 0, base);
+        if (!doublets_hit<G, false>(p, o, lane, gmask, gshift, s_inner[grp], s_pair[grp], kBuf) && lane == 0) {
+            // listed in hit_bin, free once the hits are binned (one slot per hit)
+            p.hit_bin[atomicAdd(p.counters + C_DB_PENDING, 1)] = o;
         }
-        if (lane == 0) {
-            p.in_off[o] = (int32_t)base;
-            p.in_cnt[o] = n;
-            if (base + n > p.cap_cells) set_flag(p.counters, PT_FLAG_CELLS);
-        }
-        __syncwarp(gmask);
     }
+}
+
+// Exact pass over the listed outer hits.
+__global__ void __launch_bounds__(kThreads) k_doublets_exact(Params p) {
+    constexpr int G = 8, kGroups = kThreads / G, kBuf = 32 * G;
+    __shared__ int32_t s_inner[kGroups][kBuf];
+    __shared__ uint8_t s_pair[kGroups][kBuf];
+    const int lane = threadIdx.x % G, grp = threadIdx.x / G;
+    const int gshift = (threadIdx.x & 31) & ~(G - 1);
+    const unsigned gmask = ((1u << G) - 1u) << gshift;
+    const int n = p.counters[C_DB_PENDING];
+    for (int k = blockIdx.x * kGroups + grp; k < n; k += gridDim.x * kGroups)
+        doublets_hit<G, true>(p, p.hit_bin[k], lane, gmask, gshift, s_inner[grp], s_pair[grp], kBuf);
 }
 
 void launch_doublets(const Params &p, int lanes, int grid, cudaStream_t s) {
@@ -163,6 +204,7 @@ void launch_doublets(const Params &p, int lanes, int grid, cudaStream_t s) {
     case 16: k_doublets<16><<<grid, kThreads, 0, s>>>(p); break;
     default: k_doublets<32><<<grid, kThreads, 0, s>>>(p); break;
     }
+    k_doublets_exact<<<grid / 4 + 1, kThreads, 0, s>>>(p);
 }
 
 }  // namespace ptk
