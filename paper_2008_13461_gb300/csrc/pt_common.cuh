@@ -22,7 +22,8 @@ enum Counter {
     C_FB_BIG = 10,        // Fishbone: outer hits listed for the large warps
     C_FB_BIG_NEXT = 11,   // Fishbone: next listed outer hit to take
     C_CA_PENDING = 12,    // CA connection: cells left to the exact pass
-    C_DB_PENDING = 13     // doublets: outer hits left to the exact pass
+    C_DB_PENDING = 13,    // doublets: outer hits left to the exact pass
+    C_FB_PENDING = 14     // Fishbone: outer hits left to the exact pass
 };
 
 // Byte offsets of every workspace array (all 256-byte aligned).
@@ -458,6 +459,7 @@ __device__ __forceinline__ int pred_beamspot(const FHit &a, const FHit &b, const
 // so its components are taken with det2 (relative error <= 2u each); the
 // squared norms and products of positive terms then carry relative errors
 // below 8u, which bounds F.
+template <bool kExact = true>
 __device__ __forceinline__ int pred_fb_d(float ux, float uy, float uz, float vx, float vy, float vz, float eps2,
                                          int32_t *cnt) {
     const float d1 = ux * vx, d2 = uy * vy, d3 = uz * vz;
@@ -473,6 +475,7 @@ __device__ __forceinline__ int pred_fb_d(float ux, float uy, float uz, float vx,
         if (F > e) return 1;
         if (F < -e) return 0;
     }
+    if (!kExact) return 2;
     const GHit o = {0, 0, 0, 0};
     return exact_fb(ghit(ux, uy, uz, 0.f), ghit(vx, vy, vz, 0.f), o, eps2, cnt);
 }

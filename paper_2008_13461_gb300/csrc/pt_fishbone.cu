@@ -70,22 +70,29 @@ __device__ __forceinline__ int cell_layer(const Params &p, int64_t c) { return p
 // Does sibling d (record r2, meta m2) kill cell j (record r1, unit vector
 // v1, meta m1)?  Same inner layer, unit directions close (a necessary
 // condition of alignment), aligned, and strictly shorter or as long with a
-// smaller input index of the inner hit.
+// smaller input index of the inner hit.  kExact = false: an undecided
+// alignment sets und.
+template <bool kExact>
 __device__ __forceinline__ bool fb_kills(const Params &p, int64_t b, int j, const float4 &r1, const float3 &v1,
-                                         int m1, int d, int m2, const float4 &r2, float unit_thr) {
+                                         int m1, int d, int m2, const float4 &r2, float unit_thr, bool &und) {
     if (d == j || ((m1 ^ m2) & kRecLayerMask)) return false;
     const float dx = v1.x - r2.x * r2.w, dy = v1.y - r2.y * r2.w, dz = v1.z - r2.z * r2.w;
     if (dx * dx + dy * dy + dz * dz > unit_thr) return false;
-    if (!pred_fb_d(r1.x, r1.y, r1.z, r2.x, r2.y, r2.z, p.fishbone_eps2, p.counters)) return false;
+    const int v = pred_fb_d<kExact>(r1.x, r1.y, r1.z, r2.x, r2.y, r2.z, p.fishbone_eps2, p.counters);
+    if (v == 2) und = true;
+    if (v != 1) return false;
     const long long l1 = len2u(r1.x, r1.y, r1.z), l2 = len2u(r2.x, r2.y, r2.z);
     return l2 < l1 || (l2 == l1 && p.perm[p.cell_inner[b + d]] < p.perm[p.cell_inner[b + j]]);
 }
 
 // Verdicts of the n cells of outer hit o (one warp); returns the lane's
 // count of live cells.  kGlobal: n may exceed M (pairwise loop compiled in).
-template <int W, int M, int NB, bool kGlobal>
+// kExact = false (float32 filters only): returns -1, having written no
+// verdict, when n > M or an alignment test is undecided.
+template <int W, int M, int NB, bool kGlobal, bool kExact>
 __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64_t b, int lane, int w,
                                             float unit_thr, float du, FbSmem<W, M, NB> &sm) {
+    if (!kExact && n > M) return -1;
     const float4 ho = __ldg(p.bh + o);
     const bool disk = p.layer[p.blayer[o]].kind == PT_LAYER_DISK;
     const bool in_smem = !kGlobal || n <= M;
@@ -124,6 +131,7 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
     if (lane == 0) p.hk[o] = make_float2(kmax, gmin);
     __syncwarp();
 
+    bool und = false;
     if (kGlobal && !in_smem) {
         // more siblings than the warp holds: plain pairwise loop
         const GHit gh = ghit(ho.x, ho.y, ho.z, ho.w);
@@ -155,7 +163,7 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
             const int m1 = sm.meta[w][j];
             bool dead = false;
             for (int d = 0; d < n && !dead; d++)
-                dead = fb_kills(p, b, j, r1, v1, m1, d, sm.meta[w][d], sm.rec[w][d], unit_thr);
+                dead = fb_kills<kExact>(p, b, j, r1, v1, m1, d, sm.meta[w][d], sm.rec[w][d], unit_thr, und);
             if (dead) sm.dead[w][j] = 1;
         }
     } else {
@@ -209,12 +217,13 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
             bool dead = false;
             for (int q = start; q < end && !dead; q++) {
                 const int d = sm.idx[w][q];
-                dead = fb_kills(p, b, j, r1, v1, m1, d, sm.meta[w][d], sm.rec[w][d], unit_thr);
+                dead = fb_kills<kExact>(p, b, j, r1, v1, m1, d, sm.meta[w][d], sm.rec[w][d], unit_thr, und);
             }
             if (dead) sm.dead[w][j] = 1;
         }
     }
     __syncwarp();
+    if (!kExact && __any_sync(0xffffffffu, und)) return -1;
 
     // pass 2: the live cells, sorted by slope key for the CA connection
     int alive = 0;
@@ -318,6 +327,12 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
     return alive;
 }
 
+// an outer hit left to the exact pass (listed in hit_bin, free once the
+// hits are binned and the doublets' exact pass has run)
+__device__ __forceinline__ void list_pending(const Params &p, int o, int lane) {
+    if (lane == 0) p.hit_bin[atomicAdd(p.counters + C_FB_PENDING, 1)] = o;
+}
+
 __device__ __forceinline__ void add_alive(const Params &p, int v) {
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
@@ -360,7 +375,9 @@ __global__ void __launch_bounds__(32 * W, kMinBlocks) k_fishbone_small(Params p,
             todo &= todo - 1;
             const int n = __shfl_sync(0xffffffffu, nl, t);
             const int b = __shfl_sync(0xffffffffu, bl, t);
-            my_alive += fishbone_hit<W, M, NB, false>(p, (ch << 5) + t, n, b, lane, w, unit_thr, du, sm);
+            const int a = fishbone_hit<W, M, NB, false, false>(p, (ch << 5) + t, n, b, lane, w, unit_thr, du, sm);
+            if (a >= 0) my_alive += a;
+            else list_pending(p, (ch << 5) + t, lane);
         }
     }
     add_alive(p, my_alive);
@@ -368,7 +385,7 @@ __global__ void __launch_bounds__(32 * W, kMinBlocks) k_fishbone_small(Params p,
 
 // Large warps: the listed outer hits, one at a time from a queue.
 template <int W, int M, int NB>
-__global__ void __launch_bounds__(32 * W) k_fishbone_large(Params p, float unit_thr, float du) {
+__global__ void __launch_bounds__(32 * W, 8) k_fishbone_large(Params p, float unit_thr, float du) {
     __shared__ FbSmem<W, M, NB> sm;
     if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -380,7 +397,26 @@ __global__ void __launch_bounds__(32 * W) k_fishbone_large(Params p, float unit_
         k = __shfl_sync(0xffffffffu, k, 0);
         if (k >= n_list) break;
         const int o = p.fb_big[k];
-        my_alive += fishbone_hit<W, M, NB, true>(p, o, p.in_cnt[o], p.in_off[o], lane, w, unit_thr, du, sm);
+        const int a = fishbone_hit<W, M, NB, false, false>(p, o, p.in_cnt[o], p.in_off[o], lane, w, unit_thr, du, sm);
+        if (a >= 0) my_alive += a;
+        else list_pending(p, o, lane);
+    }
+    add_alive(p, my_alive);
+}
+
+// Exact pass: the outer hits listed by the two kernels above (an undecided
+// alignment test, or more cells than a large warp holds), with the exact
+// predicate and the pairwise loop for any number of cells.
+template <int W, int M, int NB>
+__global__ void __launch_bounds__(32 * W) k_fishbone_exact(Params p, float unit_thr, float du) {
+    __shared__ FbSmem<W, M, NB> sm;
+    if (upstream_overflow(p, PT_FLAG_CELLS)) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int my_alive = 0;
+    const int n_list = p.counters[C_FB_PENDING];
+    for (int k = blockIdx.x * W + w; k < n_list; k += gridDim.x * W) {
+        const int o = p.hit_bin[k];
+        my_alive += fishbone_hit<W, M, NB, true, true>(p, o, p.in_cnt[o], p.in_off[o], lane, w, unit_thr, du, sm);
     }
     add_alive(p, my_alive);
 }
@@ -388,8 +424,9 @@ __global__ void __launch_bounds__(32 * W) k_fishbone_large(Params p, float unit_
 constexpr int kFbSmallMax = 192;
 
 void launch_fishbone(const Params &p, float unit_thr, float du, int grid, cudaStream_t s) {
-    k_fishbone_small<8, kFbSmallMax, 256, 3><<<grid, 256, 0, s>>>(p, unit_thr, du);
+    k_fishbone_small<8, kFbSmallMax, 256, 4><<<grid, 256, 0, s>>>(p, unit_thr, du);
     k_fishbone_large<2, 512, 1024><<<grid, 64, 0, s>>>(p, unit_thr, du);
+    k_fishbone_exact<2, 512, 1024><<<grid / 8 + 1, 64, 0, s>>>(p, unit_thr, du);
 }
 
 }  // namespace ptk
