@@ -120,6 +120,45 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ bytes
+# kernels the pipeline launches per step: binning 5 (count, 3 scan passes,
+# fill), doublets 2 (main, exact pass), Fishbone 3 (small, large, exact
+# pass), connection 2 (main, exact pass), n-tuplets 3 (search, 2 cleaning),
+# fit 5 (selection, one per hit count 3, 4, 5, 6..8)
+KERNELS_PER_STEP = 20
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "dram_traffic_pu200_batch8.md")
+
+
+def kernel_source_hash() -> str:
+    """Hash of the CUDA sources and the ABI header (which counters a profile
+    summary was taken on)."""
+    import hashlib
+    h = hashlib.sha256()
+    for d in (os.path.join(ROOT, "paper_2008_13461_gb300", "csrc"), os.path.join(ROOT, "include")):
+        for f in sorted(os.listdir(d)):
+            p = os.path.join(d, f)
+            if os.path.isfile(p):
+                h.update(f.encode())
+                with open(p, "rb") as fh:
+                    h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(stage: str, cells: int):
+    """DRAM bytes of one launch of an ABI call, scaled by cells from the
+    committed ncu summary; None when the kernels changed since it was taken."""
+    try:
+        with open(TRAFFIC_PROFILE) as fh:
+            lines = fh.read().splitlines()
+    except OSError:
+        return None
+    src = next((l.split(":", 1)[1].strip() for l in lines if l.startswith("kernel_sources:")), None)
+    per = next((l.split(":", 1)[1].split() for l in lines if l.startswith("traffic_bytes_per_cell:")), None)
+    if src != kernel_source_hash() or not per:
+        return None
+    table = dict(kv.split("=") for kv in per)
+    return float(table[stage]) * cells if stage in table else None
+
+
 def algorithmic_bytes(H, D, E, T, K, nbar):
     """Bytes each stage must move at least (each input read once, each output
     written once): binning 20H + 24H; doublets 16H per layer-pair slot
@@ -377,8 +416,9 @@ def run_native(args, rank, world, local_rank):
         "e2e": e2e,
         "roofline": {"bound": "hbm", "kernel": stage_names[dom], "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                     "algorithmic_bytes": stage_bytes[dom], "traffic": None},
-        "gpu_launches": 13 * args.steps,
+                     "algorithmic_bytes": stage_bytes[dom], "traffic": measured_traffic(stage_names[dom], D),
+                     "traffic_source": "profiles/dram_traffic_pu200_batch8.md, scaled by cells"},
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
         "clocks": clk,
         "cpu_baseline": cpu,
     }
