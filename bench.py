@@ -123,8 +123,8 @@ class Clocks:
 # kernels the pipeline launches per step: binning 5 (count, 3 scan passes,
 # fill), doublets 2 (main, exact pass), Fishbone 3 (small, large, exact
 # pass), connection 2 (main, exact pass), n-tuplets 3 (search, 2 cleaning),
-# fit 5 (selection, one per hit count 3, 4, 5, 6..8)
-KERNELS_PER_STEP = 20
+# fit 6 (count and selection, one per hit count 3, 4, 5, 6..8)
+KERNELS_PER_STEP = 21
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "dram_traffic_pu200_batch8.md")
 
 

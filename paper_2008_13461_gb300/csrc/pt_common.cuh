@@ -12,7 +12,7 @@ namespace ptk {
 
 constexpr int kThreads = 256;            // threads per block of every kernel
 constexpr int kMaxPairsPerLayer = 8;
-constexpr int kCounters = 16;
+constexpr int kCounters = 32;
 
 // workspace counters (int32 slots at the start of ws)
 enum Counter {
@@ -23,8 +23,13 @@ enum Counter {
     C_FB_BIG_NEXT = 11,   // Fishbone: next listed outer hit to take
     C_CA_PENDING = 12,    // CA connection: cells left to the exact pass
     C_DB_PENDING = 13,    // doublets: outer hits left to the exact pass
-    C_FB_PENDING = 14     // Fishbone: outer hits left to the exact pass
+    C_FB_PENDING = 14,    // Fishbone: outer hits left to the exact pass
+    C_TRK_CNT = 16,       // tracks with 3, 4, 5, 6..8 hits (4 slots)
+    C_TRK_CUR = 20        // next track index of each of those classes (4 slots)
 };
+
+// class of a track by its hit count: 3, 4, 5, 6..8 -> 0..3
+__device__ __forceinline__ int track_class(int n) { return min(n, 6) - 3; }
 
 // Byte offsets of every workspace array (all 256-byte aligned).
 struct WsLayout {

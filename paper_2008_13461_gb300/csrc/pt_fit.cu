@@ -344,22 +344,25 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
 }
 
 // One kernel per hit count (3, 4, 5, and 6..8), so each is compiled for its
-// own register footprint; each scans the track list and fits its own tracks.
+// own register footprint; the tracks of each count occupy a contiguous range
+// of track indices (see k_select_tracks), which each kernel walks.
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_fit(Params p) {
-    const int64_t nk = min((int64_t)p.counters[C_TRACKS], p.cap_tracks);
+    constexpr int c = N - 3;
+    int64_t k0 = 0;
+#pragma unroll
+    for (int q = 0; q < c; q++) k0 += p.counters[C_TRK_CNT + q];
+    const int64_t k1 = min(k0 + p.counters[C_TRK_CNT + c], p.cap_tracks);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nk; k += stride) {
+    for (int64_t k = k0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < k1; k += stride) {
         const int32_t t = p.trk_tuple[k];
-        const int n = p.tup_n[t];
         if (N < 6) {
-            if (n == N) fit_track<N>(p, k, t);
-        } else if (n == 6) {
-            fit_track<6>(p, k, t);
-        } else if (n == 7) {
-            fit_track<7>(p, k, t);
-        } else if (n == 8) {
-            fit_track<8>(p, k, t);
+            fit_track<N>(p, k, t);
+        } else {
+            const int n = p.tup_n[t];
+            if (n == 6) fit_track<6>(p, k, t);
+            else if (n == 7) fit_track<7>(p, k, t);
+            else fit_track<8>(p, k, t);
         }
     }
 }

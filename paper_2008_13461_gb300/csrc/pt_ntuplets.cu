@@ -98,18 +98,66 @@ __global__ void __launch_bounds__(kThreads) k_clean_keep(Params p) {
 }
 
 // queue the surviving n-tuplets with >= min_hits hits for the fit
-__global__ void __launch_bounds__(kThreads) k_select_tracks(Params p) {
+// Tracks are the surviving n-tuplets with at least min_hits hits.  Their
+// indices are grouped by hit count (3, 4, 5, 6..8) so that each fit kernel,
+// compiled for one count, works on a dense range: a first pass counts the
+// classes, the second gives each track class offset + rank.
+__global__ void __launch_bounds__(kThreads) k_count_tracks(Params p) {
+    __shared__ int s_cnt[4];
+    if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
     const int64_t nt = min((int64_t)p.counters[C_TUPLES], p.cap_tuples);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
-        if (!p.tup_alive[t] || p.tup_n[t] < p.min_hits) continue;
-        const int k = atomicAdd(p.counters + C_TRACKS, 1);
-        if (k < p.cap_tracks) p.trk_tuple[k] = (int32_t)t;
-        else set_flag(p.counters, PT_FLAG_TRACKS);
+        const int n = p.tup_n[t];
+        if (p.tup_alive[t] && n >= p.min_hits) atomicAdd(&s_cnt[track_class(n)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 4 && s_cnt[threadIdx.x]) atomicAdd(p.counters + C_TRK_CNT + threadIdx.x, s_cnt[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_select_tracks(Params p) {
+    __shared__ int s_rank[4], s_base[4];
+    int off[4], total = 0;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        off[c] = total;
+        total += p.counters[C_TRK_CNT + c];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        p.counters[C_TRACKS] = total;
+        if (total > p.cap_tracks) set_flag(p.counters, PT_FLAG_TRACKS);
+    }
+    const int64_t nt = min((int64_t)p.counters[C_TUPLES], p.cap_tuples);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x; t0 < nt; t0 += stride) {
+        if (threadIdx.x < 4) s_rank[threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t t = t0 + threadIdx.x;
+        int c = -1, r = 0;
+        if (t < nt) {
+            const int n = p.tup_n[t];
+            if (p.tup_alive[t] && n >= p.min_hits) {
+                c = track_class(n);
+                r = atomicAdd(&s_rank[c], 1);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 4 && s_rank[threadIdx.x])
+            s_base[threadIdx.x] = atomicAdd(p.counters + C_TRK_CUR + threadIdx.x, s_rank[threadIdx.x]);
+        __syncthreads();
+        if (c >= 0) {
+            const int k = off[c] + s_base[c] + r;
+            if (k < p.cap_tracks) p.trk_tuple[k] = (int32_t)t;
+        }
+        __syncthreads();
     }
 }
 
-void launch_select(const Params &p, int grid, cudaStream_t s) { k_select_tracks<<<grid, kThreads, 0, s>>>(p); }
+void launch_select(const Params &p, int grid, cudaStream_t s) {
+    k_count_tracks<<<grid, kThreads, 0, s>>>(p);
+    k_select_tracks<<<grid, kThreads, 0, s>>>(p);
+}
 
 void launch_ntuplets(const Params &p, int grid, cudaStream_t s) {
     k_dfs<<<grid, kThreads, 0, s>>>(p);
