@@ -25,7 +25,9 @@ enum Counter {
     C_DB_PENDING = 13,    // doublets: outer hits left to the exact pass
     C_FB_PENDING = 14,    // Fishbone: outer hits left to the exact pass
     C_TRK_CNT = 16,       // tracks with 3, 4, 5, 6..8 hits (4 slots)
-    C_TRK_CUR = 20        // next track index of each of those classes (4 slots)
+    C_TRK_CUR = 20,       // next track index of each of those classes (4 slots)
+    C_FB_HUGE = 24,       // Fishbone: outer hits listed for the largest warps
+    C_FB_HUGE_NEXT = 25   // Fishbone: next of those to take
 };
 
 // class of a track by its hit count: 3, 4, 5, 6..8 -> 0..3

@@ -19,11 +19,12 @@
 //
 // Shared memory per warp bounds the siblings it can hold, and the warps an
 // SM can keep resident bound how well the gathers of the inner hits are
-// hidden.  Most outer hits have fewer than ~200 cells, so two launches share
-// the work: many small warps take chunks of 32 outer hits from a queue and
-// list the outer hits with more cells, which few large warps then take one
-// at a time; beyond the large warps' capacity a plain pairwise loop over
-// global memory is used.
+// hidden.  Most outer hits have fewer than ~200 cells, so three launches
+// share the work: many small warps take chunks of 32 outer hits from a queue
+// and list the outer hits with more cells, which medium (up to 320 cells)
+// and large warps (up to 512) then take one at a time; an exact pass takes
+// the rest (undecided tests, more cells) with a pairwise loop over global
+// memory beyond 512.
 //
 // The same pass prepares the CA connection: it writes the live cells of o
 // sorted by their R-z slope key relative to o (with the inner hit and the
@@ -341,12 +342,17 @@ __device__ __forceinline__ void add_alive(const Params &p, int v) {
 
 // Small warps: take chunks of 32 consecutive binned hits from a queue, load
 // their cell counts together, work through those with 1..M cells and list
-// the ones with more.
+// the ones with more: up to kFbMidMax cells from the front of the list
+// array, more from its back.
+constexpr int kFbSmallMax = 192;
+constexpr int kFbMidMax = 320;
+
 template <int W, int M, int NB, int kMinBlocks>
 __global__ void __launch_bounds__(32 * W, kMinBlocks) k_fishbone_small(Params p, float unit_thr, float du) {
     __shared__ FbSmem<W, M, NB> sm;
     if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
     int my_alive = 0;
     const int n_binned = p.bin_cnt[p.n_bins];
     const int n_chunks = (n_binned + 31) >> 5;
@@ -362,12 +368,18 @@ __global__ void __launch_bounds__(32 * W, kMinBlocks) k_fishbone_small(Params p,
             bl = p.in_off[ol];
         }
         const bool ok = nl >= 1 && (int64_t)bl + nl <= p.cap_cells;
-        const unsigned big = __ballot_sync(0xffffffffu, ok && nl > M);
-        if (big) {
-            int base = 0;
-            if (lane == 0) base = atomicAdd(p.counters + C_FB_BIG, __popc(big));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (ok && nl > M) p.fb_big[base + __popc(big & ((1u << lane) - 1u))] = ol;
+        const unsigned mid = __ballot_sync(0xffffffffu, ok && nl > M && nl <= kFbMidMax);
+        const unsigned huge = __ballot_sync(0xffffffffu, ok && nl > kFbMidMax);
+        if (mid | huge) {
+            int bm = 0, bh = 0;
+            if (lane == 0) {
+                if (mid) bm = atomicAdd(p.counters + C_FB_BIG, __popc(mid));
+                if (huge) bh = atomicAdd(p.counters + C_FB_HUGE, __popc(huge));
+            }
+            bm = __shfl_sync(0xffffffffu, bm, 0);
+            bh = __shfl_sync(0xffffffffu, bh, 0);
+            if ((mid >> lane) & 1) p.fb_big[bm + __popc(mid & below)] = ol;
+            if ((huge >> lane) & 1) p.fb_big[p.n_hits - 1 - (bh + __popc(huge & below))] = ol;
         }
         unsigned todo = __ballot_sync(0xffffffffu, ok && nl <= M);
         while (todo) {
@@ -383,20 +395,21 @@ __global__ void __launch_bounds__(32 * W, kMinBlocks) k_fishbone_small(Params p,
     add_alive(p, my_alive);
 }
 
-// Large warps: the listed outer hits, one at a time from a queue.
-template <int W, int M, int NB>
-__global__ void __launch_bounds__(32 * W, 8) k_fishbone_large(Params p, float unit_thr, float du) {
+// Larger warps: the listed outer hits, one at a time from a queue (kFromBack:
+// the list at the back of the array).
+template <int W, int M, int NB, bool kFromBack>
+__global__ void __launch_bounds__(32 * W) k_fishbone_large(Params p, float unit_thr, float du) {
     __shared__ FbSmem<W, M, NB> sm;
     if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int my_alive = 0;
-    const int n_list = p.counters[C_FB_BIG];
+    const int n_list = p.counters[kFromBack ? C_FB_HUGE : C_FB_BIG];
     for (;;) {
         int k = 0;
-        if (lane == 0) k = atomicAdd(p.counters + C_FB_BIG_NEXT, 1);
+        if (lane == 0) k = atomicAdd(p.counters + (kFromBack ? C_FB_HUGE_NEXT : C_FB_BIG_NEXT), 1);
         k = __shfl_sync(0xffffffffu, k, 0);
         if (k >= n_list) break;
-        const int o = p.fb_big[k];
+        const int o = p.fb_big[kFromBack ? p.n_hits - 1 - k : k];
         const int a = fishbone_hit<W, M, NB, false, false>(p, o, p.in_cnt[o], p.in_off[o], lane, w, unit_thr, du, sm);
         if (a >= 0) my_alive += a;
         else list_pending(p, o, lane);
@@ -404,7 +417,7 @@ __global__ void __launch_bounds__(32 * W, 8) k_fishbone_large(Params p, float un
     add_alive(p, my_alive);
 }
 
-// Exact pass: the outer hits listed by the two kernels above (an undecided
+// Exact pass: the outer hits listed by the kernels above (an undecided
 // alignment test, or more cells than a large warp holds), with the exact
 // predicate and the pairwise loop for any number of cells.
 template <int W, int M, int NB>
@@ -421,11 +434,10 @@ __global__ void __launch_bounds__(32 * W) k_fishbone_exact(Params p, float unit_
     add_alive(p, my_alive);
 }
 
-constexpr int kFbSmallMax = 192;
-
 void launch_fishbone(const Params &p, float unit_thr, float du, int grid, cudaStream_t s) {
     k_fishbone_small<8, kFbSmallMax, 256, 4><<<grid, 256, 0, s>>>(p, unit_thr, du);
-    k_fishbone_large<2, 512, 1024><<<grid, 64, 0, s>>>(p, unit_thr, du);
+    k_fishbone_large<4, kFbMidMax, 512, false><<<grid, 128, 0, s>>>(p, unit_thr, du);
+    k_fishbone_large<2, 512, 1024, true><<<grid / 4 + 1, 64, 0, s>>>(p, unit_thr, du);
     k_fishbone_exact<2, 512, 1024><<<grid / 8 + 1, 64, 0, s>>>(p, unit_thr, du);
 }
 
