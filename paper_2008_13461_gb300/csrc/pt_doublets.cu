@@ -3,8 +3,8 @@
 // Doublets: a group of G lanes owns one outer hit (persistent grid-stride
 // over the binned hits).  For every layer pair ending on the outer hit's
 // layer it derives the phi window (PhiW) and a conservative window along z
-// (barrel) or r (disk) from ZIP and ZW, widened by one tile on each side, and
-// sweeps the inner tiles row by row: consecutive lanes load consecutive
+// (barrel) or r (disk) from ZIP and ZW, with margins above float32
+// rounding, and sweeps the inner tiles row by row: consecutive lanes load consecutive
 // binned hits (coalesced), evaluate ZW, ZIP, PhiW, PT exactly, and compact
 // the accepted ones with a ballot into a shared-memory buffer.  The cells of
 // one outer hit are written contiguously, so the cells sharing an outer hit
@@ -70,11 +70,19 @@ __device__ int sweep_outer(const Params &p, int o, int lane, unsigned gmask, int
         const pt_layer li = p.layer[pc.inner];
         const float tmin = li.kind == PT_LAYER_BARREL ? li.zmin : li.rmin;
         const float tmax = li.kind == PT_LAYER_BARREL ? li.zmax : li.rmax;
-        const int tb0 = max(t_tile(tlo, tmin, tmax, p.n_t) - 1, 0);
-        const int tb1 = min(t_tile(thi, tmin, tmax, p.n_t) + 1, p.n_t - 1);
+        // Tile ranges: the t window's float32 bounds are within ~1e-5 cm of
+        // the exact ones, so a margin of 1e-4 cm keeps every accepted hit
+        // inside; the half-width in phi already carries a 1e-4 rad margin
+        // over PhiW's exact bound, far above the rounding of the angles.
+        // Tile indices are monotone in t and phi (the binning uses the
+        // same functions), so the tiles cover a superset of the accepted
+        // hits whatever the tile counts.
+        const float mt = 1e-4f + 1e-6f * fmaxf(fabsf(tlo), fabsf(thi));
+        const int tb0 = t_tile(tlo - mt, tmin, tmax, p.n_t);
+        const int tb1 = t_tile(thi + mt, tmin, tmax, p.n_t);
         const float dphi = p.pair_dphi[pi];
-        int f0 = __float2int_rd((phio - dphi + kPi) * (p.n_phi * kTwoPiInv)) - 1;
-        int f1 = __float2int_rd((phio + dphi + kPi) * (p.n_phi * kTwoPiInv)) + 1;
+        int f0 = __float2int_rd((phio - dphi + kPi) * (p.n_phi * kTwoPiInv));
+        int f1 = __float2int_rd((phio + dphi + kPi) * (p.n_phi * kTwoPiInv));
         if (f1 - f0 + 1 >= p.n_phi) {
             f0 = 0;
             f1 = p.n_phi - 1;

@@ -16,7 +16,7 @@ import torch
 
 from . import _lib as L
 
-DEFAULT_TUNING = dict(n_phi_bins=128, n_t_bins=16, doublet_lanes=8, connect_lanes=8, blocks_per_sm=8)
+DEFAULT_TUNING = dict(n_phi_bins=128, n_t_bins=32, doublet_lanes=8, connect_lanes=8, blocks_per_sm=8)
 
 
 def _ptr(t: torch.Tensor | None) -> int | None:
