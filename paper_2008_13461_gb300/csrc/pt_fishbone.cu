@@ -49,7 +49,6 @@ struct FbSmem {
 };
 
 __device__ __forceinline__ int rec_cell(int m) { return m & 1023; }
-__device__ __forceinline__ int rec_bucket(int m) { return (m >> 15) & 1023; }
 constexpr int kRecLayerMask = 31 << 10;
 
 // Bucket key of a record: u^_z (barrel o) or the radial component of u^
@@ -84,6 +83,26 @@ __device__ __forceinline__ bool fb_kills(const Params &p, int64_t b, int j, cons
     if (v != 1) return false;
     const long long l1 = len2u(r1.x, r1.y, r1.z), l2 = len2u(r2.x, r2.y, r2.z);
     return l2 < l1 || (l2 == l1 && p.perm[p.cell_inner[b + d]] < p.perm[p.cell_inner[b + j]]);
+}
+
+// exclusive prefix sum of a[0, nb) in place (nb a power of two >= 32;
+// one warp, nb / 32 entries per lane)
+__device__ __forceinline__ void warp_exclusive_scan(int *a, int nb, int lane) {
+    const int per = nb >> 5;
+    int sum = 0;
+    for (int q = 0; q < per; q++) sum += a[lane * per + q];
+    int incl = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    int run = incl - sum;
+    for (int q = 0; q < per; q++) {
+        const int v = a[lane * per + q];
+        a[lane * per + q] = run;
+        run += v;
+    }
 }
 
 // Verdicts of the n cells of outer hit o (one warp); returns the lane's
@@ -173,54 +192,67 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
             bmin = fminf(bmin, __shfl_xor_sync(0xffffffffu, bmin, d));
             bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, d));
         }
-        // about two buckets per cell (a power of two, 32 .. NB)
-        const int nb = min(NB, max(32, 1 << (32 - __clz(2 * n - 1))));
-        const float iw = 1.0f / fmaxf(du, (bmax - bmin) / (float)(nb - 2));
+        // sort the cells by direction key (ties by position): counting sort
+        // into about one bucket per cell, then the exact rank in the bucket
+        const int nb = min(NB, max(32, 1 << (32 - __clz(n - 1))));
+        const float span = fmaxf(bmax - bmin, fmaxf(fabsf(bmin), fabsf(bmax)) * 1e-6f);
+        const float iw = span > 0.f ? (float)nb / span : 0.f;
         for (int q = lane; q < nb; q += 32) sm.pos[w][q] = 0;
         __syncwarp();
         for (int j = lane; j < n; j += 32) {
             const float key = fb_key(sm.rec[w][j], disk, rx, ry);
-            const int bk = min(max(__float2int_rd((key - bmin) * iw), 0), nb - 1);
-            sm.meta[w][j] |= bk << 15;
-            atomicAdd(&sm.pos[w][bk], 1);
+            atomicAdd(&sm.pos[w][min(max((int)((key - bmin) * iw), 0), nb - 1)], 1);
         }
         __syncwarp();
-        {   // exclusive scan of the bucket counts, nb / 32 buckets per lane
-            const int per = nb >> 5;
-            int sum = 0;
-            for (int q = 0; q < per; q++) sum += sm.pos[w][lane * per + q];
-            int incl = sum;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, incl, d);
-                if (lane >= d) incl += t;
-            }
-            int run = incl - sum;
-            for (int q = 0; q < per; q++) {
-                const int v = sm.pos[w][lane * per + q];
-                sm.pos[w][lane * per + q] = run;
-                run += v;
-            }
+        warp_exclusive_scan(sm.pos[w], nb, lane);
+        __syncwarp();
+        for (int j = lane; j < n; j += 32) {
+            const float key = fb_key(sm.rec[w][j], disk, rx, ry);
+            const int bk = min(max((int)((key - bmin) * iw), 0), nb - 1);
+            sm.idx[w][atomicAdd(&sm.pos[w][bk], 1)] = (int16_t)j;
         }
         __syncwarp();
-        for (int j = lane; j < n; j += 32) sm.idx[w][atomicAdd(&sm.pos[w][rec_bucket(sm.meta[w][j])], 1)] = (int16_t)j;
+        // sm.pos[bk] is now the end of bucket bk
+        for (int j = lane; j < n; j += 32) {
+            const float key = fb_key(sm.rec[w][j], disk, rx, ry);
+            const int bk = min(max((int)((key - bmin) * iw), 0), nb - 1);
+            const int e = sm.pos[w][bk];
+            int rank = bk > 0 ? sm.pos[w][bk - 1] : 0;
+            for (int q = rank; q < e; q++) {
+                const int i = sm.idx[w][q];
+                const float ki = fb_key(sm.rec[w][i], disk, rx, ry);
+                rank += ki < key || (ki == key && i < j);
+            }
+            sm.meta[w][j] |= rank << 16;
+        }
         __syncwarp();
-        // sm.pos[bk] is now the end of bucket bk; each lane takes sorted
-        // positions and scans the cells of buckets bk-1 .. bk+1
+        for (int j = lane; j < n; j += 32) sm.idx[w][sm.meta[w][j] >> 16] = (int16_t)j;
+        __syncwarp();
+        // Each pair once: from each cell, scan forward while the keys of the
+        // later cells are within du (alignment implies it); of an aligned
+        // pair the longer cell dies (equal lengths: the larger input index
+        // of the inner hit).
         for (int q0 = lane; q0 < n; q0 += 32) {
             const int j = sm.idx[w][q0];
             const float4 r1 = sm.rec[w][j];
+            const float k1 = fb_key(r1, disk, rx, ry);
             const float3 v1 = make_float3(r1.x * r1.w, r1.y * r1.w, r1.z * r1.w);
             const int m1 = sm.meta[w][j];
-            const int bk = rec_bucket(m1);
-            const int start = bk >= 2 ? sm.pos[w][bk - 2] : 0;
-            const int end = sm.pos[w][min(bk + 1, nb - 1)];
-            bool dead = false;
-            for (int q = start; q < end && !dead; q++) {
+            for (int q = q0 + 1; q < n; q++) {
                 const int d = sm.idx[w][q];
-                dead = fb_kills<kExact>(p, b, j, r1, v1, m1, d, sm.meta[w][d], sm.rec[w][d], unit_thr, und);
+                const float4 r2 = sm.rec[w][d];
+                if (fb_key(r2, disk, rx, ry) - k1 > du) break;
+                const int m2 = sm.meta[w][d];
+                if ((m1 ^ m2) & kRecLayerMask) continue;
+                const float dx = v1.x - r2.x * r2.w, dy = v1.y - r2.y * r2.w, dz = v1.z - r2.z * r2.w;
+                if (dx * dx + dy * dy + dz * dz > unit_thr) continue;
+                const int v = pred_fb_d<kExact>(r1.x, r1.y, r1.z, r2.x, r2.y, r2.z, p.fishbone_eps2, p.counters);
+                if (v == 2) und = true;
+                if (v != 1) continue;
+                const long long l1 = len2u(r1.x, r1.y, r1.z), l2 = len2u(r2.x, r2.y, r2.z);
+                const bool j_wins = l1 < l2 || (l1 == l2 && p.perm[p.cell_inner[b + j]] < p.perm[p.cell_inner[b + d]]);
+                sm.dead[w][j_wins ? d : j] = 1;
             }
-            if (dead) sm.dead[w][j] = 1;
         }
     }
     __syncwarp();
@@ -266,23 +298,7 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
             atomicAdd(&sm.pos[w][bk], 1);
         }
         __syncwarp();
-        {
-            const int per = nb >> 5;
-            int sum = 0;
-            for (int q = 0; q < per; q++) sum += sm.pos[w][lane * per + q];
-            int incl = sum;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, incl, d);
-                if (lane >= d) incl += t;
-            }
-            int run = incl - sum;
-            for (int q = 0; q < per; q++) {
-                const int v = sm.pos[w][lane * per + q];
-                sm.pos[w][lane * per + q] = run;
-                run += v;
-            }
-        }
+        warp_exclusive_scan(sm.pos[w], nb, lane);
         __syncwarp();
         for (int j = lane; j < n; j += 32)
             if (!sm.dead[w][j]) sm.idx[w][atomicAdd(&sm.pos[w][sm.meta[w][j]], 1)] = (int16_t)j;
