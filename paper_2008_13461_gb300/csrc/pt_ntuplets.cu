@@ -38,7 +38,12 @@ __global__ void __launch_bounds__(kThreads) k_dfs(Params p) {
             if (ne == 0) {
                 // start of a path: emit if it is a root and the path has >= 3 hits
                 if (depth >= 1 && root_layer(p.blayer[p.cell_inner[x]])) {
-                    const int t = atomicAdd(p.counters + C_TUPLES, 1);
+                    // one atomic for the lanes that emit together
+                    const unsigned am = __activemask();
+                    const int leader = __ffs(am) - 1, lane = threadIdx.x & 31;
+                    int t = 0;
+                    if (lane == leader) t = atomicAdd(p.counters + C_TUPLES, __popc(am));
+                    t = __shfl_sync(am, t, leader) + __popc(am & ((1u << lane) - 1u));
                     if (t < p.cap_tuples) {
                         const int n = depth + 2;
                         int32_t *hits = p.tup_hits + (int64_t)t * PT_NMAX;
