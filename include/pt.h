@@ -133,10 +133,13 @@ typedef struct {
 } pt_cuts;
 
 /* Broken-line fit constants (Sec. 3.4): field (T), hit resolutions (cm),
- * material per module crossing (radiation lengths). */
+ * material per module crossing (radiation lengths).  solve_fp32 = 0: the
+ * normal equations, their Cholesky factors, solutions and chi2 in float64
+ * (default); 1: everything in float32 (the precision variant; its deviation
+ * from the float64 solve is characterised by the tests, not bounded). */
 typedef struct {
     float bz, sigma_rphi, sigma_z, sigma_r, x0_barrel, x0_disk;
-    int32_t reserved;
+    int32_t solve_fp32;
 } pt_fit_params;
 
 /* Speed knobs; results do not depend on them. */

@@ -45,7 +45,7 @@ class Cuts(C.Structure):
 class FitParams(C.Structure):
     _fields_ = [("bz", C.c_float), ("sigma_rphi", C.c_float), ("sigma_z", C.c_float),
                 ("sigma_r", C.c_float), ("x0_barrel", C.c_float), ("x0_disk", C.c_float),
-                ("reserved", C.c_int32)]
+                ("solve_fp32", C.c_int32)]
 
 
 class Tuning(C.Structure):

@@ -122,7 +122,7 @@ bool config_ok(const pt_config *cfg) {
     if (lp < 0 || lp > PT_NMAX) return false;
     const pt_fit_params &f = cfg->fit;
     if (!(f.bz > 0) || !(f.sigma_rphi > 0) || !(f.sigma_z > 0) || !(f.sigma_r > 0) || !(f.x0_barrel > 0) ||
-        !(f.x0_disk > 0))
+        !(f.x0_disk > 0) || (f.solve_fp32 != 0 && f.solve_fp32 != 1))
         return false;
     return true;
 }

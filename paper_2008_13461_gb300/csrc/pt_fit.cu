@@ -24,9 +24,9 @@
 // The float64 pipe is the bound, so the unknowns are ordered with the ones
 // the track parameters need (v0, v1; u0, u1, dk) last: with A = L L^T, their
 // covariance is the inverse of the trailing block of L times its transpose
-// (the Schur complement), their values need the back-substitution of that
-// block only, and chi2 = c - |L^-1 b|^2 (c = sum of weighted squared
-// measurements) needs no full solution.
+// (the Schur complement), with no unit-vector solves.  chi2 is taken from
+// the residuals of the full solution: the shortcut c - |L^-1 b|^2 cancels
+// catastrophically for ill-conditioned tracks with large |z|.
 #include "pt_common.cuh"
 #include "pt_kernels.cuh"
 
@@ -40,33 +40,35 @@ __device__ __forceinline__ float asinc(float x) {
 template <int M>
 __device__ __forceinline__ int pidx(int r, int c) { return r * (r + 1) / 2 + c; }
 
-// Double-precision 1/sqrt(s) and 1/d from a float32 seed and one Newton
-// step (relative error 1e-7 -> ~1e-14), to keep the slow FP64 pipe to a
-// few multiply-adds.
-__device__ __forceinline__ double rsqrt_fp64(double s) {
+// 1/sqrt(s) and 1/d in the solve's precision R.  Double: from a float32
+// seed and one Newton step (relative error 1e-7 -> ~1e-14), to keep the slow
+// FP64 pipe to a few multiply-adds; float: IEEE square root and division.
+__device__ __forceinline__ double rsqrt_r(double s) {
     const double y = (double)rsqrtf((float)s);
     return y * (1.5 - 0.5 * s * y * y);
 }
+__device__ __forceinline__ float rsqrt_r(float s) { return 1.0f / sqrtf(s); }
 
-__device__ __forceinline__ double recip_fp64(double d) {
+__device__ __forceinline__ double recip_r(double d) {
     const double r = (double)(1.0f / (float)d);
     return r * (2.0 - d * r);
 }
+__device__ __forceinline__ float recip_r(float d) { return 1.0f / d; }
 
 // in-place Cholesky of a packed lower-triangular SPD matrix; the diagonal
 // holds the reciprocals of L's diagonal (so solves need no division)
-template <int M>
-__device__ __forceinline__ void chol(double *A) {
+template <int M, typename R>
+__device__ __forceinline__ void chol(R *A) {
 #pragma unroll
     for (int j = 0; j < M; j++) {
-        double s = A[pidx<M>(j, j)];
+        R s = A[pidx<M>(j, j)];
 #pragma unroll
         for (int k = 0; k < j; k++) s -= A[pidx<M>(j, k)] * A[pidx<M>(j, k)];
-        const double id = rsqrt_fp64(s > 1e-30 ? s : 1e-30);
+        const R id = rsqrt_r(s > R(1e-30) ? s : R(1e-30));
         A[pidx<M>(j, j)] = id;
 #pragma unroll
         for (int i = j + 1; i < M; i++) {
-            double t = A[pidx<M>(i, j)];
+            R t = A[pidx<M>(i, j)];
 #pragma unroll
             for (int k = 0; k < j; k++) t -= A[pidx<M>(i, k)] * A[pidx<M>(j, k)];
             A[pidx<M>(i, j)] = t * id;
@@ -74,41 +76,38 @@ __device__ __forceinline__ void chol(double *A) {
     }
 }
 
-// Given the factor of chol(), b := L^-1 b; then the last K unknowns of the
-// solution of A x = b (into x) and their covariance (the inverse of
-// L22 L22^T, L22 the trailing K x K block); returns |L^-1 b|^2.
-template <int M, int K>
-__device__ __forceinline__ double solve_tail(const double *L, double *b, double *x, double (*C)[K]) {
+// Given the factor of chol(), b := the solution of A x = b (forward and
+// back substitution), and C := the covariance of its last K unknowns, the
+// inverse of L22 L22^T (L22 the trailing K x K block of L).
+template <int M, int K, typename R>
+__device__ __forceinline__ void solve_tail(const R *L, R *b, R (*C)[K]) {
 #pragma unroll
     for (int i = 0; i < M; i++) {
-        double t = b[i];
+        R t = b[i];
 #pragma unroll
         for (int k = 0; k < i; k++) t -= L[pidx<M>(i, k)] * b[k];
         b[i] = t * L[pidx<M>(i, i)];
     }
-    double yy = 0.0;
 #pragma unroll
-    for (int i = 0; i < M; i++) yy += b[i] * b[i];
-    constexpr int o = M - K;
+    for (int i = M - 1; i >= 0; i--) {
+        R t = b[i];
 #pragma unroll
-    for (int i = K - 1; i >= 0; i--) {
-        double t = b[o + i];
-#pragma unroll
-        for (int k = i + 1; k < K; k++) t -= L[pidx<M>(o + k, o + i)] * x[k];
-        x[i] = t * L[pidx<M>(o + i, o + i)];
+        for (int k = i + 1; k < M; k++) t -= L[pidx<M>(k, i)] * b[k];
+        b[i] = t * L[pidx<M>(i, i)];
     }
     // T = L22^-1 (lower triangular), C = T^T T
-    double T[K][K];
+    constexpr int o = M - K;
+    R T[K][K];
 #pragma unroll
     for (int j = 0; j < K; j++) {
 #pragma unroll
         for (int i = 0; i < K; i++) {
             if (i < j) {
-                T[i][j] = 0.0;
+                T[i][j] = R(0);
             } else if (i == j) {
                 T[i][j] = L[pidx<M>(o + i, o + i)];
             } else {
-                double t = 0.0;
+                R t = R(0);
 #pragma unroll
                 for (int k = j; k < i; k++) t -= L[pidx<M>(o + i, o + k)] * T[k][j];
                 T[i][j] = t * L[pidx<M>(o + i, o + i)];
@@ -119,20 +118,19 @@ __device__ __forceinline__ double solve_tail(const double *L, double *b, double 
     for (int a = 0; a < K; a++)
 #pragma unroll
         for (int c = 0; c <= a; c++) {
-            double t = 0.0;
+            R t = R(0);
 #pragma unroll
             for (int k = a; k < K; k++) t += T[k][a] * T[k][c];
             C[a][c] = t;
             C[c][a] = t;
         }
-    return yy;
 }
 
 // packed index of the symmetric entry (i, j), either order
 template <int M>
 __device__ __forceinline__ int sidx(int i, int j) { return i >= j ? pidx<M>(i, j) : pidx<M>(j, i); }
 
-template <int N>
+template <int N, typename R>
 __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
     const int32_t *hid = p.tup_hits + (int64_t)t * PT_NMAX;
     float hx[N], hy[N], hz[N];
@@ -171,12 +169,12 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
         m[i] = -U / (1.0f + sqrtf(fmaxf(q, 0.f)));
     }
     ds[0] = 0.f;
-    double ids[N];
-    ids[0] = 0.0;
+    R ids[N];
+    ids[0] = R(0);
 #pragma unroll
     for (int i = 1; i < N; i++) {
         ds[i] = fmaxf(s[i] - s[i - 1], 1e-4f);
-        ids[i] = recip_fp64(ds[i]);
+        ids[i] = recip_r((R)ds[i]);
     }
     const float tanl0 = (hz[N - 1] - hz[0]) / fmaxf(s[N - 1], 1e-4f);
     const float sec2 = 1.0f + tanl0 * tanl0;
@@ -184,33 +182,31 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
     const float pmom = pt0 * sqrtf(sec2);
     const float atl = fmaxf(fabsf(tanl0), 1e-3f);
     // 2) scattering variances of the kinks at hits 1 .. n-2
-    double vb[N], vg[N];
+    R vb[N], vg[N];
 #pragma unroll
     for (int i = 1; i < N - 1; i++) {
         const float xx0 = disk[i] ? p.fit.x0_disk * sqrtf(sec2) / atl : p.fit.x0_barrel * sqrtf(sec2);
         const float th = 0.0136f / pmom * sqrtf(xx0) * (1.0f + 0.038f * logf(xx0));
-        const double th2 = (double)th * th;
-        vb[i] = recip_fp64(fmax(th2 * sec2, 1e-20));          // weights 1/variance
-        vg[i] = recip_fp64(fmax(th2 * sec2 * sec2, 1e-20));
+        const R th2 = (R)th * th;
+        vb[i] = recip_r(fmax(th2 * sec2, R(1e-20)));          // weights 1/variance
+        vg[i] = recip_r(fmax(th2 * sec2 * sec2, R(1e-20)));
     }
     // 3) line fit in s-z; unknown v_i at position ln(i): v2 .. v_{n-1}, v0, v1
     auto ln = [](int i) { return i >= 2 ? i - 2 : N - 2 + i; };
-    double A[N * (N + 1) / 2], bv[N];
-    double chi2 = 0.0;
+    R A[N * (N + 1) / 2], bv[N], wz[N];
 #pragma unroll
-    for (int i = 0; i < N * (N + 1) / 2; i++) A[i] = 0.0;
+    for (int i = 0; i < N * (N + 1) / 2; i++) A[i] = R(0);
 #pragma unroll
     for (int i = 0; i < N; i++) {
-        const double sz = disk[i] ? (double)p.fit.sigma_r * atl : (double)p.fit.sigma_z;
-        const double wz = recip_fp64(sz * sz);
-        A[pidx<N>(ln(i), ln(i))] = wz;
-        bv[ln(i)] = wz * hz[i];
-        chi2 += bv[ln(i)] * hz[i];
+        const R sz = disk[i] ? (R)p.fit.sigma_r * atl : (R)p.fit.sigma_z;
+        wz[i] = recip_r(sz * sz);
+        A[pidx<N>(ln(i), ln(i))] = wz[i];
+        bv[ln(i)] = wz[i] * hz[i];
     }
 #pragma unroll
     for (int i = 1; i < N - 1; i++) {
-        const double g0 = ids[i], g2 = ids[i + 1], g1 = -(g0 + g2), w = vg[i];
-        const double wg0 = g0 * w, wg1 = g1 * w, wg2 = g2 * w;
+        const R g0 = ids[i], g2 = ids[i + 1], g1 = -(g0 + g2), w = vg[i];
+        const R wg0 = g0 * w, wg1 = g1 * w, wg2 = g2 * w;
         A[sidx<N>(ln(i - 1), ln(i - 1))] += g0 * wg0;
         A[sidx<N>(ln(i), ln(i - 1))] += g1 * wg0;
         A[sidx<N>(ln(i), ln(i))] += g1 * wg1;
@@ -218,27 +214,35 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
         A[sidx<N>(ln(i + 1), ln(i))] += g2 * wg1;
         A[sidx<N>(ln(i + 1), ln(i + 1))] += g2 * wg2;
     }
-    chol<N>(A);
-    double v[2], Cv[2][2];
-    chi2 -= solve_tail<N, 2>(A, bv, v, Cv);
+    chol<N, R>(A);
+    R Cv[2][2];
+    solve_tail<N, 2, R>(A, bv, Cv);      // bv[ln(i)] = v_i
+    R chi2 = R(0);
+#pragma unroll
+    for (int i = 0; i < N; i++) chi2 += wz[i] * (bv[ln(i)] - hz[i]) * (bv[ln(i)] - hz[i]);
+#pragma unroll
+    for (int i = 1; i < N - 1; i++) {
+        const R gam = (bv[ln(i + 1)] - bv[ln(i)]) * ids[i + 1] - (bv[ln(i)] - bv[ln(i - 1)]) * ids[i];
+        chi2 += gam * gam * vg[i];
+    }
+    const R v[2] = {bv[ln(0)], bv[ln(1)]};
     // 4) circle fit: unknowns u_0 .. u_{n-1}, dk; u_i at position ln(i), dk last
     constexpr int M = N + 1;
-    double B[M * (M + 1) / 2], bu[M];
+    R B[M * (M + 1) / 2], bu[M];
 #pragma unroll
-    for (int i = 0; i < M * (M + 1) / 2; i++) B[i] = 0.0;
-    const double wu = recip_fp64((double)p.fit.sigma_rphi * p.fit.sigma_rphi);
+    for (int i = 0; i < M * (M + 1) / 2; i++) B[i] = R(0);
+    const R wu = recip_r((R)p.fit.sigma_rphi * p.fit.sigma_rphi);
 #pragma unroll
     for (int i = 0; i < N; i++) {
         B[pidx<M>(ln(i), ln(i))] = wu;
         bu[ln(i)] = wu * m[i];
-        chi2 += bu[ln(i)] * m[i];
     }
-    bu[N] = 0.0;
+    bu[N] = R(0);
 #pragma unroll
     for (int i = 1; i < N - 1; i++) {
-        const double h0 = ids[i], h2 = ids[i + 1], h1 = -(h0 + h2);
-        const double h3 = -0.5 * ((double)ds[i] + ds[i + 1]), w = vb[i];
-        const double wh0 = h0 * w, wh1 = h1 * w, wh2 = h2 * w;
+        const R h0 = ids[i], h2 = ids[i + 1], h1 = -(h0 + h2);
+        const R h3 = R(-0.5) * ((R)ds[i] + ds[i + 1]), w = vb[i];
+        const R wh0 = h0 * w, wh1 = h1 * w, wh2 = h2 * w;
         B[sidx<M>(ln(i - 1), ln(i - 1))] += h0 * wh0;
         B[sidx<M>(ln(i), ln(i - 1))] += h1 * wh0;
         B[sidx<M>(ln(i), ln(i))] += h1 * wh1;
@@ -250,16 +254,25 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
         B[pidx<M>(N, ln(i + 1))] += h3 * wh2;
         B[pidx<M>(N, N)] += h3 * h3 * w;
     }
-    chol<M>(B);
-    double xu[3], Cc[3][3];
-    chi2 -= solve_tail<M, 3>(B, bu, xu, Cc);
-    const double dk = xu[2];
+    chol<M, R>(B);
+    R Cc[3][3];
+    solve_tail<M, 3, R>(B, bu, Cc);      // bu[ln(i)] = u_i, bu[N] = dk
+    const R dk = bu[N];
+#pragma unroll
+    for (int i = 0; i < N; i++) chi2 += wu * (bu[ln(i)] - m[i]) * (bu[ln(i)] - m[i]);
+#pragma unroll
+    for (int i = 1; i < N - 1; i++) {
+        const R be = (bu[ln(i + 1)] - bu[ln(i)]) * ids[i + 1] - (bu[ln(i)] - bu[ln(i - 1)]) * ids[i] -
+                     dk * R(0.5) * ((R)ds[i] + ds[i + 1]);
+        chi2 += be * be * vb[i];
+    }
+    const R xu[3] = {bu[ln(0)], bu[ln(1)], dk};
     // 5) perigee of the fitted circle through P with direction psi
-    const float kf = (float)((double)k0 + dk);
+    const float kf = (float)((R)k0 + dk);
     const float u0 = (float)xu[0];
     const float px = hx[0] - u0 * sn, py = hy[0] + u0 * cs;
     const float ds1 = ds[1];
-    const float psi = psi0 + (float)((xu[1] - xu[0]) * ids[1] - dk * 0.5 * ds1);
+    const float psi = psi0 + (float)((xu[1] - xu[0]) * ids[1] - dk * R(0.5) * ds1);
     float sp, cp;
     sincosf(psi, &sp, &cp);
     const float Xo = -det2(px, cp, -py, sp);       // -(P . t)
@@ -272,8 +285,8 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
     float phi0 = psi + dpsi;
     phi0 = phi0 - 6.28318531f * rintf(phi0 * 0.159154943f);
     const float arc = kf != 0.f ? dpsi / kf : Xo;
-    const double tanl = (v[1] - v[0]) * ids[1];
-    const double z0 = v[0] + tanl * arc;
+    const R tanl = (v[1] - v[0]) * ids[1];
+    const R z0 = v[0] + tanl * arc;
     // circle-block Jacobian d(kappa, phi0, d0) / d(u0, u1, dk)
     float J[3][3];
     {
@@ -297,14 +310,14 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
         }
     }
     // F = J C J^T as (J C) J^T
-    double JC[3][3];
+    R JC[3][3];
 #pragma unroll
     for (int a = 0; a < 3; a++)
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            double acc = 0.0;
+            R acc = R(0);
 #pragma unroll
-            for (int c = 0; c < 3; c++) acc += (double)J[a][c] * Cc[c][d];
+            for (int c = 0; c < 3; c++) acc += (R)J[a][c] * Cc[c][d];
             JC[a][d] = acc;
         }
     float Fc[3][3];
@@ -312,15 +325,15 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
     for (int a = 0; a < 3; a++)
 #pragma unroll
         for (int b = 0; b <= a; b++) {
-            double acc = 0.0;
+            R acc = R(0);
 #pragma unroll
             for (int d = 0; d < 3; d++) acc += JC[a][d] * J[b][d];
             Fc[a][b] = (float)acc;
             Fc[b][a] = Fc[a][b];
         }
     // line block: tanl = (v1 - v0)/ds1, z0 = v0 + tanl arc
-    const double t0 = -ids[1], t1 = ids[1], z0a = 1.0 - arc * ids[1], z1a = arc * ids[1];
-    const double c00 = Cv[0][0], c01 = Cv[0][1], c11 = Cv[1][1];
+    const R t0 = -ids[1], t1 = ids[1], z0a = R(1) - arc * ids[1], z1a = arc * ids[1];
+    const R c00 = Cv[0][0], c01 = Cv[0][1], c11 = Cv[1][1];
     float Fl[2][2];
     Fl[0][0] = (float)(t0 * (t0 * c00 + t1 * c01) + t1 * (t0 * c01 + t1 * c11));
     Fl[1][0] = (float)(z0a * (t0 * c00 + t1 * c01) + z1a * (t0 * c01 + t1 * c11));
@@ -345,8 +358,10 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
 
 // One kernel per hit count (3, 4, 5, and 6..8), so each is compiled for its
 // own register footprint; the tracks of each count occupy a contiguous range
-// of track indices (see k_select_tracks), which each kernel walks.
-template <int N>
+// of track indices (see k_select_tracks), which each kernel walks.  R: the
+// precision of the normal equations (double, or float for the all-float32
+// variant).
+template <int N, typename R>
 __global__ void __launch_bounds__(kThreads) k_fit(Params p) {
     constexpr int c = N - 3;
     int64_t k0 = 0;
@@ -357,21 +372,27 @@ __global__ void __launch_bounds__(kThreads) k_fit(Params p) {
     for (int64_t k = k0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < k1; k += stride) {
         const int32_t t = p.trk_tuple[k];
         if (N < 6) {
-            fit_track<N>(p, k, t);
+            fit_track<N, R>(p, k, t);
         } else {
             const int n = p.tup_n[t];
-            if (n == 6) fit_track<6>(p, k, t);
-            else if (n == 7) fit_track<7>(p, k, t);
-            else fit_track<8>(p, k, t);
+            if (n == 6) fit_track<6, R>(p, k, t);
+            else if (n == 7) fit_track<7, R>(p, k, t);
+            else fit_track<8, R>(p, k, t);
         }
     }
 }
 
+template <typename R>
+void launch_fit_r(const Params &p, int grid, cudaStream_t s) {
+    k_fit<3, R><<<grid, kThreads, 0, s>>>(p);
+    k_fit<4, R><<<grid, kThreads, 0, s>>>(p);
+    k_fit<5, R><<<grid, kThreads, 0, s>>>(p);
+    k_fit<6, R><<<grid, kThreads, 0, s>>>(p);
+}
+
 void launch_fit(const Params &p, int grid, cudaStream_t s) {
-    k_fit<3><<<grid, kThreads, 0, s>>>(p);
-    k_fit<4><<<grid, kThreads, 0, s>>>(p);
-    k_fit<5><<<grid, kThreads, 0, s>>>(p);
-    k_fit<6><<<grid, kThreads, 0, s>>>(p);
+    if (p.fit.solve_fp32) launch_fit_r<float>(p, grid, s);
+    else launch_fit_r<double>(p, grid, s);
 }
 
 }  // namespace ptk

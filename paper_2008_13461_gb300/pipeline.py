@@ -84,7 +84,7 @@ class Pipeline:
         cfg.cuts.fishbone_eps2 = cuts["fishbone_eps2"]
         cfg.cuts.min_hits = cuts["min_hits"]
         cfg.fit = L.FitParams(fit["bz"], fit["sigma_rphi"], fit["sigma_z"], fit["sigma_r"], fit["x0_barrel"],
-                              fit["x0_disk"], 0)
+                              fit["x0_disk"], int(fit.get("solve_fp32", 0)))
         t = self.tuning
         cfg.tuning = L.Tuning(t["n_phi_bins"], t["n_t_bins"], t["doublet_lanes"], t["connect_lanes"],
                               t["blocks_per_sm"])
