@@ -16,7 +16,9 @@
  *                      shared-doublet cleaning of Sec. 3.3;
  *   pt_fit_tracks      Sec. 3.4 (broken-line fit: transverse pre-fit, s-z
  *                      line fit, transverse circle fit, combined parameters
- *                      and covariance).
+ *                      and covariance);
+ *   pt_fit_tracks_grad its adjoint (gradient with respect to the hits), and
+ *   pt_align_hits[_grad] per-module alignment of the hits and its adjoint.
  *
  * Conventions shared by every call
  * --------------------------------
@@ -231,9 +233,52 @@ pt_status pt_find_ntuplets(void *ws, size_t ws_bytes, const pt_hits *hits, const
                            const pt_cells *cells, const pt_edges *edges, pt_tuples *tuples,
                            void *stream);
 
-/* Sec. 3.4: broken-line fit of every live n-tuplet with >= min_hits hits. */
+/* Sec. 3.4: broken-line fit of every live n-tuplet with >= min_hits hits.
+ * It may be called again on the same workspace with moved hit coordinates
+ * (same n-tuplets; e.g. after an alignment update): it selects and fits the
+ * tracks afresh. */
 pt_status pt_fit_tracks(void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg,
                         const pt_tuples *tuples, pt_tracks *tracks, void *stream);
+
+/* Adjoint of pt_fit_tracks (Sec. 3.4 differentiated): for the tracks of
+ * the last pt_fit_tracks call on this workspace (same hits, config,
+ * tuples, tracks), given the gradient of a scalar loss with respect to each
+ * track's parameters, grad_params[K*5] in the order of pt_tracks.params
+ * (kappa, phi0, tan lambda, d0, z0), and with respect to its chi2,
+ * grad_chi2[K] (may be NULL: zero), ADDS the gradient with respect to the
+ * input hit coordinates to grad_x, grad_y, grad_z[n_hits] (device,
+ * caller-zeroed; hits on no track get nothing).  The fit is recomputed in
+ * float64 for each track (nothing is stored by the forward call); the
+ * covariance is not differentiated; clamps of the fit (minimum segment
+ * length, curvature and |tan lambda|, maximum scattering weight) have zero
+ * derivative where active.  K = pt_counts.n_tracks. */
+pt_status pt_fit_tracks_grad(void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg,
+                             const pt_tuples *tuples, const pt_tracks *tracks, const float *grad_params,
+                             const float *grad_chi2, float *grad_x, float *grad_y, float *grad_z,
+                             void *stream);
+
+/* Alignment of the hits (per-module rigid corrections, the quantity whose
+ * gradient a track-based alignment needs): a hit on module m moves to
+ *     x' = c_m + (I + [w_m]x) (x - c_m) + d_m
+ * with the module centre c_m, shift d_m and small rotation w_m (first order
+ * in w; [w]x the cross-product matrix).  centre, shift, rot: float[n_modules
+ * * 3] device arrays (x, y, z per module).  x, y, z, module: the hits
+ * (n_hits); x_out, y_out, z_out: the moved hits (may not alias the inputs).
+ * The result is not snapped to the exactness grid: use it for fitting, not
+ * for pt_build_doublets. */
+pt_status pt_align_hits(int32_t n_hits, const float *x, const float *y, const float *z, const int32_t *module,
+                        int32_t n_modules, const float *centre, const float *shift, const float *rot,
+                        float *x_out, float *y_out, float *z_out, void *stream);
+
+/* Adjoint of pt_align_hits: given the gradient at the moved hits (gx_out,
+ * gy_out, gz_out[n_hits]), ADDS the gradient with respect to the original
+ * hits to gx, gy, gz (each may be NULL together: skipped) and, summed over
+ * the hits of each module, with respect to the shifts (grad_shift) and the
+ * rotations (grad_rot, float[n_modules * 3]; each may be NULL). */
+pt_status pt_align_hits_grad(int32_t n_hits, const float *x, const float *y, const float *z,
+                             const int32_t *module, int32_t n_modules, const float *centre, const float *rot,
+                             const float *gx_out, const float *gy_out, const float *gz_out, float *gx, float *gy,
+                             float *gz, float *grad_shift, float *grad_rot, void *stream);
 
 /* Synchronises `stream`, then reports counts and device flags.  Returns
  * PT_ERR_CAPACITY or PT_ERR_INPUT when the corresponding flags are set. */

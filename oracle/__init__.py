@@ -149,6 +149,34 @@ def fit(hx, hy, hz, is_disk, fitpar: dict, ms_scale: float = 1.0):
     return p, cv, chi2.value, ndf.value, ex
 
 
+def fit_grad_fd(hx, hy, hz, is_disk, fitpar: dict, gparams, gchi2: float = 0.0, h: float = 2e-5) -> np.ndarray:
+    """Gradient of  gparams . params + gchi2 * chi2  of the broken-line fit
+    (Sec. 3.4) with respect to the hit coordinates, float[3, n] (x, y, z rows):
+    the derivative's plain definition evaluated numerically, by Richardson
+    extrapolation of central differences of the float64 fit with steps h and
+    h/2 cm (error O(h^4); phi0 differences taken modulo 2 pi)."""
+    base = [np.array(a, dtype=np.float64) for a in (hx, hy, hz)]
+    gp = np.asarray(gparams, dtype=np.float64)
+    n = len(base[0])
+
+    def central(a, i, step):
+        up = [b.copy() for b in base]
+        dn = [b.copy() for b in base]
+        up[a][i] += step
+        dn[a][i] -= step
+        pu, _, cu, _, _ = fit(up[0], up[1], up[2], is_disk, fitpar)
+        pd, _, cd, _, _ = fit(dn[0], dn[1], dn[2], is_disk, fitpar)
+        d = pu - pd
+        d[1] = (d[1] + np.pi) % (2 * np.pi) - np.pi
+        return (float(np.dot(gp, d)) + gchi2 * (cu - cd)) / (2 * step)
+
+    G = np.zeros((3, n))
+    for a in range(3):
+        for i in range(n):
+            G[a, i] = (4.0 * central(a, i, h / 2) - central(a, i, h)) / 3.0
+    return G
+
+
 def run(batch: dict, cuts: dict, fitpar: dict, module_layer: np.ndarray,
         layer_is_disk, stage: int = 4, ms_scale: float = 1.0) -> dict:
     """Run the oracle chain up to `stage` (1 doublets+Fishbone, 2 connect,

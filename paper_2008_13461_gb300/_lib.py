@@ -93,7 +93,8 @@ class Counts(C.Structure):
 
 # every symbol declared in include/pt.h
 EXPORTS = ("pt_workspace_size", "pt_build_doublets", "pt_connect_cells", "pt_find_ntuplets",
-           "pt_fit_tracks", "pt_read_counts", "pt_hit_order", "pt_status_string", "pt_bin_hits_noalloc")
+           "pt_fit_tracks", "pt_fit_tracks_grad", "pt_align_hits", "pt_align_hits_grad", "pt_read_counts",
+           "pt_hit_order", "pt_status_string", "pt_bin_hits_noalloc")
 
 _lib = None
 
@@ -121,6 +122,12 @@ def lib(build_if_missing: bool = True):
     L.pt_find_ntuplets.argtypes = common + [P(Cells), P(Edges), P(Tuples), C.c_void_p]
     L.pt_fit_tracks.restype = C.c_int
     L.pt_fit_tracks.argtypes = common + [P(Tuples), P(Tracks), C.c_void_p]
+    L.pt_fit_tracks_grad.restype = C.c_int
+    L.pt_fit_tracks_grad.argtypes = common + [P(Tuples), P(Tracks)] + [C.c_void_p] * 6
+    L.pt_align_hits.restype = C.c_int
+    L.pt_align_hits.argtypes = [C.c_int32] + [C.c_void_p] * 4 + [C.c_int32] + [C.c_void_p] * 7
+    L.pt_align_hits_grad.restype = C.c_int
+    L.pt_align_hits_grad.argtypes = [C.c_int32] + [C.c_void_p] * 4 + [C.c_int32] + [C.c_void_p] * 11
     L.pt_read_counts.restype = C.c_int
     L.pt_read_counts.argtypes = common + [P(Counts), C.c_void_p]
     L.pt_hit_order.restype = C.c_void_p
@@ -169,6 +176,22 @@ def find_ntuplets(ws, ws_bytes, hits, cfg, cells, edges, tuples, stream) -> None
 def fit_tracks(ws, ws_bytes, hits, cfg, tuples, tracks, stream) -> None:
     check(lib().pt_fit_tracks(ws, ws_bytes, C.byref(hits), C.byref(cfg), C.byref(tuples), C.byref(tracks),
                               stream), "pt_fit_tracks")
+
+
+def fit_tracks_grad(ws, ws_bytes, hits, cfg, tuples, tracks, grad_params, grad_chi2, gx, gy, gz, stream) -> None:
+    check(lib().pt_fit_tracks_grad(ws, ws_bytes, C.byref(hits), C.byref(cfg), C.byref(tuples), C.byref(tracks),
+                                   grad_params, grad_chi2, gx, gy, gz, stream), "pt_fit_tracks_grad")
+
+
+def align_hits(n_hits, x, y, z, module, n_modules, centre, shift, rot, xo, yo, zo, stream) -> None:
+    check(lib().pt_align_hits(n_hits, x, y, z, module, n_modules, centre, shift, rot, xo, yo, zo, stream),
+          "pt_align_hits")
+
+
+def align_hits_grad(n_hits, x, y, z, module, n_modules, centre, rot, gxo, gyo, gzo, gx, gy, gz, gshift, grot,
+                    stream) -> None:
+    check(lib().pt_align_hits_grad(n_hits, x, y, z, module, n_modules, centre, rot, gxo, gyo, gzo, gx, gy, gz,
+                                   gshift, grot, stream), "pt_align_hits_grad")
 
 
 def read_counts(ws, ws_bytes, hits, cfg, stream) -> tuple[int, Counts]:

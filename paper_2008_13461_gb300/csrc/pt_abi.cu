@@ -62,6 +62,7 @@ bool layout(const pt_hits *h, const pt_config *cfg, WsLayout &L) {
     L.edge_rng = take(8 * nc);
     L.has_out = take(nc);
     L.maxlen = take(4 * nc);
+    L.trk_blk = take(sizeof(int32_t) * 4 * kSelBlocks);
     L.total = o;
     return true;
 }
@@ -178,6 +179,7 @@ Params make_params(void *ws, const WsLayout &L, const pt_hits *h, const pt_confi
     p.edge_rng = (int2 *)(w + L.edge_rng);
     p.has_out = (uint8_t *)(w + L.has_out);
     p.maxlen = (int32_t *)(w + L.maxlen);
+    p.trk_blk = (int32_t *)(w + L.trk_blk);
     p.cap_cells = cfg->capacity.cells;
     p.cap_edges = cfg->capacity.edges;
     p.cap_tuples = cfg->capacity.tuples;
@@ -322,8 +324,63 @@ pt_status pt_fit_tracks(void *ws, size_t ws_bytes, const pt_hits *hits, const pt
     p.trk_ndf = tracks->ndf;
     p.trk_tuple = tracks->tuple;
     const int grid = grid_for(cfg);
-    launch_select(p, grid, (cudaStream_t)stream);
-    launch_fit(p, grid, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    // the selection counts afresh on every call
+    if (cudaMemsetAsync(p.counters + C_TRACKS, 0, sizeof(int32_t), s) != cudaSuccess ||
+        cudaMemsetAsync(p.counters + C_TRK_CNT, 0, sizeof(int32_t) * 8, s) != cudaSuccess)
+        return PT_ERR_CUDA;
+    launch_select(p, grid, s);
+    launch_fit(p, grid, s);
+    return launched();
+}
+
+pt_status pt_fit_tracks_grad(void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg,
+                             const pt_tuples *tuples, const pt_tracks *tracks, const float *grad_params,
+                             const float *grad_chi2, float *grad_x, float *grad_y, float *grad_z, void *stream) {
+    WsLayout L;
+    pt_status st = check_common(ws, ws_bytes, hits, cfg, L);
+    if (st != PT_OK) return st;
+    if (!tuples || !tracks || !tuples->hits || !tuples->n || !tracks->tuple || !grad_params || !grad_x ||
+        !grad_y || !grad_z)
+        return PT_ERR_INVALID_ARG;
+    Params p = make_params(ws, L, hits, cfg);
+    p.tup_hits = tuples->hits;
+    p.tup_n = tuples->n;
+    p.trk_tuple = tracks->tuple;
+    launch_fit_grad(p, grad_params, grad_chi2, grad_x, grad_y, grad_z, grid_for(cfg), (cudaStream_t)stream);
+    return launched();
+}
+
+static int align_grid(int32_t n) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int need = (n + kThreads - 1) / kThreads;
+    return need < 1 ? 1 : (need < sms * 8 ? need : sms * 8);
+}
+
+pt_status pt_align_hits(int32_t n_hits, const float *x, const float *y, const float *z, const int32_t *module,
+                        int32_t n_modules, const float *centre, const float *shift, const float *rot,
+                        float *x_out, float *y_out, float *z_out, void *stream) {
+    if (n_hits < 0 || n_modules <= 0) return PT_ERR_INVALID_ARG;
+    if (n_hits == 0) return PT_OK;
+    if (!x || !y || !z || !module || !centre || !shift || !rot || !x_out || !y_out || !z_out)
+        return PT_ERR_INVALID_ARG;
+    launch_align(n_hits, x, y, z, module, centre, shift, rot, x_out, y_out, z_out, align_grid(n_hits),
+                 (cudaStream_t)stream);
+    return launched();
+}
+
+pt_status pt_align_hits_grad(int32_t n_hits, const float *x, const float *y, const float *z,
+                             const int32_t *module, int32_t n_modules, const float *centre, const float *rot,
+                             const float *gx_out, const float *gy_out, const float *gz_out, float *gx, float *gy,
+                             float *gz, float *grad_shift, float *grad_rot, void *stream) {
+    if (n_hits < 0 || n_modules <= 0) return PT_ERR_INVALID_ARG;
+    if (n_hits == 0) return PT_OK;
+    if (!x || !y || !z || !module || !centre || !rot || !gx_out || !gy_out || !gz_out) return PT_ERR_INVALID_ARG;
+    if ((gx != nullptr) != (gy != nullptr) || (gx != nullptr) != (gz != nullptr)) return PT_ERR_INVALID_ARG;
+    launch_align_grad(n_hits, x, y, z, module, centre, rot, gx_out, gy_out, gz_out, gx, gy, gz, grad_shift, grad_rot,
+                      align_grid(n_hits), (cudaStream_t)stream);
     return launched();
 }
 

@@ -36,7 +36,7 @@ __device__ __forceinline__ int track_class(int n) { return min(n, 6) - 3; }
 // Byte offsets of every workspace array (all 256-byte aligned).
 struct WsLayout {
     size_t counters, bin_cnt, scan_part, hit_bin, hit_rank;
-    size_t bh, blayer, bev, perm, in_off, in_cnt, in_live, hk, ck, sk, sci, leaf_list;
+    size_t bh, blayer, bev, perm, in_off, in_cnt, in_live, hk, ck, sk, sci, leaf_list, trk_blk;
     size_t edge_rng, has_out, maxlen;
     size_t total;
     int64_t n_bins;        // events * layers * phi bins * t bins
@@ -44,6 +44,7 @@ struct WsLayout {
 };
 
 constexpr int kScanItems = 4096;         // bins per scan block (256 threads x 16)
+constexpr int kSelBlocks = 1024;         // blocks of the track selection
 
 // Everything a kernel needs, passed by value.
 struct Params {
@@ -66,6 +67,7 @@ struct Params {
     int32_t *sci;                        //   (key, inner hit as int bits) and the cell index
     uint8_t *has_out;
     int32_t *maxlen;
+    int32_t *trk_blk;                    // track selection: per block and class, counts then offsets
     // outputs
     int32_t *cell_inner, *cell_outer;
     uint8_t *cell_pair, *cell_alive;

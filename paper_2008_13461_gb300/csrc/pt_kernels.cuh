@@ -13,5 +13,12 @@ void launch_connect(const Params &p, int grid, cudaStream_t s);
 void launch_ntuplets(const Params &p, int grid, cudaStream_t s);
 void launch_select(const Params &p, int grid, cudaStream_t s);
 void launch_fit(const Params &p, int grid, cudaStream_t s);
+void launch_fit_grad(const Params &p, const float *gpar, const float *gchi, float *gx, float *gy, float *gz, int grid,
+                     cudaStream_t s);
+void launch_align(int n, const float *x, const float *y, const float *z, const int32_t *module, const float *centre,
+                  const float *shift, const float *rot, float *xo, float *yo, float *zo, int grid, cudaStream_t s);
+void launch_align_grad(int n, const float *x, const float *y, const float *z, const int32_t *module,
+                       const float *centre, const float *rot, const float *gxa, const float *gya, const float *gza,
+                       float *gx, float *gy, float *gz, float *gshift, float *grot, int grid, cudaStream_t s);
 
 }  // namespace ptk

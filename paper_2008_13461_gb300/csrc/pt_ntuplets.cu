@@ -105,24 +105,38 @@ __global__ void __launch_bounds__(kThreads) k_clean_keep(Params p) {
 // queue the surviving n-tuplets with >= min_hits hits for the fit
 // Tracks are the surviving n-tuplets with at least min_hits hits.  Their
 // indices are grouped by hit count (3, 4, 5, 6..8) so that each fit kernel,
-// compiled for one count, works on a dense range: a first pass counts the
-// classes, the second gives each track class offset + rank.
+// compiled for one count, works on a dense range, and within a class follow
+// the n-tuplet order, so a fit repeated on moved hits lists the same tracks
+// in the same order.  Block b of kSelBlocks owns a contiguous slice of the
+// n-tuplets: the first kernel counts each slice's classes, the second turns
+// the counts into offsets and ranks each slice's tracks in order.
+__device__ __forceinline__ int track_class_of(const Params &p, int64_t t) {
+    const int n = p.tup_n[t];
+    return p.tup_alive[t] && n >= p.min_hits ? track_class(n) : -1;
+}
+
 __global__ void __launch_bounds__(kThreads) k_count_tracks(Params p) {
     __shared__ int s_cnt[4];
     if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     const int64_t nt = min((int64_t)p.counters[C_TUPLES], p.cap_tuples);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
-        const int n = p.tup_n[t];
-        if (p.tup_alive[t] && n >= p.min_hits) atomicAdd(&s_cnt[track_class(n)], 1);
+    const int64_t per = (nt + kSelBlocks - 1) / kSelBlocks;
+    const int64_t t0 = blockIdx.x * per, t1 = min(t0 + per, nt);
+    for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+        const int c = track_class_of(p, t);
+        if (c >= 0) atomicAdd(&s_cnt[c], 1);
     }
     __syncthreads();
-    if (threadIdx.x < 4 && s_cnt[threadIdx.x]) atomicAdd(p.counters + C_TRK_CNT + threadIdx.x, s_cnt[threadIdx.x]);
+    if (threadIdx.x < 4) {
+        p.trk_blk[blockIdx.x * 4 + threadIdx.x] = s_cnt[threadIdx.x];
+        if (s_cnt[threadIdx.x]) atomicAdd(p.counters + C_TRK_CNT + threadIdx.x, s_cnt[threadIdx.x]);
+    }
 }
 
 __global__ void __launch_bounds__(kThreads) k_select_tracks(Params p) {
-    __shared__ int s_rank[4], s_base[4];
+    __shared__ int s_base[4];
+    __shared__ int s_wcnt[kThreads / 32][4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int off[4], total = 0;
 #pragma unroll
     for (int c = 0; c < 4; c++) {
@@ -133,35 +147,49 @@ __global__ void __launch_bounds__(kThreads) k_select_tracks(Params p) {
         p.counters[C_TRACKS] = total;
         if (total > p.cap_tracks) set_flag(p.counters, PT_FLAG_TRACKS);
     }
+    // this slice's start in each class: the counts of the slices before it
+    if (threadIdx.x < 4) {
+        int b = 0;
+        for (int q = 0; q < (int)blockIdx.x; q++) b += p.trk_blk[q * 4 + threadIdx.x];
+        s_base[threadIdx.x] = off[threadIdx.x] + b;
+    }
+    __syncthreads();
     const int64_t nt = min((int64_t)p.counters[C_TUPLES], p.cap_tuples);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x; t0 < nt; t0 += stride) {
-        if (threadIdx.x < 4) s_rank[threadIdx.x] = 0;
-        __syncthreads();
-        const int64_t t = t0 + threadIdx.x;
-        int c = -1, r = 0;
-        if (t < nt) {
-            const int n = p.tup_n[t];
-            if (p.tup_alive[t] && n >= p.min_hits) {
-                c = track_class(n);
-                r = atomicAdd(&s_rank[c], 1);
-            }
+    const int64_t per = (nt + kSelBlocks - 1) / kSelBlocks;
+    const int64_t t0 = blockIdx.x * per, t1 = min(t0 + per, nt);
+    for (int64_t tb = t0; tb < t1; tb += blockDim.x) {
+        const int64_t t = tb + threadIdx.x;
+        const int c = t < t1 ? track_class_of(p, t) : -1;
+        // rank in n-tuplet order: within the warp by ballot, across warps
+        // by the warps' counts
+        int rank = 0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const unsigned m = __ballot_sync(0xffffffffu, c == q);
+            if (lane == 0) s_wcnt[w][q] = __popc(m);
+            if (c == q) rank = __popc(m & ((1u << lane) - 1u));
         }
         __syncthreads();
-        if (threadIdx.x < 4 && s_rank[threadIdx.x])
-            s_base[threadIdx.x] = atomicAdd(p.counters + C_TRK_CUR + threadIdx.x, s_rank[threadIdx.x]);
-        __syncthreads();
         if (c >= 0) {
-            const int k = off[c] + s_base[c] + r;
+            int before = 0;
+            for (int q = 0; q < w; q++) before += s_wcnt[q][c];
+            const int k = s_base[c] + before + rank;
             if (k < p.cap_tracks) p.trk_tuple[k] = (int32_t)t;
+        }
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            int add = 0;
+            for (int q = 0; q < kThreads / 32; q++) add += s_wcnt[q][threadIdx.x];
+            s_base[threadIdx.x] += add;
         }
         __syncthreads();
     }
 }
 
 void launch_select(const Params &p, int grid, cudaStream_t s) {
-    k_count_tracks<<<grid, kThreads, 0, s>>>(p);
-    k_select_tracks<<<grid, kThreads, 0, s>>>(p);
+    (void)grid;
+    k_count_tracks<<<kSelBlocks, kThreads, 0, s>>>(p);
+    k_select_tracks<<<kSelBlocks, kThreads, 0, s>>>(p);
 }
 
 void launch_ntuplets(const Params &p, int grid, cudaStream_t s) {

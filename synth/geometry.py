@@ -104,6 +104,32 @@ def module_layer_table() -> np.ndarray:
     return t
 
 
+def module_centres() -> np.ndarray:
+    """float64[N_MODULES, 3]: the centre of each module (barrel: ladder axis
+    at the module's mid z; disks: mid radius of the ring, mid azimuth), the
+    reference point about which alignment rotations act."""
+    c = np.zeros((N_MODULES, 3))
+    hz = 2 * BARREL_HALF_Z / BARREL_ZSEG
+    for L, n in enumerate(BARREL_LADDERS):
+        for k in range(n):
+            phi = (k + 0.5) * 2 * math.pi / n
+            r = BARREL_R[L] - BARREL_DR if k % 2 == 0 else BARREL_R[L] + BARREL_DR
+            for j in range(BARREL_ZSEG):
+                c[_BARREL_BASE[L] + k * BARREL_ZSEG + j] = (r * math.cos(phi), r * math.sin(phi),
+                                                          -BARREL_HALF_Z + (j + 0.5) * hz)
+    rings = ((DISK_RMIN + DISK_RING_SPLIT) / 2, (DISK_RING_SPLIT + DISK_RMAX) / 2)
+    for layer in range(4, 10):
+        side = 1.0 if layer < 7 else -1.0
+        zd = DISK_Z[(layer - 4) % 3]
+        for ring, nm in enumerate(DISK_RING_MODULES):
+            for k in range(nm):
+                phi = (k + 0.5) * 2 * math.pi / nm
+                z = side * (zd - DISK_DZ if k % 2 == 0 else zd + DISK_DZ)
+                m = disk_module_id(layer, np.array([ring]), np.array([k]))[0]
+                c[m] = (rings[ring] * math.cos(phi), rings[ring] * math.sin(phi), z)
+    return c
+
+
 def barrel_module_id(layer: int, ladder: np.ndarray, z: np.ndarray) -> np.ndarray:
     zseg = np.clip(np.floor((z + BARREL_HALF_Z) / (2 * BARREL_HALF_Z / BARREL_ZSEG)), 0,
                    BARREL_ZSEG - 1).astype(np.int64)

@@ -402,3 +402,49 @@ def test_fit_pulls_on_scattered_tracks():
         assert 0.9 < np.std(pull) < 1.15, (j, np.std(pull))
     c2 = res["chi2"][g] / res["ndf"][g]
     assert 0.85 < np.mean(res["chi2"][g]) / np.mean(res["ndf"][g]) < 1.15, np.mean(c2)
+
+
+# ------------------------------------------------------ fit gradient
+def _smeared_helix(rng, n):
+    kappa = rng.choice([1, -1]) / rng.uniform(40.0, 3000.0)
+    s = np.cumsum(rng.uniform(3.0, 5.0, n))
+    P = _helix_points(kappa, rng.uniform(-3, 3), rng.uniform(-2.0, 2.0), rng.normal(0, 0.01),
+                      rng.normal(0, 3.0), s)
+    P[:, :2] += rng.normal(0, 10e-4, (n, 2))
+    P[:, 2] += rng.normal(0, 20e-4, n)
+    disk = list((rng.uniform(size=n) < 0.3).astype(int))
+    return P, disk
+
+
+def test_fit_gradient_sum_rules():
+    """The fit commutes with a translation of all hits along z (z0 moves by
+    the shift, the other parameters and chi2 stay) and with a rotation about
+    the beam line (phi0 turns by the angle, the rest stays), so the gradient
+    with respect to the hits obeys exact sum rules: sum_i dF/dz_i = [F = z0]
+    and sum_i (x_i dF/dy_i - y_i dF/dx_i) = [F = phi0].  Checked on the
+    oracle's float64 finite-difference gradient for smeared helices of 3, 4
+    and 5 hits (barrel and disk hits mixed)."""
+    rng = np.random.default_rng(11)
+    for n in (3, 4, 5, 5):
+        P, disk = _smeared_helix(rng, n)
+        for o in range(6):
+            gp = np.zeros(5)
+            gc = 0.0
+            if o < 5:
+                gp[o] = 1.0
+            else:
+                gc = 1.0
+            Gr = oracle.fit_grad_fd(P[:, 0], P[:, 1], P[:, 2], disk, CU.FIT_PARAMS, gp, gc)
+            sz = Gr[2].sum()
+            rot = float(np.sum(P[:, 0] * Gr[1] - P[:, 1] * Gr[0]))
+            scale = 1.0 + np.abs(Gr).sum()
+            assert abs(sz - (1.0 if o == 4 else 0.0)) < 1e-7 * scale, (n, o, sz)
+            assert abs(rot - (1.0 if o == 1 else 0.0)) < 1e-7 * scale, (n, o, rot)
+
+
+def test_fit_gradient_of_chi2_vanishes_on_exact_helices():
+    """chi2 is zero, its minimum, on the hits of an exact helix, so its
+    gradient with respect to the hits vanishes there."""
+    P = _helix_points(1 / 60.0, 0.4, 0.8, 0.002, 1.0, [3.0, 7.0, 11.0, 15.5])
+    Gr = oracle.fit_grad_fd(P[:, 0], P[:, 1], P[:, 2], [0, 0, 0, 0], CU.FIT_PARAMS, np.zeros(5), 1.0)
+    assert np.abs(Gr).max() < 1e-3
