@@ -247,6 +247,39 @@ def measure_e2e(c, args, batch, world):
             "d2h_bytes_per_step": d2h}
 
 
+def measure_differentiable(c, args):
+    """The differentiable form on the same batch: a refit of every track from
+    the hits (its n-tuplets fixed) and the adjoint pass giving the gradient
+    of a loss of all parameters and chi2 with respect to every hit; median
+    milliseconds of each, CUDA events, after warm-up."""
+    import torch
+    from paper_2008_13461_gb300 import _lib as L
+    K = c.counts.n_tracks
+    g = torch.Generator(device=c.dev).manual_seed(3)
+    gp = torch.randn(max(K, 1), 5, device=c.dev, generator=g) * 1e-3
+    gc = torch.randn(max(K, 1), device=c.dev, generator=g) * 1e-2
+    gx, gy, gz = (torch.zeros(c.bufs.n_hits, device=c.dev) for _ in range(3))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tf, tb = [], []
+    for k in range(args.warmup + args.steps):
+        for a in (gx, gy, gz):
+            a.zero_()
+        ev[0].record(c.stream)
+        L.fit_tracks(c.ws, c.nb, c.h, c.cfg, c.tuples, c.tracks, c.s)
+        ev[1].record(c.stream)
+        L.fit_tracks_grad(c.ws, c.nb, c.h, c.cfg, c.tuples, c.tracks, gp.data_ptr(), gc.data_ptr(), gx.data_ptr(),
+                          gy.data_ptr(), gz.data_ptr(), c.s)
+        ev[2].record(c.stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            tf.append(ev[0].elapsed_time(ev[1]))
+            tb.append(ev[1].elapsed_time(ev[2]))
+    fit_ms, adj_ms = statistics.median(tf), statistics.median(tb)
+    return {"tracks": K, "refit_ms": fit_ms, "adjoint_ms": adj_ms,
+            "tracks_per_s_refit_plus_adjoint": K / ((fit_ms + adj_ms) * 1e-3),
+            "note": "gradient of a loss of all track parameters and chi2 with respect to every hit"}
+
+
 def measure_per_event(c, batch):
     """Seconds for the plain per-event GPU form over the batch: the same
     kernels one event at a time, with a host read of the counts after every
@@ -357,9 +390,10 @@ def run_native(args, rank, world, local_rank):
     ctx = Ctx(dev=dev, stream=stream, s=s, ws=ws, nb=nb, h=h, cfg=cfg, cells=cells, edges=edges, tuples=tuples,
               tracks=tracks, flush=flush, counts=counts, pipe=pipe, bufs=bufs, t=t)
 
-    graph_ms = e2e = per_event_s = "skipped"
+    graph_ms = e2e = per_event_s = diff_form = "skipped"
     if not args.no_extras:
         graph_ms = measure_graph(ctx, args)
+        diff_form = measure_differentiable(ctx, args)
         e2e = measure_e2e(ctx, args, batch, world)
         if rank == 0:
             per_event_s = measure_per_event(ctx, batch)
@@ -414,6 +448,7 @@ def run_native(args, rank, world, local_rank):
             "events_per_s": n_ev / per_event_s,
             "note": "same kernels one event at a time, host read of counts after every stage"},
         "e2e": e2e,
+        "differentiable_form": diff_form,
         "roofline": {"bound": "hbm", "kernel": stage_names[dom], "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                      "algorithmic_bytes": stage_bytes[dom], "traffic": measured_traffic(stage_names[dom], D),
