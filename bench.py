@@ -339,6 +339,12 @@ def run_native(args, rank, world, local_rank):
     pipe = Pipeline(G.layers(), G.module_layer_table(), CU.cuts_for_config(3), CU.FIT_PARAMS, device=dev)
     t = {k: torch.as_tensor(batch[k]).to(dev) for k in ("x", "y", "z", "r", "module", "ev_off")}
     args6 = (t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
+    tune = "defaults"
+    if args.autotune:
+        # tile counts, lanes and grid size picked on this batch (results do
+        # not depend on them; the tuner checks that every count is unchanged)
+        timings = pipe.autotune(*args6)
+        tune = f"autotuned over {len(timings)} settings"
     res, bufs = pipe.run(*args6)
     counts = res.counts
     stream = torch.cuda.current_stream(dev)
@@ -437,7 +443,7 @@ def run_native(args, rank, world, local_rank):
                    "events_per_step": n_ev, "hits_per_step": H,
                    "parallelism": f"replicas x{world} (events sharded per rank)",
                    "l2": "512 MiB buffer written between timed steps (L2 flush)",
-                   "tuning": pipe.tuning},
+                   "tuning": pipe.tuning, "tuning_source": tune},
         "tracks_per_s": K * world / (ms_per_step * 1e-3),
         "counts_per_step": {"hits": H, "cells": D, "alive_cells": counts.n_alive_cells, "edges": Ed,
                             "ntuplets": T, "alive_ntuplets": counts.n_alive_tuples, "tracks": K,
@@ -490,6 +496,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--events", type=int, default=EVENTS_PER_STEP,
                     help="events per step (default 64; smaller batches are for profiling runs)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="time the default tuning instead of picking tile counts, lanes and grid size on the batch")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the CUDA-graph, end-to-end and per-event measurements")
     args = ap.parse_args()

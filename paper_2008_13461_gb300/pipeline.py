@@ -85,11 +85,28 @@ class Pipeline:
         cfg.cuts.min_hits = cuts["min_hits"]
         cfg.fit = L.FitParams(fit["bz"], fit["sigma_rphi"], fit["sigma_z"], fit["sigma_r"], fit["x0_barrel"],
                               fit["x0_disk"], int(fit.get("solve_fp32", 0)))
-        t = self.tuning
-        cfg.tuning = L.Tuning(t["n_phi_bins"], t["n_t_bins"], t["doublet_lanes"], t["connect_lanes"],
-                              t["blocks_per_sm"])
         self.cfg = cfg
+        self.set_tuning(self.tuning)
         L.lib()
+
+    def set_tuning(self, tuning: dict) -> None:
+        """Replace the speed knobs (results do not depend on them); buffers
+        must be allocated again, since the workspace size depends on the
+        tile counts.  (A copy of the configuration is made, so a pipeline
+        sharing this one's dictionary is not changed.)"""
+        self.tuning = dict(DEFAULT_TUNING, **tuning)
+        t = self.tuning
+        self.cfg = L.Config.from_buffer_copy(self.cfg)
+        self.cfg.tuning = L.Tuning(t["n_phi_bins"], t["n_t_bins"], t["doublet_lanes"], t["connect_lanes"],
+                                   t["blocks_per_sm"])
+
+    def autotune(self, x, y, z, r, module, ev_off, reps: int = 3) -> dict:
+        """Pick the fastest tuning for this batch (see autotune.py), adopt it
+        and return the timings of the tunings tried."""
+        from .autotune import autotune
+        best, timings = autotune(self, x, y, z, r, module, ev_off, reps=reps)
+        self.set_tuning(best)
+        return timings
 
     # ------------------------------------------------------------ buffers
     @staticmethod
