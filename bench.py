@@ -275,6 +275,15 @@ def measure_differentiable(c, args):
             tf.append(ev[0].elapsed_time(ev[1]))
             tb.append(ev[1].elapsed_time(ev[2]))
     fit_ms, adj_ms = statistics.median(tf), statistics.median(tb)
+    ta = []
+    for k in range(args.warmup + args.steps):
+        ev[0].record(c.stream)
+        keep = c.pipe.resolve_ambiguities(c.bufs, c.counts, c.bufs.n_hits, c.stream)
+        ev[1].record(c.stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            ta.append(ev[0].elapsed_time(ev[1]))
+    c.ambiguity = {"ms": statistics.median(ta), "tracks_kept": int(keep.sum().item()), "tracks": K}
     return {"tracks": K, "refit_ms": fit_ms, "adjoint_ms": adj_ms,
             "tracks_per_s_refit_plus_adjoint": K / ((fit_ms + adj_ms) * 1e-3),
             "note": "gradient of a loss of all track parameters and chi2 with respect to every hit"}
@@ -455,6 +464,7 @@ def run_native(args, rank, world, local_rank):
             "note": "same kernels one event at a time, host read of counts after every stage"},
         "e2e": e2e,
         "differentiable_form": diff_form,
+        "ambiguity_resolution": getattr(ctx, "ambiguity", "skipped"),
         "roofline": {"bound": "hbm", "kernel": stage_names[dom], "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                      "algorithmic_bytes": stage_bytes[dom], "traffic": measured_traffic(stage_names[dom], D),

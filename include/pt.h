@@ -17,8 +17,9 @@
  *   pt_fit_tracks      Sec. 3.4 (broken-line fit: transverse pre-fit, s-z
  *                      line fit, transverse circle fit, combined parameters
  *                      and covariance);
- *   pt_fit_tracks_grad its adjoint (gradient with respect to the hits), and
- *   pt_align_hits[_grad] per-module alignment of the hits and its adjoint.
+ *   pt_fit_tracks_grad its adjoint (gradient with respect to the hits),
+ *   pt_align_hits[_grad] per-module alignment of the hits and its adjoint;
+ *   pt_resolve_ambiguities  Sec. 3.5 (post-fit ambiguity resolution).
  *
  * Conventions shared by every call
  * --------------------------------
@@ -256,6 +257,23 @@ pt_status pt_fit_tracks_grad(void *ws, size_t ws_bytes, const pt_hits *hits, con
                              const pt_tuples *tuples, const pt_tracks *tracks, const float *grad_params,
                              const float *grad_chi2, float *grad_x, float *grad_y, float *grad_z,
                              void *stream);
+
+/* Sec. 3.5: ambiguity resolution of fitted tracks.  Tracks that share a
+ * hit-doublet (a cell) are ambiguous and only the smallest chi2 is kept;
+ * then triplets (3 hits) that share a hit are ambiguous and only the
+ * smallest |transverse impact parameter| is kept.  Equal values are all
+ * kept; the result does not depend on the order of the tracks.
+ *
+ * Track k is n-tuplet track_tuple[k] of `tuples` (its hits, cells and
+ * length), with chi2[k] and impact parameter tip[k * tip_stride] (for
+ * pt_tracks: tip = params + 3, tip_stride = 5).  Cell ids must lie in
+ * [0, n_cells) and hit ids in [0, n_hits) to take part (others are
+ * ignored); NaN chi2 or tip ranks last.  scratch: uint32[n_cells + n_hits]
+ * device work space; keep: uint8[n_tracks] output (1 = kept).  All device
+ * arrays; asynchronous on `stream`. */
+pt_status pt_resolve_ambiguities(const pt_tuples *tuples, const int32_t *track_tuple, int32_t n_tracks,
+                                 const float *chi2, const float *tip, int32_t tip_stride, int32_t n_cells,
+                                 int32_t n_hits, uint32_t *scratch, uint8_t *keep, void *stream);
 
 /* Alignment of the hits (per-module rigid corrections, the quantity whose
  * gradient a track-based alignment needs): a hit on module m moves to

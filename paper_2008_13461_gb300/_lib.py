@@ -93,7 +93,8 @@ class Counts(C.Structure):
 
 # every symbol declared in include/pt.h
 EXPORTS = ("pt_workspace_size", "pt_build_doublets", "pt_connect_cells", "pt_find_ntuplets",
-           "pt_fit_tracks", "pt_fit_tracks_grad", "pt_align_hits", "pt_align_hits_grad", "pt_read_counts",
+           "pt_fit_tracks", "pt_fit_tracks_grad", "pt_align_hits", "pt_align_hits_grad",
+           "pt_resolve_ambiguities", "pt_read_counts",
            "pt_hit_order", "pt_status_string", "pt_bin_hits_noalloc")
 
 _lib = None
@@ -124,6 +125,9 @@ def lib(build_if_missing: bool = True):
     L.pt_fit_tracks.argtypes = common + [P(Tuples), P(Tracks), C.c_void_p]
     L.pt_fit_tracks_grad.restype = C.c_int
     L.pt_fit_tracks_grad.argtypes = common + [P(Tuples), P(Tracks)] + [C.c_void_p] * 6
+    L.pt_resolve_ambiguities.restype = C.c_int
+    L.pt_resolve_ambiguities.argtypes = [P(Tuples), C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                                         C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
     L.pt_align_hits.restype = C.c_int
     L.pt_align_hits.argtypes = [C.c_int32] + [C.c_void_p] * 4 + [C.c_int32] + [C.c_void_p] * 7
     L.pt_align_hits_grad.restype = C.c_int
@@ -181,6 +185,12 @@ def fit_tracks(ws, ws_bytes, hits, cfg, tuples, tracks, stream) -> None:
 def fit_tracks_grad(ws, ws_bytes, hits, cfg, tuples, tracks, grad_params, grad_chi2, gx, gy, gz, stream) -> None:
     check(lib().pt_fit_tracks_grad(ws, ws_bytes, C.byref(hits), C.byref(cfg), C.byref(tuples), C.byref(tracks),
                                    grad_params, grad_chi2, gx, gy, gz, stream), "pt_fit_tracks_grad")
+
+
+def resolve_ambiguities(tuples, track_tuple, n_tracks, chi2, tip, tip_stride, n_cells, n_hits, scratch, keep,
+                        stream) -> None:
+    check(lib().pt_resolve_ambiguities(C.byref(tuples), track_tuple, n_tracks, chi2, tip, tip_stride, n_cells, n_hits,
+                                       scratch, keep, stream), "pt_resolve_ambiguities")
 
 
 def align_hits(n_hits, x, y, z, module, n_modules, centre, shift, rot, xo, yo, zo, stream) -> None:

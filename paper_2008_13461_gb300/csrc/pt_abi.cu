@@ -351,6 +351,25 @@ pt_status pt_fit_tracks_grad(void *ws, size_t ws_bytes, const pt_hits *hits, con
     return launched();
 }
 
+static int align_grid(int32_t n);
+
+pt_status pt_resolve_ambiguities(const pt_tuples *tuples, const int32_t *track_tuple, int32_t n_tracks,
+                                 const float *chi2, const float *tip, int32_t tip_stride, int32_t n_cells,
+                                 int32_t n_hits, uint32_t *scratch, uint8_t *keep, void *stream) {
+    if (n_tracks < 0 || n_cells < 0 || n_hits < 0 || tip_stride < 1) return PT_ERR_INVALID_ARG;
+    if (n_tracks == 0) return PT_OK;
+    if (!tuples || !tuples->hits || !tuples->cells || !tuples->n || !track_tuple || !chi2 || !tip || !keep ||
+        (!scratch && n_cells + n_hits > 0))
+        return PT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_cells + n_hits > 0 &&
+        cudaMemsetAsync(scratch, 0xff, sizeof(uint32_t) * ((size_t)n_cells + (size_t)n_hits), s) != cudaSuccess)
+        return PT_ERR_CUDA;
+    launch_ambiguities(tuples->hits, tuples->cells, tuples->n, track_tuple, n_tracks, chi2, tip, tip_stride, n_cells,
+                       n_hits, scratch, keep, align_grid(n_tracks), s);
+    return launched();
+}
+
 static int align_grid(int32_t n) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);

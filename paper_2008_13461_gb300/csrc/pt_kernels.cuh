@@ -15,6 +15,9 @@ void launch_select(const Params &p, int grid, cudaStream_t s);
 void launch_fit(const Params &p, int grid, cudaStream_t s);
 void launch_fit_grad(const Params &p, const float *gpar, const float *gchi, float *gx, float *gy, float *gz, int grid,
                      cudaStream_t s);
+void launch_ambiguities(const int32_t *hits, const int32_t *cells, const uint8_t *n, const int32_t *track_tuple,
+                        int32_t n_tracks, const float *chi2, const float *tip, int32_t tip_stride, int32_t n_cells,
+                        int32_t n_hits, uint32_t *scratch, uint8_t *keep, int grid, cudaStream_t s);
 void launch_align(int n, const float *x, const float *y, const float *z, const int32_t *module, const float *centre,
                   const float *shift, const float *rot, float *xo, float *yo, float *zo, int grid, cudaStream_t s);
 void launch_align_grad(int n, const float *x, const float *y, const float *z, const int32_t *module,

@@ -183,6 +183,19 @@ class Pipeline:
             hit_order=self.hit_order(bufs, x, y, z, r, module, ev_off),
         )
 
+    def resolve_ambiguities(self, bufs: Buffers, counts: L.Counts, n_hits: int,
+                            stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+        """Post-fit ambiguity resolution (Sec. 3.5) of the fitted tracks:
+        uint8 keep[n_tracks] (1 = kept), enqueued on `stream`."""
+        s = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        k, nc = counts.n_tracks, counts.n_cells
+        keep = torch.empty(max(1, k), dtype=torch.uint8, device=self.device)
+        scratch = torch.empty(max(1, nc + n_hits), dtype=torch.int32, device=self.device)
+        _, _, tuples, _ = bufs.structs()
+        L.resolve_ambiguities(tuples, bufs.trk_tuple.data_ptr(), k, bufs.trk_chi2.data_ptr(),
+                              bufs.trk_params.data_ptr() + 3 * 4, 5, nc, n_hits, scratch.data_ptr(), keep.data_ptr(), s)
+        return keep[:k]
+
     def run(self, x, y, z, r, module, ev_off, bufs: Buffers | None = None, max_retries: int = 3):
         """Run the batch and read the counts back; grow buffers on overflow.
         Returns (Result, Buffers)."""
