@@ -59,3 +59,57 @@ def test_nan_chi2_never_wins():
     H, Cc, n = _tuples(rows)
     keep = postfit.resolve_ambiguities(H, Cc, n, np.arange(2), np.float32([np.nan, 3.0]), np.float32([0, 0]))
     assert keep.tolist() == [False, True]
+
+
+VCUTS = dict(pt_min=0.5, min_hits=4, ez0_max=0.5, dz_cut=0.1, chi2_max=9.0, split_chi2=9.0, min_tracks=2)
+
+
+def _tracks(zs, ez=0.01, pt=1.0, nh=4, ev=0):
+    n = len(zs)
+    return (np.full(n, ev), np.float32(zs), np.full(n, ez, np.float32), np.full(n, pt, np.float32),
+            np.full(n, nh), np.ones(n, bool))
+
+
+def _cat(*parts):
+    return tuple(np.concatenate(a) for a in zip(*parts))
+
+
+def test_vertices_two_separated_clusters_and_noise():
+    a = _tracks([1.000, 1.004, 0.998, 1.002], pt=2.0)
+    b = _tracks([-3.0, -3.006, -2.995], pt=1.0)
+    iso = _tracks([5.0, 7.0])                              # isolated: no vertex
+    soft = _tracks([1.001, 1.003], pt=0.4)                 # below pt_min: ignored
+    short = _tracks([1.0015], nh=3)                        # too few hits: ignored
+    ev, z0, ez, pt, nh, keep = _cat(a, b, iso, soft, short)
+    V, vi = postfit.find_vertices(ev, z0, ez, pt, nh, keep, 1, VCUTS)
+    V = V[0]
+    assert len(V) == 2
+    # sorted by sum pt^2: the 4-track cluster at pt 2 first
+    assert V[0]["tracks"] == [0, 1, 2, 3] and V[1]["tracks"] == [4, 5, 6]
+    w = 1 / np.float64(np.float32(0.01)) ** 2
+    assert abs(V[0]["z"] - np.mean(np.float32([1.000, 1.004, 0.998, 1.002]).astype(np.float64))) < 1e-12
+    assert abs(V[0]["ez"] - 1 / np.sqrt(4 * w)) < 1e-12
+    assert V[0]["sumpt2"] == 16.0 and V[1]["sumpt2"] == 3.0
+    assert vi.tolist() == [0, 0, 0, 0, 1, 1, 1, -1, -1, -1, -1, -1]
+
+
+def test_vertex_with_a_large_chi2_is_split_by_two_means():
+    # two groups 0.06 cm apart, linked into one candidate (dz_cut 0.1 and
+    # loose errors), whose chi2/ndf is large -> split into the two groups
+    zs = [0.0, 0.002, -0.002, 0.06, 0.062, 0.058]
+    ev, z0, ez, pt, nh, keep = _tracks(zs, ez=0.008)
+    cuts = dict(VCUTS, chi2_max=100.0)
+    V, vi = postfit.find_vertices(ev, z0, ez, pt, nh, keep, 1, cuts)
+    assert sorted(v["tracks"] for v in V[0]) == [[0, 1, 2], [3, 4, 5]]
+    # without the split threshold being passed, one vertex
+    V2, _ = postfit.find_vertices(ev, z0, ez, pt, nh, keep, 1, dict(cuts, split_chi2=1e9))
+    assert len(V2[0]) == 1 and len(V2[0][0]["tracks"]) == 6
+
+
+def test_vertices_are_found_per_event():
+    a = _tracks([0.5, 0.502, 0.499], ev=0)
+    b = _tracks([0.5, 0.501], ev=1)
+    ev, z0, ez, pt, nh, keep = _cat(a, b)
+    V, vi = postfit.find_vertices(ev, z0, ez, pt, nh, keep, 2, VCUTS)
+    assert [len(v) for v in V] == [1, 1]
+    assert V[0][0]["tracks"] == [0, 1, 2] and V[1][0]["tracks"] == [3, 4]
