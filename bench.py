@@ -121,10 +121,10 @@ class Clocks:
 
 # ------------------------------------------------------------------ bytes
 # kernels the pipeline launches per step: binning 5 (count, 3 scan passes,
-# fill), doublets 2 (main, exact pass), Fishbone 3 (small, large, exact
-# pass), connection 2 (main, exact pass), n-tuplets 3 (search, 2 cleaning),
-# fit 6 (count and selection, one per hit count 3, 4, 5, 6..8)
-KERNELS_PER_STEP = 21
+# fill), doublets 2 (main, exact pass), Fishbone 4 (small, medium, large,
+# exact pass), connection 2 (main, exact pass), n-tuplets 3 (search, 2
+# cleaning), fit 6 (count and selection, one per hit count 3, 4, 5, 6..8)
+KERNELS_PER_STEP = 22
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "dram_traffic_pu200_batch8.md")
 
 
@@ -284,6 +284,22 @@ def measure_differentiable(c, args):
         if k >= args.warmup:
             ta.append(ev[0].elapsed_time(ev[1]))
     c.ambiguity = {"ms": statistics.median(ta), "tracks_kept": int(keep.sum().item()), "tracks": K}
+    tv = []
+    t = c.t
+    hits = (t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
+    for k in range(args.warmup + args.steps):
+        ev[0].record(c.stream)
+        v, sm = c.pipe.find_vertices(c.bufs, c.counts, *hits, stream=c.stream)
+        ev[1].record(c.stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            tv.append(ev[0].elapsed_time(ev[1]))
+    nv = v["n"].cpu()
+    elig = int((v["track_vertex"] >= 0).sum().item())
+    c.vertexing = {"ms": statistics.median(tv), "vertices_per_event": float(nv.float().mean().item()),
+                   "tracks_in_vertices": elig, "status": int(v["status"].item()),
+                   "note": "ambiguity resolution + track summary + vertex finding on the fitted tracks, "
+                           "default vertex cuts"}
     return {"tracks": K, "refit_ms": fit_ms, "adjoint_ms": adj_ms,
             "tracks_per_s_refit_plus_adjoint": K / ((fit_ms + adj_ms) * 1e-3),
             "note": "gradient of a loss of all track parameters and chi2 with respect to every hit"}
@@ -465,6 +481,7 @@ def run_native(args, rank, world, local_rank):
         "e2e": e2e,
         "differentiable_form": diff_form,
         "ambiguity_resolution": getattr(ctx, "ambiguity", "skipped"),
+        "vertexing": getattr(ctx, "vertexing", "skipped"),
         "roofline": {"bound": "hbm", "kernel": stage_names[dom], "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                      "algorithmic_bytes": stage_bytes[dom], "traffic": measured_traffic(stage_names[dom], D),

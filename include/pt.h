@@ -19,7 +19,8 @@
  *                      and covariance);
  *   pt_fit_tracks_grad its adjoint (gradient with respect to the hits),
  *   pt_align_hits[_grad] per-module alignment of the hits and its adjoint;
- *   pt_resolve_ambiguities  Sec. 3.5 (post-fit ambiguity resolution).
+ *   pt_resolve_ambiguities  Sec. 3.5 (post-fit ambiguity resolution);
+ *   pt_track_summary, pt_find_vertices  Sec. 3.6 (pixel vertices).
  *
  * Conventions shared by every call
  * --------------------------------
@@ -274,6 +275,72 @@ pt_status pt_fit_tracks_grad(void *ws, size_t ws_bytes, const pt_hits *hits, con
 pt_status pt_resolve_ambiguities(const pt_tuples *tuples, const int32_t *track_tuple, int32_t n_tracks,
                                  const float *chi2, const float *tip, int32_t tip_stride, int32_t n_cells,
                                  int32_t n_hits, uint32_t *scratch, uint8_t *keep, void *stream);
+
+/* Sec. 3.6, pixel vertices.  Per-track inputs of the vertex finder (device
+ * arrays of n_tracks): event index, z0 and its error ez0 [cm], pT [GeV], hit
+ * count, and the ambiguity-resolution flag (keep may be NULL: all kept). */
+typedef struct {
+    const int32_t *ev;
+    const float *z0, *ez0, *pt;
+    const uint8_t *nhits, *keep;
+} pt_vertex_tracks;
+
+/* Vertex-finder cuts.  Track i is eligible when kept, nhits >= min_hits,
+ * pt > pt_min, 0 < ez0 < ez0_max, z0 finite and 0 <= ev < n_events.  Tracks
+ * i, j of one event are compatible when dz = z0_i - z0_j (float32) has
+ * |dz| < dz_cut and dz*dz < chi2_max * (ez0_i*ez0_i + ez0_j*ez0_j) (float32,
+ * rounded in that order).  A vertex with chi2/ndf > split_chi2 is split by
+ * 2-means; vertices (and each part of a split) need min_tracks >= 1 tracks. */
+typedef struct {
+    float pt_min, ez0_max, dz_cut, chi2_max, split_chi2;
+    int32_t min_hits, min_tracks;
+} pt_vertex_cuts;
+
+/* Vertices found, per event e at [e * max_vertices, ...) in decreasing sum of
+ * pT^2 (the first is the primary vertex): z, its error ez, chi2, ndf = n-1,
+ * ntracks n, sumpt2; n[e] vertices of event e (at most max_vertices).
+ * track_vertex[n_tracks]: the track's vertex index within its event, -1 for
+ * none.  status[1]: PT_VTX_* bits (0 = complete). */
+typedef struct {
+    int32_t *n;
+    float *z, *ez, *chi2, *sumpt2;
+    int32_t *ndf, *ntracks;
+    int32_t *track_vertex;
+    int32_t *status;
+} pt_vertices;
+
+#define PT_VTX_MAX_TRACKS 16384   /* eligible tracks per event */
+#define PT_VTX_MAX_VERTICES 512   /* vertex candidates per event */
+#define PT_VTX_EVENT_TOO_LARGE 1  /* an event had > PT_VTX_MAX_TRACKS eligible tracks: it got no vertices */
+#define PT_VTX_TOO_MANY 2         /* more than PT_VTX_MAX_VERTICES candidates or max_vertices vertices in an
+                                     event: the extra ones were dropped */
+#define PT_VTX_INTERNAL 4         /* link chains did not resolve (not expected) */
+
+/* Per-track summary of fitted tracks for pt_find_vertices: for track k of
+ * `tracks` (n-tuplet tracks->tuple[k] of `tuples`), ev[k] = the event of its
+ * first hit (by hits->ev_off), z0[k] = params z0, ez0[k] = sqrt(cov z0,z0),
+ * pt[k] = 0.299792458e-2 bz / |kappa| (GeV, bz in T, kappa in 1/cm),
+ * nhits[k] = the n-tuplet length.  Device outputs of n_tracks each. */
+pt_status pt_track_summary(const pt_hits *hits, const pt_tuples *tuples, const pt_tracks *tracks, int32_t n_tracks,
+                           float bz, int32_t *ev, float *z0, float *ez0, float *pt, uint8_t *nhits, void *stream);
+
+/* Bytes of device scratch pt_find_vertices needs. */
+size_t pt_vertex_scratch_size(int32_t n_tracks, int32_t n_events);
+
+/* Sec. 3.6: vertices as clusters of tracks in z0.  Each eligible track gets a
+ * density rho = 1 + the number of compatible tracks; it links to the nearest
+ * compatible track (smallest |dz|, then smallest index) of higher rank
+ * (larger rho, or equal rho and smaller index); every track whose links lead
+ * to a root with rho > 1 joins that root's candidate, and candidates of at
+ * least min_tracks tracks are vertices: z the mean of z0 weighted by
+ * 1/ez0^2, ez = 1/sqrt(sum of weights), chi2 = sum w (z0 - z)^2 (float64).
+ * A vertex with chi2/ndf > split_chi2 is split in two by 2-means in z when
+ * both parts keep min_tracks tracks; vertices are sorted by sum of pT^2.
+ * scratch: device, >= pt_vertex_scratch_size() bytes, 16-byte aligned.
+ * Asynchronous on `stream`; capacity problems are reported in out->status. */
+pt_status pt_find_vertices(const pt_vertex_tracks *tracks, int32_t n_tracks, int32_t n_events,
+                           const pt_vertex_cuts *cuts, int32_t max_vertices, void *scratch, size_t scratch_bytes,
+                           pt_vertices *out, void *stream);
 
 /* Alignment of the hits (per-module rigid corrections, the quantity whose
  * gradient a track-based alignment needs): a hit on module m moves to

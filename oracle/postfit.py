@@ -56,10 +56,26 @@ def _vfit(z0, w):
     return z, 1.0 / np.sqrt(sw), float(np.sum(w * (z0 - z) ** 2))
 
 
+def track_summary(params, cov, tuple_n, first_hit, ev_off, bz):
+    """Per-track inputs of the vertex finder from fitted tracks (Sec. 3.6):
+    the event of the track's first hit, z0, its error sqrt(cov[z0, z0]),
+    pT = 0.299792458 B R with R = 1 / (100 |kappa|) m (kappa in 1/cm, B in
+    T, pT in GeV), and the hit count.  cov rows hold the lower triangle of
+    the 5x5 covariance (kappa, phi0, tan lambda, d0, z0) row by row, so
+    (z0, z0) is entry 14.  float64."""
+    params = np.asarray(params, np.float64)
+    cov = np.asarray(cov, np.float64)
+    ev = np.searchsorted(np.asarray(ev_off), np.asarray(first_hit), side="right") - 1
+    return dict(ev=ev.astype(np.int64), z0=params[:, 4].copy(), ez0=np.sqrt(cov[:, 14]),
+                pt=0.299792458 * bz / (100.0 * np.abs(params[:, 0])), nhits=np.asarray(tuple_n).astype(np.int64))
+
+
 def find_vertices(ev, z0, ez0, pt, nhits, keep, n_events, cuts: dict):
     """Pixel vertices (Sec. 3.6), read as:
 
-    * eligible tracks: kept, nhits >= min_hits, pt > pt_min, ez0 < ez0_max;
+    * eligible tracks: kept (keep None: all), nhits >= min_hits,
+      pt > pt_min, 0 < ez0 < ez0_max, z0 finite (a track without a finite
+      z0 or a positive error has no place in the clustering);
     * density rho_i: the number of eligible tracks j of the same event
       compatible with i, i itself included: |z0_i - z0_j| < dz_cut and
       (z0_i - z0_j)^2 < chi2_max (ez0_i^2 + ez0_j^2) (so rho > 1, the seed
@@ -91,29 +107,35 @@ def find_vertices(ev, z0, ez0, pt, nhits, keep, n_events, cuts: dict):
     pt = np.asarray(pt, f)
     K = len(z0)
     dzc, c2m = f(cuts["dz_cut"]), f(cuts["chi2_max"])
-    elig = np.array([bool(keep[i]) and int(nhits[i]) >= cuts["min_hits"] and pt[i] > f(cuts["pt_min"]) and
-                     ez0[i] < f(cuts["ez0_max"]) for i in range(K)])
+    keep = np.ones(K, bool) if keep is None else np.asarray(keep).astype(bool)
+    ev = np.asarray(ev)
+    elig = keep & (np.asarray(nhits).astype(np.int64) >= cuts["min_hits"]) & (pt > f(cuts["pt_min"])) & \
+        (ez0 > 0) & (ez0 < f(cuts["ez0_max"])) & np.isfinite(z0)
     out_v, vidx = [[] for _ in range(n_events)], np.full(K, -1, np.int64)
     for e in range(n_events):
-        ids = [i for i in range(K) if elig[i] and ev[i] == e]
+        ids = np.nonzero(elig & (ev == e))[0].astype(np.int64)
+        zs, es = z0[ids], ez0[ids]
+        es2 = es * es                                           # float32 products
 
-        def compatible(i, j):
-            dz = f(z0[i] - z0[j])
-            return abs(dz) < dzc and f(dz * dz) < f(c2m * f(f(ez0[i] * ez0[i]) + f(ez0[j] * ez0[j])))
+        def compatible_row(a):
+            """compatible(ids[a], ids[b]) for every b (float32, as written)."""
+            dz = zs[a] - zs                                     # float32
+            return (np.abs(dz) < dzc) & (dz * dz < c2m * (es2[a] + es2))
 
-        rho = {i: 1 + sum(1 for j in ids if j != i and compatible(i, j)) for i in ids}
+        rows = [compatible_row(a) for a in range(len(ids))]
+        for a in range(len(ids)):
+            rows[a][a] = False                                  # j != i
+        R = np.array([1 + int(rows[a].sum()) for a in range(len(ids))], dtype=np.int64)
+        rho = {int(ids[a]): int(R[a]) for a in range(len(ids))}
         parent = {}
-        for i in ids:
-            best = None
-            for j in ids:
-                if j == i or not compatible(i, j):
-                    continue
-                if not (rho[j] > rho[i] or (rho[j] == rho[i] and j < i)):
-                    continue
-                key = (abs(f(z0[i] - z0[j])), j)
-                if best is None or key < best[0]:
-                    best = (key, j)
-            parent[i] = None if best is None else best[1]
+        for a, i in enumerate(ids.tolist()):
+            higher = (R > R[a]) | ((R == R[a]) & (ids < i))
+            cand = np.nonzero(rows[a] & higher)[0]
+            if len(cand) == 0:
+                parent[i] = None
+                continue
+            d = np.abs(zs[a] - zs[cand])                        # float32 |dz|
+            parent[i] = int(ids[cand[d == d.min()]].min())      # nearest, then smallest index
 
         def root(i):
             while parent[i] is not None:
@@ -121,7 +143,7 @@ def find_vertices(ev, z0, ez0, pt, nhits, keep, n_events, cuts: dict):
             return i
 
         groups = {}
-        for i in ids:
+        for i in ids.tolist():
             groups.setdefault(root(i), []).append(i)
         verts = []
         for r, tr in groups.items():
@@ -131,7 +153,7 @@ def find_vertices(ev, z0, ez0, pt, nhits, keep, n_events, cuts: dict):
             zz, ww = z0[tr].astype(np.float64), 1.0 / ez0[tr].astype(np.float64) ** 2
             z, ez, chi2 = _vfit(zz, ww)
             parts = [tr]
-            if len(tr) > 1 and chi2 / (len(tr) - 1) > cuts["split_chi2"]:
+            if len(tr) > 1 and chi2 / (len(tr) - 1) > float(f(cuts["split_chi2"])):
                 lo, hi = zz < z, zz >= z
                 if lo.any() and hi.any():
                     c = [_vfit(zz[lo], ww[lo])[0], _vfit(zz[hi], ww[hi])[0]]

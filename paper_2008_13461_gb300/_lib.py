@@ -85,6 +85,27 @@ class Tracks(C.Structure):
                 ("tuple", C.c_void_p)]
 
 
+class VertexTracks(C.Structure):
+    _fields_ = [("ev", C.c_void_p), ("z0", C.c_void_p), ("ez0", C.c_void_p), ("pt", C.c_void_p),
+                ("nhits", C.c_void_p), ("keep", C.c_void_p)]
+
+
+class VertexCuts(C.Structure):
+    _fields_ = [("pt_min", C.c_float), ("ez0_max", C.c_float), ("dz_cut", C.c_float), ("chi2_max", C.c_float),
+                ("split_chi2", C.c_float), ("min_hits", C.c_int32), ("min_tracks", C.c_int32)]
+
+
+class Vertices(C.Structure):
+    _fields_ = [("n", C.c_void_p), ("z", C.c_void_p), ("ez", C.c_void_p), ("chi2", C.c_void_p),
+                ("sumpt2", C.c_void_p), ("ndf", C.c_void_p), ("ntracks", C.c_void_p),
+                ("track_vertex", C.c_void_p), ("status", C.c_void_p)]
+
+
+PT_VTX_MAX_TRACKS = 16384
+PT_VTX_MAX_VERTICES = 512
+PT_VTX_EVENT_TOO_LARGE, PT_VTX_TOO_MANY, PT_VTX_INTERNAL = 1, 2, 4
+
+
 class Counts(C.Structure):
     _fields_ = [("n_cells", C.c_int64), ("n_edges", C.c_int64), ("n_tuples", C.c_int64),
                 ("n_tracks", C.c_int64), ("n_alive_cells", C.c_int64), ("n_alive_tuples", C.c_int64),
@@ -94,7 +115,8 @@ class Counts(C.Structure):
 # every symbol declared in include/pt.h
 EXPORTS = ("pt_workspace_size", "pt_build_doublets", "pt_connect_cells", "pt_find_ntuplets",
            "pt_fit_tracks", "pt_fit_tracks_grad", "pt_align_hits", "pt_align_hits_grad",
-           "pt_resolve_ambiguities", "pt_read_counts",
+           "pt_resolve_ambiguities", "pt_track_summary", "pt_vertex_scratch_size", "pt_find_vertices",
+           "pt_read_counts",
            "pt_hit_order", "pt_status_string", "pt_bin_hits_noalloc")
 
 _lib = None
@@ -128,6 +150,13 @@ def lib(build_if_missing: bool = True):
     L.pt_resolve_ambiguities.restype = C.c_int
     L.pt_resolve_ambiguities.argtypes = [P(Tuples), C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
                                          C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.pt_track_summary.restype = C.c_int
+    L.pt_track_summary.argtypes = [P(Hits), P(Tuples), P(Tracks), C.c_int32, C.c_float] + [C.c_void_p] * 6
+    L.pt_vertex_scratch_size.restype = C.c_size_t
+    L.pt_vertex_scratch_size.argtypes = [C.c_int32, C.c_int32]
+    L.pt_find_vertices.restype = C.c_int
+    L.pt_find_vertices.argtypes = [P(VertexTracks), C.c_int32, C.c_int32, P(VertexCuts), C.c_int32, C.c_void_p,
+                                   C.c_size_t, P(Vertices), C.c_void_p]
     L.pt_align_hits.restype = C.c_int
     L.pt_align_hits.argtypes = [C.c_int32] + [C.c_void_p] * 4 + [C.c_int32] + [C.c_void_p] * 7
     L.pt_align_hits_grad.restype = C.c_int
@@ -191,6 +220,21 @@ def resolve_ambiguities(tuples, track_tuple, n_tracks, chi2, tip, tip_stride, n_
                         stream) -> None:
     check(lib().pt_resolve_ambiguities(C.byref(tuples), track_tuple, n_tracks, chi2, tip, tip_stride, n_cells, n_hits,
                                        scratch, keep, stream), "pt_resolve_ambiguities")
+
+
+def track_summary(hits, tuples, tracks, n_tracks, bz, ev, z0, ez0, pt, nhits, stream) -> None:
+    check(lib().pt_track_summary(C.byref(hits), C.byref(tuples), C.byref(tracks), n_tracks, bz, ev, z0, ez0, pt,
+                                 nhits, stream), "pt_track_summary")
+
+
+def vertex_scratch_size(n_tracks: int, n_events: int) -> int:
+    return int(lib().pt_vertex_scratch_size(n_tracks, n_events))
+
+
+def find_vertices(tracks: VertexTracks, n_tracks, n_events, cuts: VertexCuts, max_vertices, scratch, scratch_bytes,
+                  out: Vertices, stream) -> None:
+    check(lib().pt_find_vertices(C.byref(tracks), n_tracks, n_events, C.byref(cuts), max_vertices, scratch,
+                                 scratch_bytes, C.byref(out), stream), "pt_find_vertices")
 
 
 def align_hits(n_hits, x, y, z, module, n_modules, centre, shift, rot, xo, yo, zo, stream) -> None:

@@ -403,6 +403,43 @@ pt_status pt_align_hits_grad(int32_t n_hits, const float *x, const float *y, con
     return launched();
 }
 
+pt_status pt_track_summary(const pt_hits *hits, const pt_tuples *tuples, const pt_tracks *tracks, int32_t n_tracks,
+                           float bz, int32_t *ev, float *z0, float *ez0, float *pt, uint8_t *nhits, void *stream) {
+    if (!hits || !tuples || !tracks || n_tracks < 0 || hits->n_events < 1 || !hits->ev_off) return PT_ERR_INVALID_ARG;
+    if (n_tracks == 0) return PT_OK;
+    if (!tuples->hits || !tuples->n || !tracks->params || !tracks->cov || !tracks->tuple || !ev || !z0 || !ez0 ||
+        !pt || !nhits)
+        return PT_ERR_INVALID_ARG;
+    launch_track_summary(n_tracks, tuples->hits, tuples->n, tracks->params, tracks->cov, tracks->tuple, hits->ev_off,
+                         hits->n_events, bz, ev, z0, ez0, pt, nhits, align_grid(n_tracks), (cudaStream_t)stream);
+    return launched();
+}
+
+size_t pt_vertex_scratch_size(int32_t n_tracks, int32_t n_events) {
+    if (n_tracks < 0 || n_events < 0) return 0;
+    return vertex_scratch_bytes(n_tracks, n_events);
+}
+
+pt_status pt_find_vertices(const pt_vertex_tracks *tracks, int32_t n_tracks, int32_t n_events,
+                           const pt_vertex_cuts *cuts, int32_t max_vertices, void *scratch, size_t scratch_bytes,
+                           pt_vertices *out, void *stream) {
+    if (!tracks || !cuts || !out || n_tracks < 0 || n_events < 0 || max_vertices < 1 || cuts->min_tracks < 1)
+        return PT_ERR_INVALID_ARG;
+    if (!out->status) return PT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_events == 0) return cudaMemsetAsync(out->status, 0, sizeof(int32_t), s) == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+    if (!out->n || !out->z || !out->ez || !out->chi2 || !out->sumpt2 || !out->ndf || !out->ntracks ||
+        (n_tracks > 0 && (!out->track_vertex || !tracks->ev || !tracks->z0 || !tracks->ez0 || !tracks->pt ||
+                          !tracks->nhits)))
+        return PT_ERR_INVALID_ARG;
+    if (!scratch || ((uintptr_t)scratch & 15) || scratch_bytes < vertex_scratch_bytes(n_tracks, n_events))
+        return PT_ERR_INVALID_ARG;
+    if ((int64_t)n_events * max_vertices > INT32_MAX) return PT_ERR_INVALID_ARG;
+    const pt_status st = launch_vertices(*tracks, n_tracks, n_events, *cuts, max_vertices, scratch, *out,
+                                         align_grid(n_tracks > 0 ? n_tracks : 1), s);
+    return st != PT_OK ? st : launched();
+}
+
 pt_status pt_read_counts(const void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg,
                          pt_counts *out, void *stream) {
     WsLayout L;

@@ -23,5 +23,12 @@ void launch_align(int n, const float *x, const float *y, const float *z, const i
 void launch_align_grad(int n, const float *x, const float *y, const float *z, const int32_t *module,
                        const float *centre, const float *rot, const float *gxa, const float *gya, const float *gza,
                        float *gx, float *gy, float *gz, float *gshift, float *grot, int grid, cudaStream_t s);
+size_t vertex_scratch_bytes(int32_t n_tracks, int32_t n_events);
+pt_status launch_vertices(const pt_vertex_tracks &in, int32_t n_tracks, int32_t n_events,
+                          const pt_vertex_cuts &cuts, int32_t max_vertices, void *scratch, const pt_vertices &out,
+                          int grid, cudaStream_t s);
+void launch_track_summary(int32_t n_tracks, const int32_t *hits, const uint8_t *tn, const float *params,
+                          const float *cov, const int32_t *tuple, const int32_t *ev_off, int32_t n_events, float bz,
+                          int32_t *ev, float *z0, float *ez0, float *pt, uint8_t *nhits, int grid, cudaStream_t s);
 
 }  // namespace ptk

@@ -1,0 +1,480 @@
+// Pixel vertices (Sec. 3.6): clusters of tracks in z0, the z of each
+// track's point of closest approach to the beam line.
+//
+// Tracks are eligible when kept by the ambiguity resolution, with at least
+// min_hits hits, pT > pt_min, 0 < ez0 < ez0_max and a finite z0.  Two tracks
+// i, j of an event are compatible when dz = z0_i - z0_j satisfies
+// |dz| < dz_cut and dz^2 < chi2_max (ez0_i^2 + ez0_j^2).  A track's density
+// rho is 1 + the number of tracks compatible with it; each track links to the
+// nearest compatible track (smallest |dz|, then smallest index) of higher
+// rank (larger rho, or equal rho and smaller index); the links end at roots
+// (ranks grow along them, so there are no cycles), and a root with rho > 1
+// seeds a candidate made of every track whose links lead to it.  Candidates
+// with at least min_tracks tracks become vertices: z the mean of z0 weighted
+// by 1/ez0^2, ez = 1/sqrt(sum of weights), chi2 = sum w (z0 - z)^2, ndf =
+// n - 1.  A vertex with chi2/ndf > split_chi2 is split by 2-means in z
+// (centres from the tracks below / at-or-above z, each track to the nearer
+// centre, ties to the lower one, until no assignment changes, at most 20
+// rounds) when both parts keep min_tracks tracks.  The vertices of an event
+// are ordered by the sum of pT^2 of their tracks, largest first.
+//
+// Cuts compare float32 values rounded as written (no contraction); sums and
+// the vertex quantities are float64, converted to float32 on output.
+//
+// GPU form: a counting sort groups the eligible tracks by event; one block of
+// 1024 threads per event then sorts its tracks by (z0, index) in shared
+// memory (bitonic), so that every track's compatible tracks lie in a window
+// around it; densities and links come from window scans (one thread per
+// track), roots from pointer jumping, candidates from a second sort of
+// (root, position) keys, and each candidate's fit and 2-means split from one
+// warp (shuffle reductions).
+#include "pt_common.cuh"
+#include "pt_kernels.cuh"
+
+namespace ptk {
+namespace {
+
+constexpr int kVtxMax = PT_VTX_MAX_TRACKS;   // eligible tracks per event (sorted in shared memory)
+constexpr int kPosBits = 14;                 // bits of a sorted position
+constexpr int kPosMask = kVtxMax - 1;
+constexpr int kSideBit = 30;                 // 2-means side of a member, kept in its key
+constexpr int kVtxCap = PT_VTX_MAX_VERTICES; // vertex candidates / vertices per event
+constexpr int kVtxThreads = 1024;
+constexpr size_t kVtxDynSmem = 3 * sizeof(int32_t) * kVtxMax;
+constexpr int kKmeansRounds = 20;
+constexpr unsigned kFull = 0xffffffffu;
+
+static_assert((1 << kPosBits) == kVtxMax, "sorted positions must fit their key field");
+
+struct VtxArgs {
+    int32_t n_tracks, n_events, max_vertices;
+    pt_vertex_tracks in;
+    pt_vertex_cuts cuts;
+    // scratch
+    int32_t *ev_off, *ev_cur, *order, *rho, *root;
+    pt_vertices out;
+};
+
+__device__ __forceinline__ bool eligible(const VtxArgs &a, int i) {
+    const float e = a.in.ez0[i], z = a.in.z0[i];
+    const int ev = a.in.ev[i];
+    return (!a.in.keep || a.in.keep[i]) && (int)a.in.nhits[i] >= a.cuts.min_hits && a.in.pt[i] > a.cuts.pt_min &&
+           e > 0.f && e < a.cuts.ez0_max && fabsf(z) <= 3.402823466e38f && ev >= 0 && ev < a.n_events;
+}
+
+__device__ __forceinline__ void set_status(const VtxArgs &a, int bit) { atomicOr(a.out.status, bit); }
+
+__global__ void __launch_bounds__(kThreads) k_vtx_count(VtxArgs a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_tracks; i += gridDim.x * blockDim.x) {
+        a.out.track_vertex[i] = -1;
+        if (eligible(a, i)) atomicAdd(a.ev_off + a.in.ev[i], 1);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_vtx_fill(VtxArgs a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_tracks; i += gridDim.x * blockDim.x)
+        if (eligible(a, i)) {
+            const int e = a.in.ev[i];
+            a.order[a.ev_off[e] + atomicAdd(a.ev_cur + e, 1)] = i;
+        }
+}
+
+// the chi2 half of the compatibility of a track (squared error ep2) with a
+// track of error eq at distance dz: dz^2 < chi2_max (ep2 + eq^2)
+__device__ __forceinline__ bool chi2_ok(float dz, float ep2, float eq, float c2m) {
+    return __fmul_rn(dz, dz) < __fmul_rn(c2m, __fadd_rn(ep2, __fmul_rn(eq, eq)));
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);    // every lane ends with the same bits
+    return v;
+}
+
+__device__ __forceinline__ int warp_sum(int v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+struct WSums {
+    double sw, swz;
+    int n;
+};
+
+// Weighted sums over the members mk[0, n) of a candidate (one warp); sel < 0:
+// every member, else those whose side bit equals sel.
+__device__ __forceinline__ WSums member_sums(const VtxArgs &a, const int32_t *mk, int n, int sel, const float *sz,
+                                             const int32_t *sid) {
+    double sw = 0.0, swz = 0.0;
+    int c = 0;
+    for (int k = threadIdx.x & 31; k < n; k += 32) {
+        const int32_t kk = mk[k];
+        if (sel >= 0 && ((kk >> kSideBit) & 1) != sel) continue;
+        const int p = kk & kPosMask;
+        const double e = a.in.ez0[sid[p]], w = 1.0 / (e * e);
+        sw += w;
+        swz += w * (double)sz[p];
+        c++;
+    }
+    return WSums{warp_sum(sw), warp_sum(swz), warp_sum(c)};
+}
+
+__device__ __forceinline__ double member_chi2(const VtxArgs &a, const int32_t *mk, int n, int sel, double z,
+                                              const float *sz, const int32_t *sid) {
+    double c = 0.0;
+    for (int k = threadIdx.x & 31; k < n; k += 32) {
+        const int32_t kk = mk[k];
+        if (sel >= 0 && ((kk >> kSideBit) & 1) != sel) continue;
+        const int p = kk & kPosMask;
+        const double e = a.in.ez0[sid[p]], w = 1.0 / (e * e), d = (double)sz[p] - z;
+        c += w * d * d;
+    }
+    return warp_sum(c);
+}
+
+__device__ __forceinline__ double member_sumpt2(const VtxArgs &a, const int32_t *mk, int n, int sel,
+                                                const int32_t *sid) {
+    double s = 0.0;
+    for (int k = threadIdx.x & 31; k < n; k += 32) {
+        const int32_t kk = mk[k];
+        if (sel >= 0 && ((kk >> kSideBit) & 1) != sel) continue;
+        const double t = a.in.pt[sid[kk & kPosMask]];
+        s += t * t;
+    }
+    return warp_sum(s);
+}
+
+// ascending bitonic sort of P entries (P a power of two) under gt
+template <class Gt, class Swap>
+__device__ __forceinline__ void bitonic(int P, Gt gt, Swap swap) {
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int p = threadIdx.x; p < P; p += blockDim.x) {
+                const int q = p ^ j;
+                if (q > p && gt(p, q) == ((p & k) == 0)) swap(p, q);
+            }
+            __syncthreads();
+        }
+}
+
+__global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_event(VtxArgs a) {
+    extern __shared__ __align__(16) unsigned char vsm[];
+    float *sz = reinterpret_cast<float *>(vsm);                   // z0 by sorted position
+    int32_t *sid = reinterpret_cast<int32_t *>(sz + kVtxMax);     // track index by sorted position
+    int32_t *key = sid + kVtxMax;                                 // root << kPosBits | position
+    __shared__ int s_nc, s_nv;
+    __shared__ int s_cq[kVtxCap], s_cn[kVtxCap], s_cv0[kVtxCap], s_cv1[kVtxCap];
+    __shared__ double s_z[kVtxCap], s_sp[kVtxCap];
+    __shared__ float s_ez[kVtxCap], s_c2[kVtxCap];
+    __shared__ int s_nt[kVtxCap], s_vkey[kVtxCap], s_rank[kVtxCap];
+
+    const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int base = a.ev_off[e], cnt = a.ev_off[e + 1] - base;
+    if (cnt > kVtxMax) {                                          // uniform over the block
+        if (tid == 0) {
+            set_status(a, PT_VTX_EVENT_TOO_LARGE);
+            a.out.n[e] = 0;
+        }
+        return;
+    }
+    if (tid == 0) {
+        s_nc = 0;
+        s_nv = 0;
+    }
+    int P = 1;
+    while (P < cnt) P <<= 1;
+    for (int p = tid; p < P; p += blockDim.x) {
+        if (p < cnt) {
+            const int i = a.order[base + p];
+            sz[p] = a.in.z0[i];
+            sid[p] = i;
+        } else {
+            sz[p] = __int_as_float(0x7f800000);
+            sid[p] = 0x7fffffff;
+        }
+    }
+    __syncthreads();
+    bitonic(
+        P, [&](int p, int q) { return sz[p] > sz[q] || (sz[p] == sz[q] && sid[p] > sid[q]); },
+        [&](int p, int q) {
+            const float t = sz[p];
+            sz[p] = sz[q];
+            sz[q] = t;
+            const int u = sid[p];
+            sid[p] = sid[q];
+            sid[q] = u;
+        });
+
+    const float dzc = a.cuts.dz_cut, c2m = a.cuts.chi2_max;
+    int32_t *rho = a.rho + base, *root = a.root + base;
+    // densities: the compatible tracks lie in the window |z0 - z0_p| < dz_cut
+    // (rounded differences are monotonic along the sorted order)
+    for (int p = tid; p < cnt; p += blockDim.x) {
+        const float zp = sz[p], ep = a.in.ez0[sid[p]], ep2 = __fmul_rn(ep, ep);
+        int r = 1;
+        for (int q = p - 1; q >= 0; q--) {
+            const float dz = __fsub_rn(zp, sz[q]);
+            if (!(fabsf(dz) < dzc)) break;
+            r += chi2_ok(dz, ep2, a.in.ez0[sid[q]], c2m);
+        }
+        for (int q = p + 1; q < cnt; q++) {
+            const float dz = __fsub_rn(zp, sz[q]);
+            if (!(fabsf(dz) < dzc)) break;
+            r += chi2_ok(dz, ep2, a.in.ez0[sid[q]], c2m);
+        }
+        rho[p] = r;
+    }
+    __syncthreads();
+    // links to the nearest compatible track of higher rank
+    for (int p = tid; p < cnt; p += blockDim.x) {
+        const float zp = sz[p];
+        const int ip = sid[p], rp = rho[p];
+        const float ep = a.in.ez0[ip], ep2 = __fmul_rn(ep, ep);
+        int best = -1, bid = 0;
+        float bd = 0.f;
+        for (int dir = -1; dir <= 1; dir += 2)
+            for (int q = p + dir; q >= 0 && q < cnt; q += dir) {
+                const float dz = __fsub_rn(zp, sz[q]), ad = fabsf(dz);
+                if (!(ad < dzc)) break;
+                const int iq = sid[q], rq = rho[q];
+                if (!(rq > rp || (rq == rp && iq < ip))) continue;
+                if (!chi2_ok(dz, ep2, a.in.ez0[iq], c2m)) continue;
+                if (best < 0 || ad < bd || (ad == bd && iq < bid)) {
+                    best = q;
+                    bd = ad;
+                    bid = iq;
+                }
+            }
+        root[p] = best < 0 ? p : best;
+    }
+    __syncthreads();
+    // roots by pointer jumping; a racing read sees an old or a new value, both
+    // ancestors, so the iteration still converges (path lengths halve)
+    bool done = false;
+    for (int it = 0; it < 2 * kPosBits + 4 && !done; it++) {
+        bool ch = false;
+        for (int p = tid; p < cnt; p += blockDim.x) {
+            const int r = root[p], rr = root[r];
+            if (rr != r) {
+                root[p] = rr;
+                ch = true;
+            }
+        }
+        done = !__syncthreads_or(ch);
+    }
+    if (!done) {                                                  // uniform over the block
+        if (tid == 0) {
+            set_status(a, PT_VTX_INTERNAL);
+            a.out.n[e] = 0;
+        }
+        return;
+    }
+    // group the tracks by root: sort the (root, position) keys
+    for (int p = tid; p < P; p += blockDim.x) key[p] = p < cnt ? (root[p] << kPosBits | p) : 0x7fffffff;
+    __syncthreads();
+    bitonic(
+        P, [&](int p, int q) { return key[p] > key[q]; },
+        [&](int p, int q) {
+            const int t = key[p];
+            key[p] = key[q];
+            key[q] = t;
+        });
+    // candidates: groups whose root has rho > 1 and at least min_tracks tracks
+    for (int q = tid; q < cnt; q += blockDim.x) {
+        const int r = key[q] >> kPosBits;
+        if (q > 0 && (key[q - 1] >> kPosBits) == r) continue;
+        int n = 1;
+        while (q + n < cnt && (key[q + n] >> kPosBits) == r) n++;
+        if (rho[r] > 1 && n >= a.cuts.min_tracks) {
+            const int c = atomicAdd(&s_nc, 1);
+            if (c < kVtxCap) {
+                s_cq[c] = q;
+                s_cn[c] = n;
+            } else {
+                set_status(a, PT_VTX_TOO_MANY);
+            }
+        }
+    }
+    __syncthreads();
+    const int nc = min(s_nc, kVtxCap);
+    // one warp per candidate: fit, 2-means split, provisional vertices
+    for (int c = wid; c < nc; c += nw) {
+        const int q = s_cq[c], n = s_cn[c];
+        int32_t *mk = key + q;
+        const WSums all = member_sums(a, mk, n, -1, sz, sid);
+        const double z = all.swz / all.sw;
+        const double chi2 = member_chi2(a, mk, n, -1, z, sz, sid);
+        bool split = false;
+        if (n > 1 && chi2 / (double)(n - 1) > (double)a.cuts.split_chi2) {
+            int hi = 0;
+            for (int k = lane; k < n; k += 32) {
+                const int32_t kk = mk[k];
+                const int s = (double)sz[kk & kPosMask] >= z;
+                mk[k] = (kk & ~(1 << kSideBit)) | (s << kSideBit);
+                hi += s;
+            }
+            hi = warp_sum(hi);
+            __syncwarp();
+            if (hi > 0 && hi < n) {
+                WSums s0 = member_sums(a, mk, n, 0, sz, sid), s1 = member_sums(a, mk, n, 1, sz, sid);
+                double c0 = s0.swz / s0.sw, c1 = s1.swz / s1.sw;
+                int up = 0;
+                bool have = false;
+                for (int round = 0; round < kKmeansRounds; round++) {
+                    bool diff = false;
+                    up = 0;
+                    for (int k = lane; k < n; k += 32) {
+                        const int32_t kk = mk[k];
+                        const double zz = sz[kk & kPosMask];
+                        const int u = fabs(zz - c1) < fabs(zz - c0);      // ties: the lower centre
+                        diff |= u != ((kk >> kSideBit) & 1);
+                        mk[k] = (kk & ~(1 << kSideBit)) | (u << kSideBit);
+                        up += u;
+                    }
+                    up = warp_sum(up);
+                    diff = __any_sync(kFull, diff);
+                    __syncwarp();
+                    if (have && !diff) break;
+                    have = true;
+                    if (up == 0 || up == n) break;
+                    s0 = member_sums(a, mk, n, 0, sz, sid);
+                    s1 = member_sums(a, mk, n, 1, sz, sid);
+                    c0 = s0.swz / s0.sw;
+                    c1 = s1.swz / s1.sw;
+                }
+                split = up >= a.cuts.min_tracks && n - up >= a.cuts.min_tracks;
+            }
+        }
+        for (int part = 0; part < (split ? 2 : 1); part++) {
+            const int sel = split ? part : -1;
+            const WSums s = member_sums(a, mk, n, sel, sz, sid);
+            const double zv = s.swz / s.sw;
+            const double c2v = member_chi2(a, mk, n, sel, zv, sz, sid);
+            const double sp = member_sumpt2(a, mk, n, sel, sid);
+            int v = 0;
+            if (lane == 0) {
+                v = atomicAdd(&s_nv, 1);
+                if (v < kVtxCap) {
+                    s_z[v] = zv;
+                    s_ez[v] = (float)(1.0 / sqrt(s.sw));
+                    s_c2[v] = (float)c2v;
+                    s_nt[v] = s.n;
+                    s_sp[v] = sp;
+                    s_vkey[v] = 2 * q + part;
+                } else {
+                    set_status(a, PT_VTX_TOO_MANY);
+                }
+                if (part == 0) s_cv0[c] = v;
+                else s_cv1[c] = v;
+                if (!split) s_cv1[c] = -1;
+            }
+        }
+    }
+    __syncthreads();
+    // order: sum pT^2 descending, then z, then the (root, part) key
+    const int nv = min(s_nv, kVtxCap);
+    for (int v = tid; v < nv; v += blockDim.x) {
+        const double sv = s_sp[v], zv = s_z[v];
+        const int kv = s_vkey[v];
+        int r = 0;
+        for (int u = 0; u < nv; u++)
+            r += s_sp[u] > sv || (s_sp[u] == sv && (s_z[u] < zv || (s_z[u] == zv && s_vkey[u] < kv)));
+        s_rank[v] = r;
+        if (r < a.max_vertices) {
+            const int64_t o = (int64_t)e * a.max_vertices + r;
+            a.out.z[o] = (float)zv;
+            a.out.ez[o] = s_ez[v];
+            a.out.chi2[o] = s_c2[v];
+            a.out.ndf[o] = s_nt[v] - 1;
+            a.out.ntracks[o] = s_nt[v];
+            a.out.sumpt2[o] = (float)sv;
+        }
+    }
+    if (tid == 0) {
+        a.out.n[e] = min(nv, a.max_vertices);
+        if (nv > a.max_vertices) set_status(a, PT_VTX_TOO_MANY);
+    }
+    __syncthreads();
+    for (int c = wid; c < nc; c += nw) {
+        const int q = s_cq[c], n = s_cn[c], v0 = s_cv0[c], v1 = s_cv1[c];
+        for (int k = lane; k < n; k += 32) {
+            const int32_t kk = key[q + k];
+            const int v = (v1 >= 0 && ((kk >> kSideBit) & 1)) ? v1 : v0;
+            if (v < nv && s_rank[v] < a.max_vertices) a.out.track_vertex[sid[kk & kPosMask]] = s_rank[v];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_track_summary(int32_t n_tracks, const int32_t *hits, const uint8_t *tn,
+                                                            const float *params, const float *cov,
+                                                            const int32_t *tuple, const int32_t *ev_off,
+                                                            int32_t n_events, float pt_of_kappa, int32_t *ev,
+                                                            float *z0, float *ez0, float *pt, uint8_t *nh) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_tracks; k += gridDim.x * blockDim.x) {
+        const int t = tuple[k];
+        const int h = hits[(int64_t)t * PT_NMAX];
+        int lo = 0, hi = n_events;                       // the last e with ev_off[e] <= h
+        while (hi - lo > 1) {
+            const int m = (lo + hi) >> 1;
+            if (ev_off[m] <= h) lo = m;
+            else hi = m;
+        }
+        ev[k] = lo;
+        z0[k] = params[(int64_t)k * 5 + 4];
+        ez0[k] = sqrtf(cov[(int64_t)k * 15 + 14]);
+        pt[k] = pt_of_kappa / fabsf(params[(int64_t)k * 5]);
+        nh[k] = tn[t];
+    }
+}
+
+}  // namespace
+
+size_t vertex_scratch_bytes(int32_t n_tracks, int32_t n_events) {
+    return sizeof(int32_t) * (2 * ((size_t)n_events + 1) + (size_t)n_events / kScanItems + 2 +
+                              3 * ((size_t)n_tracks + 1)) +
+           256;
+}
+
+pt_status launch_vertices(const pt_vertex_tracks &in, int32_t n_tracks, int32_t n_events,
+                          const pt_vertex_cuts &cuts, int32_t max_vertices, void *scratch, const pt_vertices &out,
+                          int grid, cudaStream_t s) {
+    VtxArgs a;
+    a.n_tracks = n_tracks;
+    a.n_events = n_events;
+    a.max_vertices = max_vertices;
+    a.in = in;
+    a.cuts = cuts;
+    int32_t *w = (int32_t *)scratch;
+    a.ev_off = w;
+    a.ev_cur = a.ev_off + (n_events + 1);
+    int32_t *part = a.ev_cur + (n_events + 1);
+    a.order = part + (n_events / kScanItems + 2);
+    a.rho = a.order + (n_tracks + 1);
+    a.root = a.rho + (n_tracks + 1);
+    a.out = out;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_vtx_event, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVtxDynSmem) !=
+            cudaSuccess)
+            return PT_ERR_CUDA;
+        attr = true;
+    }
+    if (cudaMemsetAsync(w, 0, sizeof(int32_t) * 2 * ((size_t)n_events + 1), s) != cudaSuccess ||
+        cudaMemsetAsync(out.status, 0, sizeof(int32_t), s) != cudaSuccess)
+        return PT_ERR_CUDA;
+    k_vtx_count<<<grid, kThreads, 0, s>>>(a);
+    launch_scan(a.ev_off, n_events, part, s);
+    k_vtx_fill<<<grid, kThreads, 0, s>>>(a);
+    k_vtx_event<<<n_events, kVtxThreads, kVtxDynSmem, s>>>(a);
+    return PT_OK;
+}
+
+void launch_track_summary(int32_t n_tracks, const int32_t *hits, const uint8_t *tn, const float *params,
+                          const float *cov, const int32_t *tuple, const int32_t *ev_off, int32_t n_events, float bz,
+                          int32_t *ev, float *z0, float *ez0, float *pt, uint8_t *nhits, int grid, cudaStream_t s) {
+    // pT [GeV] = 0.299792458 B[T] R[m], R = 1 / (100 |kappa|) with kappa in 1/cm
+    const float pt_of_kappa = 0.299792458e-2f * bz;
+    k_track_summary<<<grid, kThreads, 0, s>>>(n_tracks, hits, tn, params, cov, tuple, ev_off, n_events, pt_of_kappa,
+                                             ev, z0, ez0, pt, nhits);
+}
+
+}  // namespace ptk

@@ -18,6 +18,12 @@ from . import _lib as L
 
 DEFAULT_TUNING = dict(n_phi_bins=128, n_t_bins=32, doublet_lanes=8, connect_lanes=8, blocks_per_sm=8)
 
+# Vertex-finder cuts (Sec. 3.6 fixes pT > 0.5 GeV, >= 4 hits, the split at
+# chi2/ndf > 9 and >= 2 tracks per vertex; the z0-error, dz and chi2
+# compatibility thresholds are configurable there without values).
+DEFAULT_VERTEX_CUTS = dict(pt_min=0.5, min_hits=4, ez0_max=0.05, dz_cut=0.07, chi2_max=9.0, split_chi2=9.0,
+                           min_tracks=2)
+
 
 def _ptr(t: torch.Tensor | None) -> int | None:
     return None if t is None else t.data_ptr()
@@ -52,6 +58,49 @@ class Buffers:
         tracks = L.Tracks(_ptr(self.trk_params), _ptr(self.trk_cov), _ptr(self.trk_chi2), _ptr(self.trk_ndf),
                           _ptr(self.trk_tuple))
         return cells, edges, tuples, tracks
+
+
+def find_vertices(ev, z0, ez0, pt, nhits, keep, n_events: int, cuts: dict | None = None, max_vertices: int = 256,
+                  stream: torch.cuda.Stream | None = None) -> dict:
+    """Pixel vertices (Sec. 3.6) of per-track summaries (device tensors of
+    n_tracks: ev int32, z0 / ez0 / pt float32, nhits uint8, keep uint8 or
+    None), enqueued on `stream`.  Returns device tensors: n[E], z, ez, chi2,
+    sumpt2, ndf, ntracks [E, max_vertices] (event e's first n[e] rows, in
+    decreasing sum pT^2), track_vertex[n_tracks] and status[1] (PT_VTX_*)."""
+    c = dict(DEFAULT_VERTEX_CUTS, **(cuts or {}))
+    dev = z0.device
+    s = (stream or torch.cuda.current_stream(dev)).cuda_stream
+    k = z0.numel()
+    for t, dt in ((ev, torch.int32), (z0, torch.float32), (ez0, torch.float32), (pt, torch.float32),
+                  (nhits, torch.uint8)) + (((keep, torch.uint8),) if keep is not None else ()):
+        if t.dtype != dt or not t.is_contiguous() or t.numel() != k:
+            raise ValueError("find_vertices: per-track tensors must be contiguous, of equal length and dtypes "
+                             "int32 / float32 x3 / uint8 / uint8")
+    E, M = n_events, max_vertices
+    out = dict(n=torch.empty(max(1, E), dtype=torch.int32, device=dev),
+               z=torch.empty(max(1, E * M), dtype=torch.float32, device=dev),
+               ez=torch.empty(max(1, E * M), dtype=torch.float32, device=dev),
+               chi2=torch.empty(max(1, E * M), dtype=torch.float32, device=dev),
+               sumpt2=torch.empty(max(1, E * M), dtype=torch.float32, device=dev),
+               ndf=torch.empty(max(1, E * M), dtype=torch.int32, device=dev),
+               ntracks=torch.empty(max(1, E * M), dtype=torch.int32, device=dev),
+               track_vertex=torch.empty(max(1, k), dtype=torch.int32, device=dev),
+               status=torch.zeros(1, dtype=torch.int32, device=dev))
+    nbytes = L.vertex_scratch_size(k, E)
+    scratch = torch.empty((nbytes + 15) // 16, dtype=torch.int64, device=dev)
+    trk = L.VertexTracks(ev.data_ptr(), z0.data_ptr(), ez0.data_ptr(), pt.data_ptr(), nhits.data_ptr(),
+                         _ptr(keep))
+    vc = L.VertexCuts(c["pt_min"], c["ez0_max"], c["dz_cut"], c["chi2_max"], c["split_chi2"], int(c["min_hits"]),
+                      int(c["min_tracks"]))
+    vo = L.Vertices(*(out[n].data_ptr() for n in ("n", "z", "ez", "chi2", "sumpt2", "ndf", "ntracks",
+                                                    "track_vertex", "status")))
+    L.find_vertices(trk, k, E, vc, M, scratch.data_ptr(), scratch.numel() * 16, vo, s)
+    out["scratch"] = scratch                                   # kept alive until the stream has used it
+    res = {n: (t[:E * M].view(E, M) if n in ("z", "ez", "chi2", "sumpt2", "ndf", "ntracks") else t)
+           for n, t in out.items()}
+    res["n"] = out["n"][:E]
+    res["track_vertex"] = out["track_vertex"][:k]
+    return res
 
 
 @dataclasses.dataclass
@@ -195,6 +244,34 @@ class Pipeline:
         L.resolve_ambiguities(tuples, bufs.trk_tuple.data_ptr(), k, bufs.trk_chi2.data_ptr(),
                               bufs.trk_params.data_ptr() + 3 * 4, 5, nc, n_hits, scratch.data_ptr(), keep.data_ptr(), s)
         return keep[:k]
+
+    def track_summary(self, bufs: Buffers, counts: L.Counts, x, y, z, r, module, ev_off,
+                      stream: torch.cuda.Stream | None = None) -> dict:
+        """Per-track inputs of the vertex finder for the fitted tracks:
+        ev, z0, ez0, pt, nhits (device tensors of n_tracks)."""
+        s = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        k = counts.n_tracks
+        o = dict(ev=torch.empty(max(1, k), dtype=torch.int32, device=self.device),
+                 z0=torch.empty(max(1, k), dtype=torch.float32, device=self.device),
+                 ez0=torch.empty(max(1, k), dtype=torch.float32, device=self.device),
+                 pt=torch.empty(max(1, k), dtype=torch.float32, device=self.device),
+                 nhits=torch.empty(max(1, k), dtype=torch.uint8, device=self.device))
+        _, _, tuples, tracks = bufs.structs()
+        L.track_summary(self._hits(x, y, z, r, module, ev_off), tuples, tracks, k, self.cfg.fit.bz,
+                        o["ev"].data_ptr(), o["z0"].data_ptr(), o["ez0"].data_ptr(), o["pt"].data_ptr(),
+                        o["nhits"].data_ptr(), s)
+        return {n: t[:k] for n, t in o.items()}
+
+    def find_vertices(self, bufs: Buffers, counts: L.Counts, x, y, z, r, module, ev_off, cuts: dict | None = None,
+                      max_vertices: int = 256, stream: torch.cuda.Stream | None = None) -> tuple[dict, dict]:
+        """Sec. 3.5 + 3.6 on the fitted tracks: ambiguity resolution, track
+        summaries, vertices.  Returns (vertices, summaries incl. keep)."""
+        keep = self.resolve_ambiguities(bufs, counts, x.numel(), stream)
+        sm = self.track_summary(bufs, counts, x, y, z, r, module, ev_off, stream)
+        sm["keep"] = keep
+        v = find_vertices(sm["ev"], sm["z0"], sm["ez0"], sm["pt"], sm["nhits"], keep.contiguous(),
+                          ev_off.numel() - 1, cuts, max_vertices, stream)
+        return v, sm
 
     def run(self, x, y, z, r, module, ev_off, bufs: Buffers | None = None, max_retries: int = 3):
         """Run the batch and read the counts back; grow buffers on overflow.

@@ -113,3 +113,25 @@ def test_vertices_are_found_per_event():
     V, vi = postfit.find_vertices(ev, z0, ez, pt, nh, keep, 2, VCUTS)
     assert [len(v) for v in V] == [1, 1]
     assert V[0][0]["tracks"] == [0, 1, 2] and V[1][0]["tracks"] == [3, 4]
+
+
+def test_track_summary_inverts_the_generator_curvature_and_reads_the_z0_variance():
+    from synth import events as E
+    pt = np.array([0.5, 1.0, 7.3, 42.0])
+    kappa = 1.0 / E.rho_of_pt(pt)                     # the generator's radius of curvature (cm) for pT
+    params = np.zeros((4, 5))
+    params[:, 0] = kappa * np.array([1, -1, 1, -1])   # either charge
+    params[:, 4] = [0.1, -3.0, 2.5, 0.0]
+    cov = np.zeros((4, 15))
+    for k in range(4):                                # lower triangle of a 5x5, row by row
+        M = np.arange(25, dtype=np.float64).reshape(5, 5) + k
+        M = M + M.T
+        cov[k] = [M[i, j] for i in range(5) for j in range(i + 1)]
+    ev_off = np.array([0, 10, 10, 25])                # the middle event is empty
+    first = np.array([0, 9, 10, 24])
+    s = postfit.track_summary(params, cov, np.array([3, 4, 5, 6]), first, ev_off, E.BZ_TESLA)
+    assert np.allclose(s["pt"], pt, rtol=1e-12)
+    assert np.array_equal(s["ev"], [0, 0, 2, 2])
+    assert np.allclose(s["ez0"] ** 2, [2 * (24 + k) for k in range(4)])   # M[4, 4] = 2 (24 + k)
+    assert np.array_equal(s["z0"], params[:, 4])
+    assert np.array_equal(s["nhits"], [3, 4, 5, 6])
