@@ -122,9 +122,10 @@ class Clocks:
 # ------------------------------------------------------------------ bytes
 # kernels the pipeline launches per step: binning 5 (count, 3 scan passes,
 # fill), doublets 2 (main, exact pass), Fishbone 4 (small, medium, large,
-# exact pass), connection 2 (main, exact pass), n-tuplets 3 (search, 2
-# cleaning), fit 6 (count and selection, one per hit count 3, 4, 5, 6..8)
-KERNELS_PER_STEP = 22
+# exact pass), connection 2 (main, exact pass), n-tuplets 4 (edge records,
+# search, 2 cleaning), fit 6 (count and selection, one per hit count 3, 4,
+# 5, 6..8)
+KERNELS_PER_STEP = 23
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "dram_traffic_pu200_batch8.md")
 
 
@@ -365,7 +366,10 @@ def run_native(args, rank, world, local_rank):
     t = {k: torch.as_tensor(batch[k]).to(dev) for k in ("x", "y", "z", "r", "module", "ev_off")}
     args6 = (t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
     tune = "defaults"
-    if args.autotune:
+    if args.tuning:
+        pipe.set_tuning(dict((k, int(v)) for k, v in (kv.split("=") for kv in args.tuning.split(","))))
+        tune = "given"
+    elif args.autotune:
         # tile counts, lanes and grid size picked on this batch (results do
         # not depend on them; the tuner checks that every count is unchanged)
         timings = pipe.autotune(*args6)
@@ -525,6 +529,8 @@ def main():
                     help="events per step (default 64; smaller batches are for profiling runs)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="time the default tuning instead of picking tile counts, lanes and grid size on the batch")
+    ap.add_argument("--tuning", default="",
+                    help="explicit pt_tuning as k=v,k=v (skips the autotuner), e.g. to profile a tuned run")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the CUDA-graph, end-to-end and per-event measurements")
     args = ap.parse_args()

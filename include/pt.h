@@ -169,7 +169,8 @@ typedef struct {
 } pt_config;
 
 /* Hits of a batch of events (structure of arrays, device).  Event e owns
- * hits [ev_off[e], ev_off[e+1]); ev_off[0] = 0, ev_off[n_events] = n_hits. */
+ * hits [ev_off[e], ev_off[e+1]); ev_off[0] = 0, ev_off[n_events] = n_hits;
+ * n_hits at most 2^30. */
 typedef struct {
     const float *x, *y, *z, *r;
     const int32_t *module;

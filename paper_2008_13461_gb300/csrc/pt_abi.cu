@@ -62,6 +62,7 @@ bool layout(const pt_hits *h, const pt_config *cfg, WsLayout &L) {
     L.edge_rng = take(8 * nc);
     L.has_out = take(nc);
     L.maxlen = take(4 * nc);
+    L.erec = take(16 * (size_t)(cfg->capacity.edges > 0 ? cfg->capacity.edges : 1));
     L.trk_blk = take(sizeof(int32_t) * 4 * kSelBlocks);
     L.total = o;
     return true;
@@ -129,7 +130,7 @@ bool config_ok(const pt_config *cfg) {
 }
 
 bool hits_ok(const pt_hits *h) {
-    if (!h || h->n_hits < 0 || h->n_events < 1 || !h->ev_off) return false;
+    if (!h || h->n_hits < 0 || h->n_hits > (1 << 30) || h->n_events < 1 || !h->ev_off) return false;
     if (h->n_hits > 0 && (!h->x || !h->y || !h->z || !h->r || !h->module)) return false;
     return true;
 }
@@ -179,6 +180,7 @@ Params make_params(void *ws, const WsLayout &L, const pt_hits *h, const pt_confi
     p.edge_rng = (int2 *)(w + L.edge_rng);
     p.has_out = (uint8_t *)(w + L.has_out);
     p.maxlen = (int32_t *)(w + L.maxlen);
+    p.erec = (int4 *)(w + L.erec);
     p.trk_blk = (int32_t *)(w + L.trk_blk);
     p.cap_cells = cfg->capacity.cells;
     p.cap_edges = cfg->capacity.edges;

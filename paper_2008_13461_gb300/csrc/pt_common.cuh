@@ -37,7 +37,7 @@ __device__ __forceinline__ int track_class(int n) { return min(n, 6) - 3; }
 struct WsLayout {
     size_t counters, bin_cnt, scan_part, hit_bin, hit_rank;
     size_t bh, blayer, bev, perm, in_off, in_cnt, in_live, hk, ck, sk, sci, leaf_list, trk_blk;
-    size_t edge_rng, has_out, maxlen;
+    size_t edge_rng, has_out, maxlen, erec;
     size_t total;
     int64_t n_bins;        // events * layers * phi bins * t bins
     int32_t n_scan_blocks;
@@ -59,6 +59,8 @@ struct Params {
     int32_t *bev, *perm, *in_off, *in_cnt;
     int32_t *fb_big;                     // outer hits with many cells (reuses hit_rank after binning)
     int2 *edge_rng;                      // per cell: (first incoming edge, count)
+    int4 *erec;                          // per edge: its source cell, that cell's (first, count) of
+                                         //   incoming edges, input index of its inner hit * 2 + root
     int32_t *leaf_list;
     float *ck;                           // R-z slope key of each cell w.r.t. its outer hit (scratch)
     float2 *hk;                          // per hit: max sqrt(1+key^2), min gap of its incoming cells
@@ -110,8 +112,10 @@ __device__ __forceinline__ bool upstream_overflow(const Params &p, uint32_t mask
 }
 
 __device__ __forceinline__ long long grid_int(float v) {
-    // exact: v is a multiple of 2^-14 below 64 in magnitude
-    return __float2ll_rn(v * 16384.0f);
+    // exact: v is a multiple of 2^-14 below 2^17 in magnitude (hits below 64
+    // and their differences), so v * 2^14 is an integer that fits 32 bits;
+    // the 32-bit conversion avoids the 64-bit one, which is slow here
+    return (long long)__float2int_rn(v * 16384.0f);
 }
 
 // Azimuthal tile of angle phi in [-pi, pi]: monotone in phi, clamped.

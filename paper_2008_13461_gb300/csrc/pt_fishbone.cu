@@ -39,13 +39,17 @@ constexpr int kFbDirect = 12;        // up to this many siblings: compare all pa
 
 // Per warp and cell: u = h_inner - h_o (exact) and 1/|u| in w; the cell's
 // position (bits 0-9), its inner layer (10-14) and key bucket (15-24).
-template <int W, int M, int NB>
+// C: the cell's R-z slope key and inner hit are kept for the second pass
+// (else written to and read back from global memory).
+template <int W, int M, int NB, bool C>
 struct FbSmem {
     float4 rec[W][M];
     int meta[W][M];
     int16_t idx[W][M];               // cell positions sorted by bucket
     uint8_t dead[W][M];
     int pos[W][NB];
+    float ck[W][C ? M : 1];
+    int32_t inner[W][C ? M : 1];
 };
 
 __device__ __forceinline__ int rec_cell(int m) { return m & 1023; }
@@ -61,8 +65,8 @@ __device__ __forceinline__ float fb_key(const float4 &r, bool disk, float rx, fl
 
 // squared length of a difference vector, in grid units (exact)
 __device__ __forceinline__ long long len2u(float ux, float uy, float uz) {
-    const long long x = grid_int(ux), y = grid_int(uy), z = grid_int(uz);
-    return x * x + y * y + z * z;
+    const int x = __float2int_rn(ux * 16384.0f), y = __float2int_rn(uy * 16384.0f), z = __float2int_rn(uz * 16384.0f);
+    return (long long)x * x + (long long)y * y + (long long)z * z;     // |x| < 2^21: 32x32 -> 64-bit products
 }
 
 __device__ __forceinline__ int cell_layer(const Params &p, int64_t c) { return p.pair[p.cell_pair[c]].inner; }
@@ -109,9 +113,9 @@ __device__ __forceinline__ void warp_exclusive_scan(int *a, int nb, int lane) {
 // count of live cells.  kGlobal: n may exceed M (pairwise loop compiled in).
 // kExact = false (float32 filters only): returns -1, having written no
 // verdict, when n > M or an alignment test is undecided.
-template <int W, int M, int NB, bool kGlobal, bool kExact>
+template <int W, int M, int NB, bool kGlobal, bool kExact, bool C>
 __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64_t b, int lane, int w,
-                                            float unit_thr, float du, FbSmem<W, M, NB> &sm) {
+                                            float unit_thr, float du, FbSmem<W, M, NB, C> &sm) {
     if (!kExact && n > M) return -1;
     const float4 ho = __ldg(p.bh + o);
     const bool disk = p.layer[p.blayer[o]].kind == PT_LAYER_DISK;
@@ -131,7 +135,12 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
         const float ck = den != 0.f ? num / den : __int_as_float(0x7f800000);
         kmax = fmaxf(kmax, sqrtf(1.0f + ck * ck));
         gmin = fminf(gmin, fabsf(den));
-        p.ck[b + j] = ck;
+        if (C && in_smem) {
+            sm.ck[w][j] = ck;
+            sm.inner[w][j] = i;
+        } else {
+            p.ck[b + j] = ck;
+        }
         if (in_smem) {
             const float ux = a.x - ho.x, uy = a.y - ho.y, uz = a.z - ho.z;
             const float4 r = make_float4(ux, uy, uz, rsqrtf(ux * ux + uy * uy + uz * uz));
@@ -268,8 +277,8 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
                 p.cell_alive[b + j] = 0;
                 continue;
             }
-            const float key = p.ck[b + j];
-            const int ii = p.cell_inner[b + j];
+            const float key = C ? sm.ck[w][j] : p.ck[b + j];
+            const int ii = C ? sm.inner[w][j] : p.cell_inner[b + j];
             sm.rec[w][j] = make_float4(key, __int_as_float(ii), 0.f, 0.f);
             if (fabsf(key) <= 3.4e38f) {
                 smin = fminf(smin, key);
@@ -365,7 +374,7 @@ constexpr int kFbMidMax = 320;
 
 template <int W, int M, int NB, int kMinBlocks>
 __global__ void __launch_bounds__(32 * W, kMinBlocks) k_fishbone_small(Params p, float unit_thr, float du) {
-    __shared__ FbSmem<W, M, NB> sm;
+    __shared__ FbSmem<W, M, NB, true> sm;
     if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned below = (1u << lane) - 1u;
@@ -403,7 +412,8 @@ __global__ void __launch_bounds__(32 * W, kMinBlocks) k_fishbone_small(Params p,
             todo &= todo - 1;
             const int n = __shfl_sync(0xffffffffu, nl, t);
             const int b = __shfl_sync(0xffffffffu, bl, t);
-            const int a = fishbone_hit<W, M, NB, false, false>(p, (ch << 5) + t, n, b, lane, w, unit_thr, du, sm);
+            const int a = fishbone_hit<W, M, NB, false, false, true>(p, (ch << 5) + t, n, b, lane, w, unit_thr, du,
+                                                                     sm);
             if (a >= 0) my_alive += a;
             else list_pending(p, (ch << 5) + t, lane);
         }
@@ -413,9 +423,9 @@ __global__ void __launch_bounds__(32 * W, kMinBlocks) k_fishbone_small(Params p,
 
 // Larger warps: the listed outer hits, one at a time from a queue (kFromBack:
 // the list at the back of the array).
-template <int W, int M, int NB, bool kFromBack>
+template <int W, int M, int NB, bool kFromBack, bool C>
 __global__ void __launch_bounds__(32 * W) k_fishbone_large(Params p, float unit_thr, float du) {
-    __shared__ FbSmem<W, M, NB> sm;
+    __shared__ FbSmem<W, M, NB, C> sm;
     if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int my_alive = 0;
@@ -426,7 +436,8 @@ __global__ void __launch_bounds__(32 * W) k_fishbone_large(Params p, float unit_
         k = __shfl_sync(0xffffffffu, k, 0);
         if (k >= n_list) break;
         const int o = p.fb_big[kFromBack ? p.n_hits - 1 - k : k];
-        const int a = fishbone_hit<W, M, NB, false, false>(p, o, p.in_cnt[o], p.in_off[o], lane, w, unit_thr, du, sm);
+        const int a = fishbone_hit<W, M, NB, false, false, C>(p, o, p.in_cnt[o], p.in_off[o], lane, w, unit_thr, du,
+                                                              sm);
         if (a >= 0) my_alive += a;
         else list_pending(p, o, lane);
     }
@@ -438,22 +449,22 @@ __global__ void __launch_bounds__(32 * W) k_fishbone_large(Params p, float unit_
 // predicate and the pairwise loop for any number of cells.
 template <int W, int M, int NB>
 __global__ void __launch_bounds__(32 * W) k_fishbone_exact(Params p, float unit_thr, float du) {
-    __shared__ FbSmem<W, M, NB> sm;
+    __shared__ FbSmem<W, M, NB, true> sm;
     if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int my_alive = 0;
     const int n_list = p.counters[C_FB_PENDING];
     for (int k = blockIdx.x * W + w; k < n_list; k += gridDim.x * W) {
         const int o = p.hit_bin[k];
-        my_alive += fishbone_hit<W, M, NB, true, true>(p, o, p.in_cnt[o], p.in_off[o], lane, w, unit_thr, du, sm);
+        my_alive += fishbone_hit<W, M, NB, true, true, true>(p, o, p.in_cnt[o], p.in_off[o], lane, w, unit_thr, du, sm);
     }
     add_alive(p, my_alive);
 }
 
 void launch_fishbone(const Params &p, float unit_thr, float du, int grid, cudaStream_t s) {
     k_fishbone_small<8, kFbSmallMax, 256, 4><<<grid, 256, 0, s>>>(p, unit_thr, du);
-    k_fishbone_large<4, kFbMidMax, 512, false><<<grid, 128, 0, s>>>(p, unit_thr, du);
-    k_fishbone_large<2, 512, 1024, true><<<grid / 4 + 1, 64, 0, s>>>(p, unit_thr, du);
+    k_fishbone_large<4, kFbMidMax, 512, false, false><<<grid, 128, 0, s>>>(p, unit_thr, du);
+    k_fishbone_large<2, 512, 1024, true, true><<<grid / 4 + 1, 64, 0, s>>>(p, unit_thr, du);
     k_fishbone_exact<2, 512, 1024><<<grid / 8 + 1, 64, 0, s>>>(p, unit_thr, du);
 }
 

@@ -18,6 +18,20 @@ namespace ptk {
 
 __device__ __forceinline__ bool root_layer(int L) { return L == 0 || L == 1 || L == 4 || L == 7; }
 
+// One record per edge with what the search needs of its source cell, so that
+// each step back along a path is one dependent load: the source, its own
+// incoming-edge range, and its inner hit (input index) with the root flag.
+__global__ void __launch_bounds__(kThreads) k_edge_records(Params p) {
+    if (upstream_overflow(p, PT_FLAG_CELLS)) return;
+    const int64_t ne = min((int64_t)p.counters[C_EDGES], p.cap_edges);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+        const int src = p.edge_src[e];
+        const int2 r = p.edge_rng[src];
+        const int bi = p.cell_inner[src];
+        p.erec[e] = make_int4(src, r.x, r.y, p.perm[bi] * 2 + (root_layer(p.blayer[bi]) ? 1 : 0));
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_dfs(Params p) {
     if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int64_t n_list = min((int64_t)p.counters[C_LEAVES], p.cap_cells);
@@ -26,18 +40,23 @@ __global__ void __launch_bounds__(kThreads) k_dfs(Params p) {
         // the list holds the live cells with incoming edges; leaves have no outer neighbour
         const int c = p.leaf_list[k];
         if (p.has_out[c]) continue;
-        int32_t st_cell[PT_NMAX - 1];
-        int32_t st_it[PT_NMAX - 1];
+        // per depth: the cell, its first incoming edge and their count, the
+        // edges taken, its inner hit * 2 + root
+        int32_t st_cell[PT_NMAX - 1], st_first[PT_NMAX - 1], st_cnt[PT_NMAX - 1], st_it[PT_NMAX - 1];
+        int32_t st_hit[PT_NMAX - 1];
+        const int2 er = p.edge_rng[c];
+        const int leaf_outer = p.perm[p.cell_outer[c]];
         int depth = 0;
-        st_cell[0] = (int32_t)c;
+        st_cell[0] = c;
+        st_first[0] = er.x;
+        st_cnt[0] = er.y;
         st_it[0] = 0;
+        st_hit[0] = p.perm[p.cell_inner[c]] * 2;
         while (depth >= 0) {
-            const int x = st_cell[depth];
-            const int2 er = p.edge_rng[x];
-            const int ne = er.y;
-            if (ne == 0) {
+            const int cnt = st_cnt[depth], taken = st_it[depth];
+            if (cnt == 0) {
                 // start of a path: emit if it is a root and the path has >= 3 hits
-                if (depth >= 1 && root_layer(p.blayer[p.cell_inner[x]])) {
+                if (depth >= 1 && (st_hit[depth] & 1)) {
                     // one atomic for the lanes that emit together
                     const unsigned am = __activemask();
                     const int leader = __ffs(am) - 1, lane = threadIdx.x & 31;
@@ -48,11 +67,11 @@ __global__ void __launch_bounds__(kThreads) k_dfs(Params p) {
                         const int n = depth + 2;
                         int32_t *hits = p.tup_hits + (int64_t)t * PT_NMAX;
                         int32_t *cells = p.tup_cells + (int64_t)t * PT_NMAX;
-                        hits[0] = p.perm[p.cell_inner[x]];
-                        for (int k = 0; k <= depth; k++) {
-                            const int cc = st_cell[depth - k];
-                            cells[k] = cc;
-                            hits[k + 1] = p.perm[p.cell_outer[cc]];
+                        hits[0] = st_hit[depth] >> 1;
+                        for (int q = 0; q <= depth; q++) {
+                            // the outer hit of a cell is the inner hit of the next one
+                            cells[q] = st_cell[depth - q];
+                            hits[q + 1] = depth - q >= 1 ? st_hit[depth - q - 1] >> 1 : leaf_outer;
                         }
                         p.tup_n[t] = (uint8_t)n;
                         p.tup_alive[t] = 1;
@@ -63,13 +82,17 @@ __global__ void __launch_bounds__(kThreads) k_dfs(Params p) {
                 depth--;
                 continue;
             }
-            if (st_it[depth] < ne) {
-                const int64_t eidx = (int64_t)er.x + st_it[depth];
-                st_it[depth]++;
+            if (taken < cnt) {
+                const int64_t eidx = (int64_t)st_first[depth] + taken;
+                st_it[depth] = taken + 1;
                 if (eidx >= p.cap_edges || depth + 1 >= PT_NMAX - 1) continue;
+                const int4 r = p.erec[eidx];
                 depth++;
-                st_cell[depth] = p.edge_src[eidx];
+                st_cell[depth] = r.x;
+                st_first[depth] = r.y;
+                st_cnt[depth] = r.z;
                 st_it[depth] = 0;
+                st_hit[depth] = r.w;
             } else {
                 depth--;
             }
@@ -193,6 +216,7 @@ void launch_select(const Params &p, int grid, cudaStream_t s) {
 }
 
 void launch_ntuplets(const Params &p, int grid, cudaStream_t s) {
+    k_edge_records<<<grid, kThreads, 0, s>>>(p);
     k_dfs<<<grid, kThreads, 0, s>>>(p);
     k_clean_max<<<grid, kThreads, 0, s>>>(p);
     k_clean_keep<<<grid, kThreads, 0, s>>>(p);
