@@ -12,10 +12,11 @@
 // memory traffic.  Alignment within eps implies that the unit directions of
 // two siblings differ by at most du = eps pi/2 (plus float32 slack), hence
 // so does any 1-Lipschitz key of them (u^_z for a barrel o, the radial
-// component for a disk o).  The siblings are counting-sorted into key
-// buckets of width >= du, and each cell is compared only with the cells of
-// its own and the two neighbouring buckets: a superset of its aligned
-// siblings, so the result is exact at ~O(k) work per outer hit.
+// component for a disk o).  The siblings are counting-sorted into about
+// one key bucket each, and each cell is compared only with the later cells
+// of its own bucket and of the next K buckets, K covering a key difference
+// of du: a superset of its aligned siblings, so the result is exact at
+// ~O(k) work per outer hit.
 //
 // Shared memory per warp bounds the siblings it can hold, and the warps an
 // SM can keep resident bound how well the gathers of the inner hits are
@@ -38,7 +39,7 @@ namespace ptk {
 constexpr int kFbDirect = 12;        // up to this many siblings: compare all pairs
 
 // Per warp and cell: u = h_inner - h_o (exact) and 1/|u| in w; the cell's
-// position (bits 0-9), its inner layer (10-14) and key bucket (15-24).
+// position (bits 0-9), its inner layer (10-14) and key bucket (16-25).
 // C: the cell's R-z slope key and inner hit are kept for the second pass
 // (else written to and read back from global memory).
 template <int W, int M, int NB, bool C>
@@ -201,58 +202,43 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
             bmin = fminf(bmin, __shfl_xor_sync(0xffffffffu, bmin, d));
             bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, d));
         }
-        // sort the cells by direction key (ties by position): counting sort
-        // into about one bucket per cell, then the exact rank in the bucket
+        // counting sort of the cells into buckets of the direction key
+        // (about one bucket per cell); two keys within du lie at most K
+        // buckets apart (K bounds du / width plus the rounding of the
+        // bucket coordinates, below 3e-4 for up to 1024 buckets)
         const int nb = min(NB, max(32, 1 << (32 - __clz(n - 1))));
         const float span = fmaxf(bmax - bmin, fmaxf(fabsf(bmin), fabsf(bmax)) * 1e-6f);
         const float iw = span > 0.f ? (float)nb / span : 0.f;
+        const int K = (int)fminf(du * iw + 3e-4f, (float)nb) + 1;
         for (int q = lane; q < nb; q += 32) sm.pos[w][q] = 0;
         __syncwarp();
         for (int j = lane; j < n; j += 32) {
             const float key = fb_key(sm.rec[w][j], disk, rx, ry);
-            atomicAdd(&sm.pos[w][min(max((int)((key - bmin) * iw), 0), nb - 1)], 1);
+            const int bk = min(max((int)((key - bmin) * iw), 0), nb - 1);
+            sm.meta[w][j] |= bk << 16;
+            atomicAdd(&sm.pos[w][bk], 1);
         }
         __syncwarp();
         warp_exclusive_scan(sm.pos[w], nb, lane);
         __syncwarp();
-        for (int j = lane; j < n; j += 32) {
-            const float key = fb_key(sm.rec[w][j], disk, rx, ry);
-            const int bk = min(max((int)((key - bmin) * iw), 0), nb - 1);
-            sm.idx[w][atomicAdd(&sm.pos[w][bk], 1)] = (int16_t)j;
-        }
+        for (int j = lane; j < n; j += 32) sm.idx[w][atomicAdd(&sm.pos[w][sm.meta[w][j] >> 16], 1)] = (int16_t)j;
         __syncwarp();
-        // sm.pos[bk] is now the end of bucket bk
-        for (int j = lane; j < n; j += 32) {
-            const float key = fb_key(sm.rec[w][j], disk, rx, ry);
-            const int bk = min(max((int)((key - bmin) * iw), 0), nb - 1);
-            const int e = sm.pos[w][bk];
-            int rank = bk > 0 ? sm.pos[w][bk - 1] : 0;
-            for (int q = rank; q < e; q++) {
-                const int i = sm.idx[w][q];
-                const float ki = fb_key(sm.rec[w][i], disk, rx, ry);
-                rank += ki < key || (ki == key && i < j);
-            }
-            sm.meta[w][j] |= rank << 16;
-        }
-        __syncwarp();
-        for (int j = lane; j < n; j += 32) sm.idx[w][sm.meta[w][j] >> 16] = (int16_t)j;
-        __syncwarp();
-        // Each pair once: from each cell, scan forward while the keys of the
-        // later cells are within du (alignment implies it); of an aligned
-        // pair the longer cell dies (equal lengths: the larger input index
-        // of the inner hit).
+        // sm.pos[bk] is now the end of bucket bk.  Each pair once: every cell
+        // against the cells after it in its own bucket and the next K
+        // buckets (a superset of its siblings within du of its key); of an
+        // aligned pair the longer cell dies (equal lengths: the larger input
+        // index of the inner hit).
         for (int q0 = lane; q0 < n; q0 += 32) {
             const int j = sm.idx[w][q0];
             const float4 r1 = sm.rec[w][j];
-            const float k1 = fb_key(r1, disk, rx, ry);
             const float3 v1 = make_float3(r1.x * r1.w, r1.y * r1.w, r1.z * r1.w);
             const int m1 = sm.meta[w][j];
-            for (int q = q0 + 1; q < n; q++) {
+            const int qend = sm.pos[w][min((m1 >> 16) + K, nb - 1)];
+            for (int q = q0 + 1; q < qend; q++) {
                 const int d = sm.idx[w][q];
-                const float4 r2 = sm.rec[w][d];
-                if (fb_key(r2, disk, rx, ry) - k1 > du) break;
                 const int m2 = sm.meta[w][d];
                 if ((m1 ^ m2) & kRecLayerMask) continue;
+                const float4 r2 = sm.rec[w][d];
                 const float dx = v1.x - r2.x * r2.w, dy = v1.y - r2.y * r2.w, dz = v1.z - r2.z * r2.w;
                 if (dx * dx + dy * dy + dz * dz > unit_thr) continue;
                 const int v = pred_fb_d<kExact>(r1.x, r1.y, r1.z, r2.x, r2.y, r2.z, p.fishbone_eps2, p.counters);
