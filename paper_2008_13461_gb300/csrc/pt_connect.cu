@@ -21,6 +21,10 @@
 // window test itself, a float32 R-z test with an error bound and then the
 // exact predicate chain decide.
 //
+// The kernel waits on dependent L2 loads, so it is compiled for 12
+// resident blocks of 4 warps per SM (40 registers, a few spilled to L1),
+// which hides more of that latency than 8 blocks without spills did.
+//
 // A warp takes 128 consecutive cells at a time.  Only cells whose inner hit
 // has live cells ending on it have candidates at all (about a quarter), so
 // the warp first lists those and then runs their searches on full lanes.
@@ -41,7 +45,7 @@
 namespace ptk {
 
 constexpr int kCaWarps = 4;
-constexpr int kCaQueue = 8;         // accepted candidates remembered per cell
+constexpr int kCaQueue = 4;         // accepted candidates remembered per cell
 constexpr int kCaChunk = 4;         // rounds of 32 cells per edge reservation
 
 // The predicate chain: 1 connects, 0 does not; with kExact = false, 2 when
@@ -148,7 +152,7 @@ __device__ __forceinline__ int scan_cell(const Params &p, int x, Emit &&emit) {
     return n;
 }
 
-__global__ void __launch_bounds__(32 * kCaWarps, 8) k_connect(Params p) {
+__global__ void __launch_bounds__(32 * kCaWarps, 12) k_connect(Params p) {
     constexpr int kPer = 32 * kCaChunk;
     __shared__ int32_t s_q[kCaWarps][kCaQueue][kPer];   // accepted inner cells per chunk position
     __shared__ int32_t s_m[kCaWarps][kPer];             // edges per chunk position (-1: no live cell)

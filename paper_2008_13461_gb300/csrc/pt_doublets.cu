@@ -175,7 +175,7 @@ __device__ __forceinline__ bool doublets_hit(const Params &p, int o, int lane, u
 // registers); an outer hit with an undecided candidate (about one in 10^3)
 // is listed for the exact pass.
 template <int G>
-__global__ void __launch_bounds__(kThreads) k_doublets(Params p) {
+__global__ void __launch_bounds__(kThreads, 5) k_doublets(Params p) {
     constexpr int kGroups = kThreads / G;
     constexpr int kBuf = 32 * G;   // 40 KB of shared memory per block for every G
     __shared__ int32_t s_inner[kGroups][kBuf];
