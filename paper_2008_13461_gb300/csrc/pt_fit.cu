@@ -10,7 +10,8 @@
 //  3. s-z line fit: unknowns v_i, measurement z_i (sigma_z; disks sigma_r
 //     |tan lambda0|), kinks of the slope;
 //  4. transverse circle fit: unknowns u_i and dk, measurement m_i
-//     (sigma_rphi), kinks of the offset slope minus dk times the mean step;
+//     (sigma_rphi), kinks of the offset slope minus dk times the mean step
+//     (three hits: solved in closed form, the offsets are fitted exactly);
 //  5. perigee parameters w.r.t. the beam line and their covariance (line block
 //     by its linear Jacobian, circle block by the analytic Jacobian).
 //
@@ -182,13 +183,14 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
     const float pmom = pt0 * sqrtf(sec2);
     const float atl = fmaxf(fabsf(tanl0), 1e-3f);
     // 2) scattering variances of the kinks at hits 1 .. n-2
-    R vb[N], vg[N];
+    R vb[N], vg[N], kv[N];
 #pragma unroll
     for (int i = 1; i < N - 1; i++) {
         const float xx0 = disk[i] ? p.fit.x0_disk * sqrtf(sec2) / atl : p.fit.x0_barrel * sqrtf(sec2);
         const float th = 0.0136f / pmom * sqrtf(xx0) * (1.0f + 0.038f * logf(xx0));
         const R th2 = (R)th * th;
-        vb[i] = recip_r(fmax(th2 * sec2, R(1e-20)));          // weights 1/variance
+        kv[i] = fmax(th2 * sec2, R(1e-20));                   // transverse kink variance
+        vb[i] = recip_r(kv[i]);                               // weights 1/variance
         vg[i] = recip_r(fmax(th2 * sec2 * sec2, R(1e-20)));
     }
     // 3) line fit in s-z; unknown v_i at position ln(i): v2 .. v_{n-1}, v0, v1
@@ -227,46 +229,69 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
     }
     const R v[2] = {bv[ln(0)], bv[ln(1)]};
     // 4) circle fit: unknowns u_0 .. u_{n-1}, dk; u_i at position ln(i), dk last
-    constexpr int M = N + 1;
-    R B[M * (M + 1) / 2], bu[M];
+    R xu[3], Cc[3][3];
+    if constexpr (N == 3) {
+        // Three offsets and one kink: the minimum has u_i = m_i and the kink
+        // at hit 1 zero, so dk = a . m with a_i = -h_i / h3; the inverse of
+        // the normal matrix gives cov(u) = sigma^2 I, cov(u, dk) = sigma^2 a
+        // and var(dk) = sigma^2 |a|^2 + var(kink) / h3^2; the circle chi2 is 0.
+        const R h0 = ids[1], h2 = ids[2], h1 = -(h0 + h2);
+        const R ih3 = recip_r(R(-0.5) * ((R)ds[1] + ds[2]));
+        const R a0 = -h0 * ih3, a1 = -h1 * ih3, a2 = -h2 * ih3;
+        const R s2 = (R)p.fit.sigma_rphi * p.fit.sigma_rphi;
+        xu[0] = m[0];
+        xu[1] = m[1];
+        xu[2] = a0 * m[0] + a1 * m[1] + a2 * m[2];
+        Cc[0][0] = s2;
+        Cc[0][1] = Cc[1][0] = R(0);
+        Cc[1][1] = s2;
+        Cc[0][2] = Cc[2][0] = s2 * a0;
+        Cc[1][2] = Cc[2][1] = s2 * a1;
+        Cc[2][2] = s2 * (a0 * a0 + a1 * a1 + a2 * a2) + kv[1] * ih3 * ih3;
+    } else {
+        constexpr int M = N + 1;
+        R B[M * (M + 1) / 2], bu[M];
 #pragma unroll
-    for (int i = 0; i < M * (M + 1) / 2; i++) B[i] = R(0);
-    const R wu = recip_r((R)p.fit.sigma_rphi * p.fit.sigma_rphi);
+        for (int i = 0; i < M * (M + 1) / 2; i++) B[i] = R(0);
+        const R wu = recip_r((R)p.fit.sigma_rphi * p.fit.sigma_rphi);
 #pragma unroll
-    for (int i = 0; i < N; i++) {
-        B[pidx<M>(ln(i), ln(i))] = wu;
-        bu[ln(i)] = wu * m[i];
+        for (int i = 0; i < N; i++) {
+            B[pidx<M>(ln(i), ln(i))] = wu;
+            bu[ln(i)] = wu * m[i];
+        }
+        bu[N] = R(0);
+#pragma unroll
+        for (int i = 1; i < N - 1; i++) {
+            const R h0 = ids[i], h2 = ids[i + 1], h1 = -(h0 + h2);
+            const R h3 = R(-0.5) * ((R)ds[i] + ds[i + 1]), w = vb[i];
+            const R wh0 = h0 * w, wh1 = h1 * w, wh2 = h2 * w;
+            B[sidx<M>(ln(i - 1), ln(i - 1))] += h0 * wh0;
+            B[sidx<M>(ln(i), ln(i - 1))] += h1 * wh0;
+            B[sidx<M>(ln(i), ln(i))] += h1 * wh1;
+            B[sidx<M>(ln(i + 1), ln(i - 1))] += h2 * wh0;
+            B[sidx<M>(ln(i + 1), ln(i))] += h2 * wh1;
+            B[sidx<M>(ln(i + 1), ln(i + 1))] += h2 * wh2;
+            B[pidx<M>(N, ln(i - 1))] += h3 * wh0;
+            B[pidx<M>(N, ln(i))] += h3 * wh1;
+            B[pidx<M>(N, ln(i + 1))] += h3 * wh2;
+            B[pidx<M>(N, N)] += h3 * h3 * w;
+        }
+        chol<M, R>(B);
+        solve_tail<M, 3, R>(B, bu, Cc);      // bu[ln(i)] = u_i, bu[N] = dk
+        const R dkk = bu[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) chi2 += wu * (bu[ln(i)] - m[i]) * (bu[ln(i)] - m[i]);
+#pragma unroll
+        for (int i = 1; i < N - 1; i++) {
+            const R be = (bu[ln(i + 1)] - bu[ln(i)]) * ids[i + 1] - (bu[ln(i)] - bu[ln(i - 1)]) * ids[i] -
+                         dkk * R(0.5) * ((R)ds[i] + ds[i + 1]);
+            chi2 += be * be * vb[i];
+        }
+        xu[0] = bu[ln(0)];
+        xu[1] = bu[ln(1)];
+        xu[2] = dkk;
     }
-    bu[N] = R(0);
-#pragma unroll
-    for (int i = 1; i < N - 1; i++) {
-        const R h0 = ids[i], h2 = ids[i + 1], h1 = -(h0 + h2);
-        const R h3 = R(-0.5) * ((R)ds[i] + ds[i + 1]), w = vb[i];
-        const R wh0 = h0 * w, wh1 = h1 * w, wh2 = h2 * w;
-        B[sidx<M>(ln(i - 1), ln(i - 1))] += h0 * wh0;
-        B[sidx<M>(ln(i), ln(i - 1))] += h1 * wh0;
-        B[sidx<M>(ln(i), ln(i))] += h1 * wh1;
-        B[sidx<M>(ln(i + 1), ln(i - 1))] += h2 * wh0;
-        B[sidx<M>(ln(i + 1), ln(i))] += h2 * wh1;
-        B[sidx<M>(ln(i + 1), ln(i + 1))] += h2 * wh2;
-        B[pidx<M>(N, ln(i - 1))] += h3 * wh0;
-        B[pidx<M>(N, ln(i))] += h3 * wh1;
-        B[pidx<M>(N, ln(i + 1))] += h3 * wh2;
-        B[pidx<M>(N, N)] += h3 * h3 * w;
-    }
-    chol<M, R>(B);
-    R Cc[3][3];
-    solve_tail<M, 3, R>(B, bu, Cc);      // bu[ln(i)] = u_i, bu[N] = dk
-    const R dk = bu[N];
-#pragma unroll
-    for (int i = 0; i < N; i++) chi2 += wu * (bu[ln(i)] - m[i]) * (bu[ln(i)] - m[i]);
-#pragma unroll
-    for (int i = 1; i < N - 1; i++) {
-        const R be = (bu[ln(i + 1)] - bu[ln(i)]) * ids[i + 1] - (bu[ln(i)] - bu[ln(i - 1)]) * ids[i] -
-                     dk * R(0.5) * ((R)ds[i] + ds[i + 1]);
-        chi2 += be * be * vb[i];
-    }
-    const R xu[3] = {bu[ln(0)], bu[ln(1)], dk};
+    const R dk = xu[2];
     // 5) perigee of the fitted circle through P with direction psi
     const float kf = (float)((R)k0 + dk);
     const float u0 = (float)xu[0];
@@ -309,10 +334,10 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
             J[2][j] = dd0;
         }
     }
-    // F = J C J^T as (J C) J^T
+    // F = J C J^T as (J C) J^T; the first row of J is (0, 0, -1)
     R JC[3][3];
 #pragma unroll
-    for (int a = 0; a < 3; a++)
+    for (int a = 1; a < 3; a++)
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             R acc = R(0);
@@ -321,16 +346,19 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
             JC[a][d] = acc;
         }
     float Fc[3][3];
+    Fc[0][0] = (float)Cc[2][2];
 #pragma unroll
-    for (int a = 0; a < 3; a++)
+    for (int a = 1; a < 3; a++) {
+        Fc[a][0] = Fc[0][a] = (float)(-JC[a][2]);
 #pragma unroll
-        for (int b = 0; b <= a; b++) {
+        for (int b = 1; b <= a; b++) {
             R acc = R(0);
 #pragma unroll
             for (int d = 0; d < 3; d++) acc += JC[a][d] * J[b][d];
             Fc[a][b] = (float)acc;
             Fc[b][a] = Fc[a][b];
         }
+    }
     // line block: tanl = (v1 - v0)/ds1, z0 = v0 + tanl arc
     const R t0 = -ids[1], t1 = ids[1], z0a = R(1) - arc * ids[1], z1a = arc * ids[1];
     const R c00 = Cv[0][0], c01 = Cv[0][1], c11 = Cv[1][1];
