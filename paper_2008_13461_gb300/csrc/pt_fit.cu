@@ -8,7 +8,8 @@
 //  2. multiple-scattering variances of the kinks at the inner hits (Highland,
 //     momentum from k0 and the pre-fit dip);
 //  3. s-z line fit: unknowns v_i, measurement z_i (sigma_z; disks sigma_r
-//     |tan lambda0|), kinks of the slope;
+//     |tan lambda0|), kinks of the slope (three hits: one kink, solved in
+//     closed form);
 //  4. transverse circle fit: unknowns u_i and dk, measurement m_i
 //     (sigma_rphi), kinks of the offset slope minus dk times the mean step
 //     (three hits: solved in closed form, the offsets are fitted exactly);
@@ -183,51 +184,81 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
     const float pmom = pt0 * sqrtf(sec2);
     const float atl = fmaxf(fabsf(tanl0), 1e-3f);
     // 2) scattering variances of the kinks at hits 1 .. n-2
-    R vb[N], vg[N], kv[N];
+    R vb[N], vg[N], kv[N], kz[N];
 #pragma unroll
     for (int i = 1; i < N - 1; i++) {
         const float xx0 = disk[i] ? p.fit.x0_disk * sqrtf(sec2) / atl : p.fit.x0_barrel * sqrtf(sec2);
         const float th = 0.0136f / pmom * sqrtf(xx0) * (1.0f + 0.038f * logf(xx0));
         const R th2 = (R)th * th;
-        kv[i] = fmax(th2 * sec2, R(1e-20));                   // transverse kink variance
-        vb[i] = recip_r(kv[i]);                               // weights 1/variance
-        vg[i] = recip_r(fmax(th2 * sec2 * sec2, R(1e-20)));
+        kv[i] = fmax(th2 * sec2, R(1e-20));                   // kink variances: transverse,
+        kz[i] = fmax(th2 * sec2 * sec2, R(1e-20));            //   s-z slope
+        if (N > 3) {
+            vb[i] = recip_r(kv[i]);                           // weights 1/variance
+            vg[i] = recip_r(kz[i]);
+        }
     }
     // 3) line fit in s-z; unknown v_i at position ln(i): v2 .. v_{n-1}, v0, v1
     auto ln = [](int i) { return i >= 2 ? i - 2 : N - 2 + i; };
-    R A[N * (N + 1) / 2], bv[N], wz[N];
+    R v[2], Cv[2][2], chi2;
+    if constexpr (N == 3) {
+        // One kink: the normal matrix is diag(1/var_i) + g g^T / var_k, and
+        // its inverse follows from Sherman-Morrison: with q = g . z and
+        // D = var_k + sum g_i^2 var_i, v_i = z_i - var_i g_i q / D, chi2 =
+        // q^2 / D, cov(v_i, v_j) = var_i delta_ij - var_i g_i var_j g_j / D
+        // (the diagonal as var_i (D - g_i^2 var_i) / D, a sum of positive
+        // terms).
+        R var[3];
 #pragma unroll
-    for (int i = 0; i < N * (N + 1) / 2; i++) A[i] = R(0);
+        for (int i = 0; i < 3; i++) {
+            const R sz = disk[i] ? (R)p.fit.sigma_r * atl : (R)p.fit.sigma_z;
+            var[i] = sz * sz;
+        }
+        const R g0 = ids[1], g2 = ids[2], g1 = -(g0 + g2);
+        const R t0 = g0 * g0 * var[0], t1 = g1 * g1 * var[1], t2 = g2 * g2 * var[2];
+        const R iD = recip_r(kz[1] + t0 + t1 + t2);
+        const R q = g0 * hz[0] + g1 * hz[1] + g2 * hz[2];
+        const R f = q * iD;
+        v[0] = hz[0] - var[0] * g0 * f;
+        v[1] = hz[1] - var[1] * g1 * f;
+        chi2 = q * f;
+        Cv[0][0] = var[0] * (kz[1] + t1 + t2) * iD;
+        Cv[1][1] = var[1] * (kz[1] + t0 + t2) * iD;
+        Cv[0][1] = Cv[1][0] = -(var[0] * g0) * (var[1] * g1) * iD;
+    } else {
+        R A[N * (N + 1) / 2], bv[N], wz[N];
 #pragma unroll
-    for (int i = 0; i < N; i++) {
-        const R sz = disk[i] ? (R)p.fit.sigma_r * atl : (R)p.fit.sigma_z;
-        wz[i] = recip_r(sz * sz);
-        A[pidx<N>(ln(i), ln(i))] = wz[i];
-        bv[ln(i)] = wz[i] * hz[i];
+        for (int i = 0; i < N * (N + 1) / 2; i++) A[i] = R(0);
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+            const R sz = disk[i] ? (R)p.fit.sigma_r * atl : (R)p.fit.sigma_z;
+            wz[i] = recip_r(sz * sz);
+            A[pidx<N>(ln(i), ln(i))] = wz[i];
+            bv[ln(i)] = wz[i] * hz[i];
+        }
+#pragma unroll
+        for (int i = 1; i < N - 1; i++) {
+            const R g0 = ids[i], g2 = ids[i + 1], g1 = -(g0 + g2), w = vg[i];
+            const R wg0 = g0 * w, wg1 = g1 * w, wg2 = g2 * w;
+            A[sidx<N>(ln(i - 1), ln(i - 1))] += g0 * wg0;
+            A[sidx<N>(ln(i), ln(i - 1))] += g1 * wg0;
+            A[sidx<N>(ln(i), ln(i))] += g1 * wg1;
+            A[sidx<N>(ln(i + 1), ln(i - 1))] += g2 * wg0;
+            A[sidx<N>(ln(i + 1), ln(i))] += g2 * wg1;
+            A[sidx<N>(ln(i + 1), ln(i + 1))] += g2 * wg2;
+        }
+        chol<N, R>(A);
+        solve_tail<N, 2, R>(A, bv, Cv);      // bv[ln(i)] = v_i
+        chi2 = R(0);
+#pragma unroll
+        for (int i = 0; i < N; i++) chi2 += wz[i] * (bv[ln(i)] - hz[i]) * (bv[ln(i)] - hz[i]);
+#pragma unroll
+        for (int i = 1; i < N - 1; i++) {
+            const R gam = (bv[ln(i + 1)] - bv[ln(i)]) * ids[i + 1] - (bv[ln(i)] - bv[ln(i - 1)]) * ids[i];
+            chi2 += gam * gam * vg[i];
+        }
+        v[0] = bv[ln(0)];
+        v[1] = bv[ln(1)];
     }
-#pragma unroll
-    for (int i = 1; i < N - 1; i++) {
-        const R g0 = ids[i], g2 = ids[i + 1], g1 = -(g0 + g2), w = vg[i];
-        const R wg0 = g0 * w, wg1 = g1 * w, wg2 = g2 * w;
-        A[sidx<N>(ln(i - 1), ln(i - 1))] += g0 * wg0;
-        A[sidx<N>(ln(i), ln(i - 1))] += g1 * wg0;
-        A[sidx<N>(ln(i), ln(i))] += g1 * wg1;
-        A[sidx<N>(ln(i + 1), ln(i - 1))] += g2 * wg0;
-        A[sidx<N>(ln(i + 1), ln(i))] += g2 * wg1;
-        A[sidx<N>(ln(i + 1), ln(i + 1))] += g2 * wg2;
-    }
-    chol<N, R>(A);
-    R Cv[2][2];
-    solve_tail<N, 2, R>(A, bv, Cv);      // bv[ln(i)] = v_i
-    R chi2 = R(0);
-#pragma unroll
-    for (int i = 0; i < N; i++) chi2 += wz[i] * (bv[ln(i)] - hz[i]) * (bv[ln(i)] - hz[i]);
-#pragma unroll
-    for (int i = 1; i < N - 1; i++) {
-        const R gam = (bv[ln(i + 1)] - bv[ln(i)]) * ids[i + 1] - (bv[ln(i)] - bv[ln(i - 1)]) * ids[i];
-        chi2 += gam * gam * vg[i];
-    }
-    const R v[2] = {bv[ln(0)], bv[ln(1)]};
     // 4) circle fit: unknowns u_0 .. u_{n-1}, dk; u_i at position ln(i), dk last
     R xu[3], Cc[3][3];
     if constexpr (N == 3) {
