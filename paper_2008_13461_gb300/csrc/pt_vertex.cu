@@ -206,20 +206,24 @@ __global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_event(VtxArgs a) {
 
     const float dzc = a.cuts.dz_cut, c2m = a.cuts.chi2_max;
     int32_t *rho = a.rho + base, *root = a.root + base;
+    // the z0 errors by sorted position, in the key array until the keys are built
+    float *sez = reinterpret_cast<float *>(key);
+    for (int p = tid; p < cnt; p += blockDim.x) sez[p] = a.in.ez0[sid[p]];
+    __syncthreads();
     // densities: the compatible tracks lie in the window |z0 - z0_p| < dz_cut
     // (rounded differences are monotonic along the sorted order)
     for (int p = tid; p < cnt; p += blockDim.x) {
-        const float zp = sz[p], ep = a.in.ez0[sid[p]], ep2 = __fmul_rn(ep, ep);
+        const float zp = sz[p], ep = sez[p], ep2 = __fmul_rn(ep, ep);
         int r = 1;
         for (int q = p - 1; q >= 0; q--) {
             const float dz = __fsub_rn(zp, sz[q]);
             if (!(fabsf(dz) < dzc)) break;
-            r += chi2_ok(dz, ep2, a.in.ez0[sid[q]], c2m);
+            r += chi2_ok(dz, ep2, sez[q], c2m);
         }
         for (int q = p + 1; q < cnt; q++) {
             const float dz = __fsub_rn(zp, sz[q]);
             if (!(fabsf(dz) < dzc)) break;
-            r += chi2_ok(dz, ep2, a.in.ez0[sid[q]], c2m);
+            r += chi2_ok(dz, ep2, sez[q], c2m);
         }
         rho[p] = r;
     }
@@ -228,7 +232,7 @@ __global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_event(VtxArgs a) {
     for (int p = tid; p < cnt; p += blockDim.x) {
         const float zp = sz[p];
         const int ip = sid[p], rp = rho[p];
-        const float ep = a.in.ez0[ip], ep2 = __fmul_rn(ep, ep);
+        const float ep = sez[p], ep2 = __fmul_rn(ep, ep);
         int best = -1, bid = 0;
         float bd = 0.f;
         for (int dir = -1; dir <= 1; dir += 2)
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_event(VtxArgs a) {
                 if (!(ad < dzc)) break;
                 const int iq = sid[q], rq = rho[q];
                 if (!(rq > rp || (rq == rp && iq < ip))) continue;
-                if (!chi2_ok(dz, ep2, a.in.ez0[iq], c2m)) continue;
+                if (!chi2_ok(dz, ep2, sez[q], c2m)) continue;
                 if (best < 0 || ad < bd || (ad == bd && iq < bid)) {
                     best = q;
                     bd = ad;
