@@ -64,19 +64,33 @@ __device__ __forceinline__ bool eligible(const VtxArgs &a, int i) {
 
 __device__ __forceinline__ void set_status(const VtxArgs &a, int bit) { atomicOr(a.out.status, bit); }
 
+// Tracks of one event are mostly consecutive, so the per-event atomics are
+// aggregated over the lanes of a warp that share an event.
 __global__ void __launch_bounds__(kThreads) k_vtx_count(VtxArgs a) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_tracks; i += gridDim.x * blockDim.x) {
-        a.out.track_vertex[i] = -1;
-        if (eligible(a, i)) atomicAdd(a.ev_off + a.in.ev[i], 1);
+    const int lane = threadIdx.x & 31;
+    for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < a.n_tracks; i0 += gridDim.x * blockDim.x) {
+        const int i = i0 + lane;
+        const bool ok = i < a.n_tracks && eligible(a, i);
+        if (i < a.n_tracks) a.out.track_vertex[i] = -1;
+        const int e = ok ? a.in.ev[i] : -1;
+        const unsigned grp = __match_any_sync(kFull, e);
+        if (ok && lane == __ffs(grp) - 1) atomicAdd(a.ev_off + e, __popc(grp));
     }
 }
 
 __global__ void __launch_bounds__(kThreads) k_vtx_fill(VtxArgs a) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_tracks; i += gridDim.x * blockDim.x)
-        if (eligible(a, i)) {
-            const int e = a.in.ev[i];
-            a.order[a.ev_off[e] + atomicAdd(a.ev_cur + e, 1)] = i;
-        }
+    const int lane = threadIdx.x & 31;
+    for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < a.n_tracks; i0 += gridDim.x * blockDim.x) {
+        const int i = i0 + lane;
+        const bool ok = i < a.n_tracks && eligible(a, i);
+        const int e = ok ? a.in.ev[i] : -1;
+        const unsigned grp = __match_any_sync(kFull, e);
+        const int leader = __ffs(grp) - 1;
+        int slot = 0;
+        if (ok && lane == leader) slot = atomicAdd(a.ev_cur + e, __popc(grp));
+        slot = __shfl_sync(kFull, slot, leader) + __popc(grp & ((1u << lane) - 1u));
+        if (ok) a.order[a.ev_off[e] + slot] = i;
+    }
 }
 
 // the chi2 half of the compatibility of a track (squared error ep2) with a
