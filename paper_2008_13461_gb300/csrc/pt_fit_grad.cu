@@ -168,8 +168,26 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
 #pragma unroll
             for (int c = 0; c <= a; c++) A[pk<N>(i - 1 + a, i - 1 + c)] += vg[i] * g[a] * g[c];
     }
-    chol_d<N>(A);
-    solve_d<N>(A, v);
+    // Three hits: one kink per plane.  A = diag(wz) + vg_1 g g^T is
+    // inverted by Sherman-Morrison; B = wu diag(1, 1, 1, 0) + vb_1 h h^T has
+    // the explicit inverse [[I, a], [a^T, |a|^2 + var_1 wu / h3^2]] / wu with
+    // a = -(h0, h1, h2) / h3.  Otherwise Cholesky.
+    auto solve_line = [&](double *yv) {
+        if constexpr (N == 3) {
+            const double g0 = ids[1], g2 = ids[2], g1 = -(g0 + g2);
+            const double r0 = 1.0 / wz[0], r1 = 1.0 / wz[1], r2 = 1.0 / wz[2];
+            const double kz = fmax(th[1] * th[1] * sec2 * sec2, 1e-20);
+            const double w0 = r0 * yv[0], w1 = r1 * yv[1], w2 = r2 * yv[2];
+            const double f = (g0 * w0 + g1 * w1 + g2 * w2) / (kz + g0 * g0 * r0 + g1 * g1 * r1 + g2 * g2 * r2);
+            yv[0] = w0 - r0 * g0 * f;
+            yv[1] = w1 - r1 * g1 * f;
+            yv[2] = w2 - r2 * g2 * f;
+        } else {
+            solve_d<N>(A, yv);
+        }
+    };
+    if constexpr (N != 3) chol_d<N>(A);
+    solve_line(v);
     // 4) circle fit: B x = b, x = (u_0 .. u_{n-1}, dk)
     const double wu = 1.0 / ((double)p.fit.sigma_rphi * p.fit.sigma_rphi);
     double B[M * (M + 1) / 2], xs[M];
@@ -190,8 +208,22 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
 #pragma unroll
             for (int c = 0; c <= a; c++) B[pk<M>(at[a], at[c])] += vb[i] * h[a] * h[c];
     }
-    chol_d<M>(B);
-    solve_d<M>(B, xs);
+    auto solve_circle = [&](double *yv) {
+        if constexpr (N == 3) {
+            const double h0 = ids[1], h2 = ids[2], h1 = -(h0 + h2), ih3 = 1.0 / (-0.5 * (ds[1] + ds[2]));
+            const double a0 = -h0 * ih3, a1 = -h1 * ih3, a2 = -h2 * ih3;
+            const double s2 = 1.0 / wu, kv = fmax(th[1] * th[1] * sec2, 1e-20);
+            const double ay = a0 * yv[0] + a1 * yv[1] + a2 * yv[2], y3 = yv[3];
+            yv[0] = s2 * (yv[0] + a0 * y3);
+            yv[1] = s2 * (yv[1] + a1 * y3);
+            yv[2] = s2 * (yv[2] + a2 * y3);
+            yv[3] = s2 * ay + (s2 * (a0 * a0 + a1 * a1 + a2 * a2) + kv * ih3 * ih3) * y3;
+        } else {
+            solve_d<M>(B, yv);
+        }
+    };
+    if constexpr (N != 3) chol_d<M>(B);
+    solve_circle(xs);
     const double dk = xs[N];
     // 5) perigee
     const double kf = k0 + dk;
@@ -286,7 +318,7 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
         double bb[M];
 #pragma unroll
         for (int i = 0; i < M; i++) bb[i] = xsb[i];
-        solve_d<M>(B, bb);                     // bbar = B^-1 xbar
+        solve_circle(bb);                      // bbar = B^-1 xbar
 #pragma unroll
         for (int i = 0; i < N; i++) {
             // b_i = wu m_i; diagonal wu constant
@@ -320,7 +352,7 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
         for (int i = 0; i < N; i++) bb[i] = 0.0;
         bb[0] = v0b;
         bb[1] = v1b;
-        solve_d<N>(A, bb);
+        solve_line(bb);
 #pragma unroll
         for (int i = 0; i < N; i++) {
             // b_i = wz_i z_i, A_ii += wz_i
