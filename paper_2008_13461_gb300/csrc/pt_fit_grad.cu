@@ -29,6 +29,21 @@ namespace {
 template <int M>
 __device__ __forceinline__ int pk(int r, int c) { return r >= c ? r * (r + 1) / 2 + c : c * (c + 1) / 2 + r; }
 
+// Reciprocal, reciprocal square root and square root from a float32 seed and
+// one Newton step (relative error about 1e-14): a few FP64 multiply-adds
+// instead of the full IEEE sequences on the slow FP64 pipe.  Used where the
+// argument is nonzero and well inside the float32 range (lengths, weights,
+// variances); sqrt_d(0) = 0.
+__device__ __forceinline__ double rcp_d(double x) {
+    const double r = (double)__frcp_rn((float)x);
+    return r * (2.0 - x * r);
+}
+__device__ __forceinline__ double rsqrt_d(double x) {
+    const double y = (double)rsqrtf((float)x);
+    return y * (1.5 - 0.5 * x * y * y);
+}
+__device__ __forceinline__ double sqrt_d(double x) { return x > 0.0 ? x * rsqrt_d(x) : 0.0; }
+
 // Cholesky in place (packed lower triangle), inverse diagonal stored
 template <int M>
 __device__ __forceinline__ void chol_d(double *A) {
@@ -37,7 +52,7 @@ __device__ __forceinline__ void chol_d(double *A) {
         double s = A[pk<M>(j, j)];
 #pragma unroll
         for (int k = 0; k < j; k++) s -= A[pk<M>(j, k)] * A[pk<M>(j, k)];
-        const double id = 1.0 / sqrt(s > 1e-30 ? s : 1e-30);
+        const double id = rsqrt_d(s > 1e-30 ? s : 1e-30);
         A[pk<M>(j, j)] = id;
 #pragma unroll
         for (int i = j + 1; i < M; i++) {
@@ -69,11 +84,13 @@ __device__ __forceinline__ void solve_d(const double *L, double *b) {
 }
 
 // asin(q)/q and its derivative (q clamped to [-1, 1] by the caller)
-__device__ __forceinline__ double asinc_d(double q) { return fabs(q) < 1e-4 ? 1.0 + q * q / 6.0 : asin(q) / q; }
+__device__ __forceinline__ double asinc_d(double q) {
+    return fabs(q) < 1e-4 ? 1.0 + q * q * (1.0 / 6.0) : asin(q) * rcp_d(q);
+}
 __device__ __forceinline__ double dasinc_d(double q) {
-    if (fabs(q) < 1e-4) return q / 3.0;
+    if (fabs(q) < 1e-4) return q * (1.0 / 3.0);
     if (fabs(q) >= 1.0) return 0.0;
-    return (q / sqrt(1.0 - q * q) - asin(q)) / (q * q);
+    return (q * rsqrt_d(1.0 - q * q) - asin(q)) * rcp_d(q * q);
 }
 
 template <int N>
@@ -98,10 +115,11 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
     const double acx = x[ic] - x[0], acy = y[ic] - y[0];
     const double bcx = x[ic] - x[ib], bcy = y[ic] - y[ib];
     const double orient = abx * acy - aby * acx;
-    const double dab = sqrt(abx * abx + aby * aby), dbc = sqrt(bcx * bcx + bcy * bcy);
-    const double dca = sqrt(acx * acx + acy * acy);
+    const double dab = sqrt_d(abx * abx + aby * aby), dbc = sqrt_d(bcx * bcx + bcy * bcy);
+    const double dca = sqrt_d(acx * acx + acy * acy);
     const double den = dab * dbc * dca;
-    const double k0 = den > 0.0 ? 2.0 * orient / den : 0.0;
+    const double iden = den > 0.0 ? rcp_d(den) : 0.0;
+    const double k0 = 2.0 * orient * iden;
     const double ta = 0.5 * k0 * dab;
     const bool ta_in = fabs(ta) < 1.0;
     const double tac = fmin(fmax(ta, -1.0), 1.0);
@@ -109,19 +127,20 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
     double sn, cs;
     sincos(psi0, &sn, &cs);
     // arc lengths and offsets from the pre-fit circle
-    double s[N], m[N], dxs[N], dys[N], dist[N], qs[N], Xs[N], Ys[N], Us[N], Sq[N];
+    double s[N], m[N], dxs[N], dys[N], dist[N], qs[N], Xs[N], Ys[N], Us[N], Sq[N], i1Sq[N];
 #pragma unroll
     for (int i = 0; i < N; i++) {
         dxs[i] = x[i] - x[0];
         dys[i] = y[i] - y[0];
-        dist[i] = sqrt(dxs[i] * dxs[i] + dys[i] * dys[i]);
+        dist[i] = sqrt_d(dxs[i] * dxs[i] + dys[i] * dys[i]);
         qs[i] = fmin(fmax(0.5 * k0 * dist[i], -1.0), 1.0);
         s[i] = dist[i] * asinc_d(qs[i]);
         Xs[i] = dxs[i] * cs + dys[i] * sn;
         Ys[i] = dys[i] * cs - dxs[i] * sn;
         Us[i] = k0 * (Xs[i] * Xs[i] + Ys[i] * Ys[i]) - 2.0 * Ys[i];
-        Sq[i] = sqrt(fmax(1.0 + k0 * Us[i], 0.0));
-        m[i] = -Us[i] / (1.0 + Sq[i]);
+        Sq[i] = sqrt_d(fmax(1.0 + k0 * Us[i], 0.0));
+        i1Sq[i] = rcp_d(1.0 + Sq[i]);
+        m[i] = -Us[i] * i1Sq[i];
     }
     double ds[N], ids[N];
     ds[0] = 0.0;
@@ -129,34 +148,36 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
 #pragma unroll
     for (int i = 1; i < N; i++) {
         ds[i] = fmax(s[i] - s[i - 1], 1e-4);
-        ids[i] = 1.0 / ds[i];
+        ids[i] = rcp_d(ds[i]);
     }
     const double Sl = fmax(s[N - 1], 1e-4);
-    const double tanl0 = (z[N - 1] - z[0]) / Sl;
-    const double sec2 = 1.0 + tanl0 * tanl0, rsec = sqrt(sec2);
-    const double ak = fmax(fabs(k0), 1e-7);
-    const double pt0 = 0.00299792458 * bz / ak;
-    const double pmom = pt0 * rsec;
-    const double atl = fmax(fabs(tanl0), 1e-3);
+    const double iSl = rcp_d(Sl);
+    const double tanl0 = (z[N - 1] - z[0]) * iSl;
+    const double sec2 = 1.0 + tanl0 * tanl0, rsec = sqrt_d(sec2);
+    const double ak = fmax(fabs(k0), 1e-7), iak = rcp_d(ak);
+    const double pt0 = 0.00299792458 * bz * iak;
+    const double pmom = pt0 * rsec, ipmom = rcp_d(pmom);
+    const double atl = fmax(fabs(tanl0), 1e-3), iatl = rcp_d(atl);
     // 2) scattering weights of the kinks at hits 1 .. n-2
     double vb[N], vg[N], th[N], xx0[N];
 #pragma unroll
     for (int i = 0; i < N; i++) vb[i] = vg[i] = th[i] = xx0[i] = 0.0;
 #pragma unroll
     for (int i = 1; i < N - 1; i++) {
-        xx0[i] = disk[i] ? p.fit.x0_disk * rsec / atl : p.fit.x0_barrel * rsec;
-        th[i] = 0.0136 / pmom * sqrt(xx0[i]) * (1.0 + 0.038 * log(xx0[i]));
-        vb[i] = 1.0 / fmax(th[i] * th[i] * sec2, 1e-20);
-        vg[i] = 1.0 / fmax(th[i] * th[i] * sec2 * sec2, 1e-20);
+        xx0[i] = disk[i] ? p.fit.x0_disk * rsec * iatl : p.fit.x0_barrel * rsec;
+        th[i] = 0.0136 * ipmom * sqrt_d(xx0[i]) * (1.0 + 0.038 * log(xx0[i]));
+        vb[i] = rcp_d(fmax(th[i] * th[i] * sec2, 1e-20));
+        vg[i] = rcp_d(fmax(th[i] * th[i] * sec2 * sec2, 1e-20));
     }
     // 3) line fit: A v = b
-    double wz[N], A[N * (N + 1) / 2], v[N];
+    double wz[N], vz[N], A[N * (N + 1) / 2], v[N];
 #pragma unroll
     for (int i = 0; i < N * (N + 1) / 2; i++) A[i] = 0.0;
 #pragma unroll
     for (int i = 0; i < N; i++) {
         const double sz = disk[i] ? (double)p.fit.sigma_r * atl : (double)p.fit.sigma_z;
-        wz[i] = 1.0 / (sz * sz);
+        vz[i] = sz * sz;
+        wz[i] = rcp_d(vz[i]);
         A[pk<N>(i, i)] = wz[i];
         v[i] = wz[i] * z[i];
     }
@@ -175,10 +196,10 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
     auto solve_line = [&](double *yv) {
         if constexpr (N == 3) {
             const double g0 = ids[1], g2 = ids[2], g1 = -(g0 + g2);
-            const double r0 = 1.0 / wz[0], r1 = 1.0 / wz[1], r2 = 1.0 / wz[2];
+            const double r0 = vz[0], r1 = vz[1], r2 = vz[2];
             const double kz = fmax(th[1] * th[1] * sec2 * sec2, 1e-20);
             const double w0 = r0 * yv[0], w1 = r1 * yv[1], w2 = r2 * yv[2];
-            const double f = (g0 * w0 + g1 * w1 + g2 * w2) / (kz + g0 * g0 * r0 + g1 * g1 * r1 + g2 * g2 * r2);
+            const double f = (g0 * w0 + g1 * w1 + g2 * w2) * rcp_d(kz + g0 * g0 * r0 + g1 * g1 * r1 + g2 * g2 * r2);
             yv[0] = w0 - r0 * g0 * f;
             yv[1] = w1 - r1 * g1 * f;
             yv[2] = w2 - r2 * g2 * f;
@@ -189,7 +210,7 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
     if constexpr (N != 3) chol_d<N>(A);
     solve_line(v);
     // 4) circle fit: B x = b, x = (u_0 .. u_{n-1}, dk)
-    const double wu = 1.0 / ((double)p.fit.sigma_rphi * p.fit.sigma_rphi);
+    const double wu = rcp_d((double)p.fit.sigma_rphi * p.fit.sigma_rphi);
     double B[M * (M + 1) / 2], xs[M];
 #pragma unroll
     for (int i = 0; i < M * (M + 1) / 2; i++) B[i] = 0.0;
@@ -210,9 +231,9 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
     }
     auto solve_circle = [&](double *yv) {
         if constexpr (N == 3) {
-            const double h0 = ids[1], h2 = ids[2], h1 = -(h0 + h2), ih3 = 1.0 / (-0.5 * (ds[1] + ds[2]));
+            const double h0 = ids[1], h2 = ids[2], h1 = -(h0 + h2), ih3 = rcp_d(-0.5 * (ds[1] + ds[2]));
             const double a0 = -h0 * ih3, a1 = -h1 * ih3, a2 = -h2 * ih3;
-            const double s2 = 1.0 / wu, kv = fmax(th[1] * th[1] * sec2, 1e-20);
+            const double s2 = (double)p.fit.sigma_rphi * p.fit.sigma_rphi, kv = fmax(th[1] * th[1] * sec2, 1e-20);
             const double ay = a0 * yv[0] + a1 * yv[1] + a2 * yv[2], y3 = yv[3];
             yv[0] = s2 * (yv[0] + a0 * y3);
             yv[1] = s2 * (yv[1] + a1 * y3);
@@ -234,7 +255,7 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
     const double Xo = -(px * cp + py * sp), Yo = px * sp - py * cp;
     const double U = kf * (Xo * Xo + Yo * Yo) - 2.0 * Yo;
     const double q1 = 1.0 + kf * U;
-    const double S = sqrt(fmax(q1, 0.0));
+    const double S = sqrt_d(fmax(q1, 0.0)), i1S = rcp_d(1.0 + S);
     const double Aa = kf * Xo, Bb = 1.0 - kf * Yo;
     const double dpsi = atan2(Aa, Bb);
     const double tanl = (v[1] - v[0]) * ids[1];
@@ -269,8 +290,8 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
         Xob += arcb;
     }
     {
-        const double r2 = Aa * Aa + Bb * Bb;
-        const double Aab = dpsib * Bb / r2, Bbb = -dpsib * Aa / r2;
+        const double ir2 = rcp_d(Aa * Aa + Bb * Bb);
+        const double Aab = dpsib * Bb * ir2, Bbb = -dpsib * Aa * ir2;
         kfb += Aab * Xo;
         Xob += Aab * kf;
         kfb -= Bbb * Yo;
@@ -278,10 +299,10 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
     }
     {
         // d0 = -U / (1 + S), S = sqrt(1 + kf U)
-        Ub += -gd0 / (1.0 + S);
-        const double Sb = gd0 * U / ((1.0 + S) * (1.0 + S));
+        Ub += -gd0 * i1S;
+        const double Sb = gd0 * U * i1S * i1S;
         if (q1 > 0.0 && S > 0.0) {
-            const double qb = Sb / (2.0 * S);
+            const double qb = 0.5 * Sb * rcp_d(S);
             kfb += qb * U;
             Ub += qb * kf;
         }
@@ -382,7 +403,7 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
     for (int i = 0; i < N; i++)
         if (disk[i]) {
             // wz = 1 / (sigma_r atl)^2
-            atlb += wzb[i] * (-2.0 * wz[i] / atl);
+            atlb += wzb[i] * (-2.0 * wz[i] * iatl);
         }
 #pragma unroll
     for (int i = 1; i < N - 1; i++) {
@@ -398,24 +419,25 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
         }
         const double thb = 2.0 * th[i] * th2b;
         // th = 0.0136 / pmom * sqrt(xx0) * (1 + 0.038 ln xx0)
-        pmomb += -thb * th[i] / pmom;
-        const double sx = sqrt(xx0[i]);
-        const double xx0b = thb * 0.0136 / pmom * ((1.0 + 0.038 * log(xx0[i])) / (2.0 * sx) + sx * 0.038 / xx0[i]);
+        pmomb += -thb * th[i] * ipmom;
+        const double sx = sqrt_d(xx0[i]);
+        const double xx0b =
+            thb * 0.0136 * ipmom * ((1.0 + 0.038 * log(xx0[i])) * 0.5 * rcp_d(sx) + sx * 0.038 * rcp_d(xx0[i]));
         // xx0 = x0 sqrt(sec2) [/ atl]
-        sec2b += xx0b * xx0[i] / (2.0 * sec2);
-        if (disk[i]) atlb += -xx0b * xx0[i] / atl;
+        sec2b += 0.5 * xx0b * xx0[i] * rcp_d(sec2);
+        if (disk[i]) atlb += -xx0b * xx0[i] * iatl;
     }
     double tanl0b = 0.0;
     if (fabs(tanl0) > 1e-3) tanl0b += atlb * (tanl0 > 0.0 ? 1.0 : -1.0);
     // pmom = pt0 sqrt(sec2), pt0 = c bz / max(|k0|, 1e-7)
-    sec2b += pmomb * pt0 / (2.0 * rsec);
+    sec2b += 0.5 * pmomb * pt0 * rcp_d(rsec);
     const double pt0b = pmomb * rsec;
-    if (fabs(k0) > 1e-7) k0b += pt0b * (-pt0 / ak) * (k0 > 0.0 ? 1.0 : -1.0);
+    if (fabs(k0) > 1e-7) k0b += pt0b * (-pt0 * iak) * (k0 > 0.0 ? 1.0 : -1.0);
     tanl0b += 2.0 * tanl0 * sec2b;
     // tanl0 = (z_{n-1} - z_0) / max(s_{n-1}, 1e-4)
-    zb[N - 1] += tanl0b / Sl;
-    zb[0] -= tanl0b / Sl;
-    if (s[N - 1] > 1e-4) sb[N - 1] -= tanl0b * tanl0 / Sl;
+    zb[N - 1] += tanl0b * iSl;
+    zb[0] -= tanl0b * iSl;
+    if (s[N - 1] > 1e-4) sb[N - 1] -= tanl0b * tanl0 * iSl;
     // ids = 1/ds, ds = max(s_i - s_{i-1}, 1e-4)
 #pragma unroll
     for (int i = 1; i < N; i++) {
@@ -430,10 +452,10 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
     for (int i = 1; i < N; i++) {
         double dxb = 0.0, dyb = 0.0;
         // m = -U / (1 + Sq), Sq = sqrt(max(1 + k0 U, 0))
-        double Ubi = -mb[i] / (1.0 + Sq[i]);
+        double Ubi = -mb[i] * i1Sq[i];
         if (1.0 + k0 * Us[i] > 0.0 && Sq[i] > 0.0) {
-            const double Sqb = mb[i] * Us[i] / ((1.0 + Sq[i]) * (1.0 + Sq[i]));
-            const double qb = Sqb / (2.0 * Sq[i]);
+            const double Sqb = mb[i] * Us[i] * i1Sq[i] * i1Sq[i];
+            const double qb = 0.5 * Sqb * rcp_d(Sq[i]);
             k0b += qb * Us[i];
             Ubi += qb * k0;
         }
@@ -451,8 +473,9 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
             const double da = qin ? dasinc_d(qs[i]) : 0.0;
             const double distb = sb[i] * (asinc_d(qs[i]) + dist[i] * da * 0.5 * k0);
             k0b += sb[i] * dist[i] * da * 0.5 * dist[i];
-            dxb += distb * dxs[i] / dist[i];
-            dyb += distb * dys[i] / dist[i];
+            const double idist = rcp_d(dist[i]);
+            dxb += distb * dxs[i] * idist;
+            dyb += distb * dys[i] * idist;
         }
         xb[i] += dxb;
         xb[0] -= dxb;
@@ -465,31 +488,32 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
     double abxb = 0.0, abyb = 0.0, acxb = 0.0, acyb = 0.0, bcxb = 0.0, bcyb = 0.0, dabb = 0.0;
     {
         // psi0 = atan2(aby, abx) - asin(ta), ta = k0 dab / 2
-        const double r2 = abx * abx + aby * aby;
-        abyb += psi0b * abx / r2;
-        abxb += -psi0b * aby / r2;
+        const double ir2 = rcp_d(abx * abx + aby * aby);
+        abyb += psi0b * abx * ir2;
+        abxb += -psi0b * aby * ir2;
         if (ta_in) {
-            const double tb = -psi0b / sqrt(1.0 - ta * ta);
+            const double tb = -psi0b * rsqrt_d(1.0 - ta * ta);
             k0b += tb * 0.5 * dab;
             dabb += tb * 0.5 * k0;
         }
     }
     if (den > 0.0) {
         // k0 = 2 orient / (dab dbc dca)
-        const double orb = k0b * 2.0 / den;
-        const double denb = -k0b * k0 / den;
+        const double orb = k0b * 2.0 * iden;
+        const double denb = -k0b * k0 * iden;
         dabb += denb * dbc * dca;
         const double dbcb = denb * dab * dca, dcab = denb * dab * dbc;
         abxb += orb * acy;
         acyb += orb * abx;
         abyb -= orb * acx;
         acxb -= orb * aby;
-        abxb += dabb * abx / dab;
-        abyb += dabb * aby / dab;
-        bcxb += dbcb * bcx / dbc;
-        bcyb += dbcb * bcy / dbc;
-        acxb += dcab * acx / dca;
-        acyb += dcab * acy / dca;
+        const double idab = rcp_d(dab), idbc = rcp_d(dbc), idca = rcp_d(dca);
+        abxb += dabb * abx * idab;
+        abyb += dabb * aby * idab;
+        bcxb += dbcb * bcx * idbc;
+        bcyb += dbcb * bcy * idbc;
+        acxb += dcab * acx * idca;
+        acyb += dcab * acy * idca;
     } else {
         const double r2 = abx * abx + aby * aby;
         (void)r2;
