@@ -115,14 +115,20 @@ __global__ void __launch_bounds__(kThreads) k_clean_max(Params p) {
 __global__ void __launch_bounds__(kThreads) k_clean_keep(Params p) {
     const int64_t nt = min((int64_t)p.counters[C_TUPLES], p.cap_tuples);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int kept = 0;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
         const int n = p.tup_n[t];
         const int32_t *cells = p.tup_cells + t * PT_NMAX;
         bool keep = true;
-        for (int k = 0; k < n - 1; k++) keep = keep && n >= p.maxlen[cells[k]];
+#pragma unroll
+        for (int k = 0; k < PT_NMAX - 1; k++)     // independent loads
+            if (k < n - 1) keep &= n >= p.maxlen[cells[k]];
         p.tup_alive[t] = keep;
-        if (keep) atomicAdd(p.counters + C_ALIVE_TUPLES, 1);
+        kept += keep;
     }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, d);
+    if ((threadIdx.x & 31) == 0 && kept) atomicAdd(p.counters + C_ALIVE_TUPLES, kept);
 }
 
 // queue the surviving n-tuplets with >= min_hits hits for the fit
