@@ -126,15 +126,17 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
     // pass 1: R-z slope keys (barrel o: (z_o - z_a)/(r_o - r_a); disk o:
     // (r_o - r_a)/(z_o - z_a)) with the per-hit bounds; records and the
     // range of the bucket keys
-    float kmax = 0.f, gmin = 3.0e38f, bmin = 3.0f, bmax = -3.0f;
+    float k2max = 0.f, gmin = 3.0e38f, bmin = 3.0f, bmax = -3.0f;
     for (int j = lane; j < n; j += 32) {
         const int i = p.cell_inner[b + j];
         const int L = cell_layer(p, b + j);
         const float4 a = __ldg(p.bh + i);
         const float dr = ho.w - a.w, dz = ho.z - a.z;
         const float num = disk ? dr : dz, den = disk ? dz : dr;
-        const float ck = den != 0.f ? num / den : __int_as_float(0x7f800000);
-        kmax = fmaxf(kmax, sqrtf(1.0f + ck * ck));
+        // the key only places the cell in the connection's search window,
+        // whose margins (1e-5 relative) are far above the 2 ulp of this quotient
+        const float ck = den != 0.f ? __fdividef(num, den) : __int_as_float(0x7f800000);
+        k2max = fmaxf(k2max, ck * ck);
         gmin = fminf(gmin, fabsf(den));
         if (C && in_smem) {
             sm.ck[w][j] = ck;
@@ -155,9 +157,10 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
-        kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, d));
+        k2max = fmaxf(k2max, __shfl_xor_sync(0xffffffffu, k2max, d));
         gmin = fminf(gmin, __shfl_xor_sync(0xffffffffu, gmin, d));
     }
+    const float kmax = sqrtf(1.0f + k2max);        // max of sqrt(1 + key^2)
     if (lane == 0) p.hk[o] = make_float2(kmax, gmin);
     __syncwarp();
 
