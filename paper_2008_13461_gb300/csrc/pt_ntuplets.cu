@@ -32,6 +32,61 @@ __global__ void __launch_bounds__(kThreads) k_edge_records(Params p) {
     }
 }
 
+// A path being searched: per depth d (0 = the leaf), the cell and its inner
+// hit's input index * 2 + root flag.  Indexed with compile-time depths only,
+// so it lives in registers.
+struct DfsPath {
+    int32_t cell[PT_NMAX - 1];
+    int32_t hit[PT_NMAX - 1];
+};
+
+// the path of cells cell[D] (a root) .. cell[0] (the leaf) as an n-tuplet
+template <int D>
+__device__ __forceinline__ void dfs_emit(const Params &p, const DfsPath &pa, int leaf_outer) {
+    // one atomic for the lanes that emit together
+    const unsigned am = __activemask();
+    const int leader = __ffs(am) - 1, lane = threadIdx.x & 31;
+    int t = 0;
+    if (lane == leader) t = atomicAdd(p.counters + C_TUPLES, __popc(am));
+    t = __shfl_sync(am, t, leader) + __popc(am & ((1u << lane) - 1u));
+    if (t >= p.cap_tuples) {
+        set_flag(p.counters, PT_FLAG_TUPLES);
+        return;
+    }
+    int32_t *hits = p.tup_hits + (int64_t)t * PT_NMAX;
+    int32_t *cells = p.tup_cells + (int64_t)t * PT_NMAX;
+    hits[0] = pa.hit[D] >> 1;
+#pragma unroll
+    for (int q = 0; q <= D; q++) {
+        // the outer hit of a cell is the inner hit of the next one
+        cells[q] = pa.cell[D - q];
+        hits[q + 1] = D - q >= 1 ? pa.hit[D - q - 1] >> 1 : leaf_outer;
+    }
+    p.tup_n[t] = (uint8_t)(D + 2);
+    p.tup_alive[t] = 1;
+}
+
+// Depth D of the search: cell[D] has cnt incoming edges from position first.
+// No incoming edge: a path starts here, emitted if cell[D] is a root and the
+// path has at least three hits.  Paths longer than PT_NMAX hits are cut.
+template <int D>
+__device__ __forceinline__ void dfs_level(const Params &p, DfsPath &pa, int first, int cnt, int leaf_outer) {
+    if (cnt == 0) {
+        if (D >= 1 && (pa.hit[D] & 1)) dfs_emit<D>(p, pa, leaf_outer);
+        return;
+    }
+    if constexpr (D + 1 < PT_NMAX - 1) {
+        for (int it = 0; it < cnt; it++) {
+            const int64_t e = (int64_t)first + it;
+            if (e >= p.cap_edges) continue;
+            const int4 r = p.erec[e];
+            pa.cell[D + 1] = r.x;
+            pa.hit[D + 1] = r.w;
+            dfs_level<D + 1>(p, pa, r.y, r.z, leaf_outer);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_dfs(Params p) {
     if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int64_t n_list = min((int64_t)p.counters[C_LEAVES], p.cap_cells);
@@ -40,63 +95,11 @@ __global__ void __launch_bounds__(kThreads) k_dfs(Params p) {
         // the list holds the live cells with incoming edges; leaves have no outer neighbour
         const int c = p.leaf_list[k];
         if (p.has_out[c]) continue;
-        // per depth: the cell, its first incoming edge and their count, the
-        // edges taken, its inner hit * 2 + root
-        int32_t st_cell[PT_NMAX - 1], st_first[PT_NMAX - 1], st_cnt[PT_NMAX - 1], st_it[PT_NMAX - 1];
-        int32_t st_hit[PT_NMAX - 1];
         const int2 er = p.edge_rng[c];
-        const int leaf_outer = p.perm[p.cell_outer[c]];
-        int depth = 0;
-        st_cell[0] = c;
-        st_first[0] = er.x;
-        st_cnt[0] = er.y;
-        st_it[0] = 0;
-        st_hit[0] = p.perm[p.cell_inner[c]] * 2;
-        while (depth >= 0) {
-            const int cnt = st_cnt[depth], taken = st_it[depth];
-            if (cnt == 0) {
-                // start of a path: emit if it is a root and the path has >= 3 hits
-                if (depth >= 1 && (st_hit[depth] & 1)) {
-                    // one atomic for the lanes that emit together
-                    const unsigned am = __activemask();
-                    const int leader = __ffs(am) - 1, lane = threadIdx.x & 31;
-                    int t = 0;
-                    if (lane == leader) t = atomicAdd(p.counters + C_TUPLES, __popc(am));
-                    t = __shfl_sync(am, t, leader) + __popc(am & ((1u << lane) - 1u));
-                    if (t < p.cap_tuples) {
-                        const int n = depth + 2;
-                        int32_t *hits = p.tup_hits + (int64_t)t * PT_NMAX;
-                        int32_t *cells = p.tup_cells + (int64_t)t * PT_NMAX;
-                        hits[0] = st_hit[depth] >> 1;
-                        for (int q = 0; q <= depth; q++) {
-                            // the outer hit of a cell is the inner hit of the next one
-                            cells[q] = st_cell[depth - q];
-                            hits[q + 1] = depth - q >= 1 ? st_hit[depth - q - 1] >> 1 : leaf_outer;
-                        }
-                        p.tup_n[t] = (uint8_t)n;
-                        p.tup_alive[t] = 1;
-                    } else {
-                        set_flag(p.counters, PT_FLAG_TUPLES);
-                    }
-                }
-                depth--;
-                continue;
-            }
-            if (taken < cnt) {
-                const int64_t eidx = (int64_t)st_first[depth] + taken;
-                st_it[depth] = taken + 1;
-                if (eidx >= p.cap_edges || depth + 1 >= PT_NMAX - 1) continue;
-                const int4 r = p.erec[eidx];
-                depth++;
-                st_cell[depth] = r.x;
-                st_first[depth] = r.y;
-                st_cnt[depth] = r.z;
-                st_it[depth] = 0;
-                st_hit[depth] = r.w;
-            } else {
-                depth--;
-            }
-        }
+        DfsPath pa;
+        pa.cell[0] = c;
+        pa.hit[0] = p.perm[p.cell_inner[c]] * 2;
+        dfs_level<0>(p, pa, er.x, er.y, p.perm[p.cell_outer[c]]);
     }
 }
 
