@@ -45,3 +45,25 @@ def test_workspace_size_is_host_only():
     assert n > 4 * 128 * 16 * 10 * 4
     cfg.tuning = L.Tuning(7, 16, 8, 8, 8)
     assert L.workspace_size(h, cfg) == 0
+
+
+def test_post_fit_entry_points_reject_bad_arguments_without_gpu():
+    """Argument checks return before any device call."""
+    import ctypes as C
+    from paper_2008_13461_gb300 import _lib as L
+    lib = L.lib()
+    bad = 1   # PT_ERR_INVALID_ARG
+    assert lib.pt_vertex_scratch_size(-1, 4) == 0
+    assert lib.pt_vertex_scratch_size(1000, 4) >= 4 * 3 * 1000
+    trk = L.VertexTracks()
+    out = L.Vertices()
+    cuts = L.VertexCuts(0.5, 0.05, 0.07, 9.0, 9.0, 4, 2)
+    assert lib.pt_find_vertices(None, 10, 1, C.byref(cuts), 8, None, 0, C.byref(out), None) == bad
+    assert lib.pt_find_vertices(C.byref(trk), 10, 1, C.byref(cuts), 0, None, 0, C.byref(out), None) == bad
+    cuts.min_tracks = 0
+    assert lib.pt_find_vertices(C.byref(trk), 10, 1, C.byref(cuts), 8, None, 0, C.byref(out), None) == bad
+    h = L.Hits(None, None, None, None, None, None, 10, 0)
+    assert lib.pt_track_summary(C.byref(h), C.byref(L.Tuples()), C.byref(L.Tracks()), 5, 3.8,
+                                None, None, None, None, None, None) == bad
+    assert lib.pt_resolve_ambiguities(C.byref(L.Tuples()), None, -1, None, None, 5, 0, 0, None, None, None) == bad
+    assert lib.pt_align_hits(10, None, None, None, None, 0, None, None, None, None, None, None, None) == bad
