@@ -18,10 +18,10 @@ from typing import Callable
 import torch
 
 SPACE = (
-    ("n_t_bins", (16, 32, 64)),
-    ("n_phi_bins", (64, 128, 256)),
+    ("n_t_bins", (24, 32, 48, 64)),
+    ("n_phi_bins", (32, 48, 64, 96, 128)),
     ("doublet_lanes", (4, 8, 16)),
-    ("blocks_per_sm", (4, 8, 16)),
+    ("blocks_per_sm", (8, 12, 16, 24, 32)),
 )
 
 
