@@ -16,7 +16,7 @@ import torch
 
 from . import _lib as L
 
-DEFAULT_TUNING = dict(n_phi_bins=128, n_t_bins=32, doublet_lanes=8, connect_lanes=8, blocks_per_sm=8)
+DEFAULT_TUNING = dict(n_phi_bins=96, n_t_bins=48, doublet_lanes=8, connect_lanes=8, blocks_per_sm=24)
 
 # Vertex-finder cuts (Sec. 3.6 fixes pT > 0.5 GeV, >= 4 hits, the split at
 # chi2/ndf > 9 and >= 2 tracks per vertex; the z0-error, dz and chi2
