@@ -129,18 +129,26 @@ KERNELS_PER_STEP = 23
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "dram_traffic_pu200_batch8.md")
 
 
+# the sources of the four seeding and fitting calls (whose DRAM traffic the
+# profile summary records); the post-fit and adjoint kernels are not among them
+PIPELINE_SOURCES = ("pt_common.cuh", "pt_kernels.cuh", "pt_bin.cu", "pt_doublets.cu", "pt_fishbone.cu",
+                    "pt_connect.cu", "pt_ntuplets.cu", "pt_fit.cu", "pt_abi.cu")
+
+
 def kernel_source_hash() -> str:
-    """Hash of the CUDA sources and the ABI header (which counters a profile
-    summary was taken on)."""
+    """Hash of the code (comments and blank space removed) of the pipeline's
+    CUDA sources and the ABI header: which kernels a profile summary was
+    taken on."""
     import hashlib
+    import re
     h = hashlib.sha256()
-    for d in (os.path.join(ROOT, "paper_2008_13461_gb300", "csrc"), os.path.join(ROOT, "include")):
-        for f in sorted(os.listdir(d)):
-            p = os.path.join(d, f)
-            if os.path.isfile(p):
-                h.update(f.encode())
-                with open(p, "rb") as fh:
-                    h.update(fh.read())
+    csrc = os.path.join(ROOT, "paper_2008_13461_gb300", "csrc")
+    for p in [os.path.join(csrc, f) for f in PIPELINE_SOURCES] + [os.path.join(ROOT, "include", "pt.h")]:
+        with open(p) as fh:
+            code = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        code = re.sub(r"//[^\n]*", "", code)
+        h.update(os.path.basename(p).encode())
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 
