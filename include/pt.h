@@ -330,8 +330,9 @@ size_t pt_vertex_scratch_size(int32_t n_tracks, int32_t n_events);
 
 /* Sec. 3.6: vertices as clusters of tracks in z0.  Each eligible track gets a
  * density rho = 1 + the number of compatible tracks; it links to the nearest
- * compatible track (smallest |dz|, then smallest index) of higher rank
- * (larger rho, or equal rho and smaller index); every track whose links lead
+ * compatible track (smallest |dz|, then smaller z0, then smaller index) of
+ * higher rank (larger rho, or equal rho and smaller z0, or equal rho and z0
+ * and smaller index); every track whose links lead
  * to a root with rho > 1 joins that root's candidate, and candidates of at
  * least min_tracks tracks are vertices: z the mean of z0 weighted by
  * 1/ez0^2, ez = 1/sqrt(sum of weights), chi2 = sum w (z0 - z)^2 (float64).

@@ -82,8 +82,11 @@ def find_vertices(ev, z0, ez0, pt, nhits, keep, n_events, cuts: dict):
       condition, means at least one compatible neighbour, and a 2-track
       cluster can form a vertex);
     * each eligible track links to its nearest compatible track (smallest
-      |dz|, then smallest index) ranking higher: larger rho, or equal rho
-      and smaller index; tracks without such a track are roots;
+      |dz|, then smaller z0, then smallest index) ranking higher: larger
+      rho, or equal rho and smaller z0, or equal rho and z0 and smaller
+      index; tracks without such a track are roots (ties go by z0 before
+      the index, so the result does not depend on the order of the tracks
+      unless two share a z0);
     * a root with rho > 1 seeds a vertex candidate made of every track whose
       links lead to it; a candidate with at least min_tracks tracks is a
       vertex: z = weighted mean of z0 (w = 1/ez0^2), ez = 1/sqrt(sum w),
@@ -129,13 +132,15 @@ def find_vertices(ev, z0, ez0, pt, nhits, keep, n_events, cuts: dict):
         rho = {int(ids[a]): int(R[a]) for a in range(len(ids))}
         parent = {}
         for a, i in enumerate(ids.tolist()):
-            higher = (R > R[a]) | ((R == R[a]) & (ids < i))
+            higher = (R > R[a]) | ((R == R[a]) & ((zs < zs[a]) | ((zs == zs[a]) & (ids < i))))
             cand = np.nonzero(rows[a] & higher)[0]
             if len(cand) == 0:
                 parent[i] = None
                 continue
             d = np.abs(zs[a] - zs[cand])                        # float32 |dz|
-            parent[i] = int(ids[cand[d == d.min()]].min())      # nearest, then smallest index
+            near = cand[d == d.min()]                           # nearest,
+            near = near[zs[near] == zs[near].min()]             # then smaller z0,
+            parent[i] = int(ids[near].min())                    # then smallest index
 
         def root(i):
             while parent[i] is not None:

@@ -6,8 +6,10 @@
 // i, j of an event are compatible when dz = z0_i - z0_j satisfies
 // |dz| < dz_cut and dz^2 < chi2_max (ez0_i^2 + ez0_j^2).  A track's density
 // rho is 1 + the number of tracks compatible with it; each track links to the
-// nearest compatible track (smallest |dz|, then smallest index) of higher
-// rank (larger rho, or equal rho and smaller index); the links end at roots
+// nearest compatible track (smallest |dz|, then smaller z0, then smaller
+// index) of higher rank (larger rho, or equal rho and smaller z0, or equal
+// rho and z0 and smaller index: ties go by z0 first, so the result does not
+// depend on the order of the tracks unless two share a z0); the links end at roots
 // (ranks grow along them, so there are no cycles), and a root with rho > 1
 // seeds a candidate made of every track whose links lead to it.  Candidates
 // with at least min_tracks tracks become vertices: z the mean of z0 weighted
@@ -242,24 +244,24 @@ __global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_event(VtxArgs a) {
         rho[p] = r;
     }
     __syncthreads();
-    // links to the nearest compatible track of higher rank
+    // links to the nearest compatible track of higher rank; the sorted
+    // position orders equal densities and equal distances by (z0, index)
     for (int p = tid; p < cnt; p += blockDim.x) {
         const float zp = sz[p];
-        const int ip = sid[p], rp = rho[p];
+        const int rp = rho[p];
         const float ep = sez[p], ep2 = __fmul_rn(ep, ep);
-        int best = -1, bid = 0;
+        int best = -1;
         float bd = 0.f;
         for (int dir = -1; dir <= 1; dir += 2)
             for (int q = p + dir; q >= 0 && q < cnt; q += dir) {
                 const float dz = __fsub_rn(zp, sz[q]), ad = fabsf(dz);
                 if (!(ad < dzc)) break;
-                const int iq = sid[q], rq = rho[q];
-                if (!(rq > rp || (rq == rp && iq < ip))) continue;
+                const int rq = rho[q];
+                if (!(rq > rp || (rq == rp && q < p))) continue;
                 if (!chi2_ok(dz, ep2, sez[q], c2m)) continue;
-                if (best < 0 || ad < bd || (ad == bd && iq < bid)) {
+                if (best < 0 || ad < bd || (ad == bd && q < best)) {
                     best = q;
                     bd = ad;
-                    bid = iq;
                 }
             }
         root[p] = best < 0 ? p : best;

@@ -160,3 +160,15 @@ def test_vertices_of_the_pipeline_tracks():
             w = 1.0 / ez[m] ** 2
             assert m.sum() == int(v["ntracks"][e, k])
             assert abs(float(v["z"][e, k]) - np.sum(w * z0[m]) / np.sum(w)) <= 1e-5
+
+
+def test_vertices_do_not_depend_on_the_order_of_the_tracks():
+    d = vertex_tracks(10, 4, pileup=40.0)
+    assert len(np.unique(d["z0"])) == len(d["z0"])          # distinct z0: no tie left to the index
+    g1 = _gpu(d, 4)
+    perm = np.random.default_rng(2).permutation(len(d["z0"]))
+    g2 = _gpu({k: d[k][perm] for k in KEYS}, 4)
+    assert np.array_equal(g1["n"], g2["n"])
+    assert np.array_equal(g1["track_vertex"][perm], g2["track_vertex"])
+    assert np.array_equal(g1["ntracks"], g2["ntracks"])
+    assert np.allclose(g1["z"], g2["z"], rtol=1e-6, atol=1e-6)

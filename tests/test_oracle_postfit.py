@@ -135,3 +135,17 @@ def test_track_summary_inverts_the_generator_curvature_and_reads_the_z0_variance
     assert np.allclose(s["ez0"] ** 2, [2 * (24 + k) for k in range(4)])   # M[4, 4] = 2 (24 + k)
     assert np.array_equal(s["z0"], params[:, 4])
     assert np.array_equal(s["nhits"], [3, 4, 5, 6])
+
+
+def test_vertices_do_not_depend_on_the_order_of_the_tracks():
+    from synth.vertices import vertex_tracks
+    d = vertex_tracks(8, 2, pileup=30.0)
+    keys = ("ev", "z0", "ez0", "pt", "nhits", "keep")
+    assert len(np.unique(d["z0"])) == len(d["z0"])          # distinct z0: no tie left to the index
+    v1, i1 = postfit.find_vertices(*(d[k] for k in keys), 2, VCUTS)
+    perm = np.random.default_rng(1).permutation(len(d["z0"]))
+    v2, i2 = postfit.find_vertices(*(d[k][perm] for k in keys), 2, VCUTS)
+    assert np.array_equal(i1[perm], i2)
+    for a, b in zip(v1, v2):                                # the sums only change their order
+        assert [len(v["tracks"]) for v in a] == [len(v["tracks"]) for v in b]
+        assert np.allclose([v["z"] for v in a], [v["z"] for v in b], rtol=0, atol=1e-12)
