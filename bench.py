@@ -41,13 +41,14 @@ def _peaks():
 
 
 # ------------------------------------------------------------- CPU oracle
-def _oracle_sample(batch):
+def _oracle_sample(batch, sector: int = 0):
     import numpy as np
-    phi = np.arctan2(batch["y"], batch["x"])
+    phi = np.arctan2(batch["y"], batch["x"]) + np.pi
     a, b = batch["ev_off"][0], batch["ev_off"][1]
     m = np.zeros(batch["x"].size, bool)
     m[a:b] = True
-    m &= (phi >= 0) & (phi < 2 * np.pi / SECTOR)
+    lo = (sector + SECTOR // 2) % SECTOR            # sector 0 is phi in [0, 2 pi / SECTOR)
+    m &= (phi >= lo * 2 * np.pi / SECTOR) & (phi < (lo + 1) * 2 * np.pi / SECTOR)
     s = {k: batch[k][m] for k in ("x", "y", "z", "r", "module")}
     s["ev_off"] = np.array([0, int(m.sum())], dtype=np.int32)
     return s
@@ -64,6 +65,45 @@ def _time_oracle(sample, repeats):
         oracle.run(sample, CU.cuts_for_config(3), CU.FIT_PARAMS, G.module_layer_table(), [0] * 4 + [1] * 6)
         times.append(time.perf_counter() - t)
     return times
+
+
+def _oracle_sector_worker(sample):
+    """One sector through the oracle in a worker process; seconds taken."""
+    import oracle
+    from synth import cuts as CU
+    from synth import geometry as G
+    t = time.perf_counter()
+    oracle.run(sample, CU.cuts_for_config(3), CU.FIT_PARAMS, G.module_layer_table(), [0] * 4 + [1] * 6)
+    return time.perf_counter() - t
+
+
+def _time_oracle_all_cores(batch):
+    """Wall time of the oracle over the SECTOR azimuthal sectors of PU200
+    event 0, one sector per worker process (spawned), on all host cores."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    samples = [_oracle_sample(batch, k) for k in range(SECTOR)]
+    workers = max(1, min(SECTOR, os.cpu_count() or 1))
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_oracle_sector_worker, samples[:workers]))          # warm the workers up
+        t = time.perf_counter()
+        list(ex.map(_oracle_sector_worker, samples))
+        wall = time.perf_counter() - t
+    return wall, workers, sum(int(x["x"].size) for x in samples)
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
 
 
 def _cpu_desc(n_hits):
@@ -152,20 +192,58 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(stage: str, cells: int):
-    """DRAM bytes of one launch of an ABI call, scaled by cells from the
-    committed ncu summary; None when the kernels changed since it was taken."""
+def _profile_entry(key: str):
+    """Value list of `key:` in the committed ncu summary, or None when the
+    kernels changed since it was taken."""
     try:
         with open(TRAFFIC_PROFILE) as fh:
             lines = fh.read().splitlines()
     except OSError:
         return None
     src = next((l.split(":", 1)[1].strip() for l in lines if l.startswith("kernel_sources:")), None)
-    per = next((l.split(":", 1)[1].split() for l in lines if l.startswith("traffic_bytes_per_cell:")), None)
-    if src != kernel_source_hash() or not per:
+    val = next((l.split(":", 1)[1].split() for l in lines if l.startswith(key + ":")), None)
+    return val if src == kernel_source_hash() and val else None
+
+
+def measured_traffic(stage: str, cells: int):
+    """DRAM bytes of one launch of an ABI call, scaled by cells from the
+    committed ncu summary; None when the kernels changed since it was taken."""
+    per = _profile_entry("traffic_bytes_per_cell")
+    if not per:
         return None
     table = dict(kv.split("=") for kv in per)
     return float(table[stage]) * cells if stage in table else None
+
+
+def measured_fit_flops(tracks: int):
+    """float64 flops of one pt_fit_tracks call (FMA = 2, add, multiply),
+    scaled by tracks from the ncu instruction counts of the summary."""
+    per = _profile_entry("fit_fp64_flops_per_track")
+    return float(per[0]) * tracks if per else None
+
+
+def measure_alu_peaks(dev, stream):
+    """The GPU's float32 and float64 fused-multiply-add peaks, from the
+    library's probe (8 independent FMA chains per thread, 2048 threads per
+    SM), best of 5 launches after one warm-up."""
+    import torch
+    from paper_2008_13461_gb300 import _lib as L
+    n = torch.cuda.get_device_properties(dev).multi_processor_count * 2048
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    out = {}
+    for fp64, iters in ((False, 4096), (True, 256)):
+        buf = torch.empty(n, dtype=torch.float64 if fp64 else torch.float32, device=dev)
+        times = []
+        for k in range(6):
+            ev[0].record(stream)
+            L.fma_probe(fp64, iters, n, buf.data_ptr(), stream.cuda_stream)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            if k:
+                times.append(ev[0].elapsed_time(ev[1]))
+        out["fp64_tflops" if fp64 else "fp32_tflops"] = 16.0 * iters * n / (min(times) * 1e-3) / 1e12
+    out["method"] = "pt_fma_probe: dependent FMA chains, 8 per thread, 2048 threads per SM, best of 5"
+    return out
 
 
 def algorithmic_bytes(H, D, E, T, K, nbar):
@@ -452,15 +530,34 @@ def run_native(args, rank, world, local_rank):
     peak, peak_kind = _peaks()
     achieved = stage_bytes[dom] / (stage_ms[dom] * 1e-3) / 1e9
 
+    # the fit is bound by the float64 pipe: its arithmetic roofline
+    alu = measure_alu_peaks(dev, stream)
+    fit_flops = measured_fit_flops(K)
+    fit_roofline = {"bound": "alu", "kernel": "fit_tracks", "unit": "TFLOP/s", "precision": "f64",
+                    "peak": alu["fp64_tflops"], "peak_source": alu["method"], "fp32_peak": alu["fp32_tflops"],
+                    "algorithmic_flops": fit_flops,
+                    "flops_source": "ncu float64 instruction counts, profiles/dram_traffic_pu200_batch8.md"}
+    if fit_flops is not None:
+        fit_roofline["achieved"] = fit_flops / (stage_ms[3] * 1e-3) / 1e12
+        fit_roofline["frac"] = fit_roofline["achieved"] / alu["fp64_tflops"]
+
     if rank != 0:
         return None
-    cpu = None
+    cpu = cpu_all = None
     if world == 1 and not args.no_cpu_baseline:
         sample = _oracle_sample(batch)
         times = _time_oracle(sample, repeats=3)
         tm = statistics.median(times)
         cpu = {"value": 1.0 / (SECTOR * tm), "unit": "events/s", "cores": 1, "kind": "oracle",
-               "sample": _cpu_desc(int(sample["x"].size)), "seconds_per_sample": tm}
+               "sample": _cpu_desc(int(sample["x"].size)), "seconds_per_sample": tm, "cpu": _cpu_model()}
+        try:
+            wall, workers, nh = _time_oracle_all_cores(batch)
+            cpu_all = {"value": 1.0 / wall, "unit": "events/s", "cores": workers, "kind": "oracle",
+                       "sample": f"PU200 event 0 as {SECTOR} azimuthal sectors ({nh} hits), one sector per "
+                                 f"process on {workers} host cores; events/s = 1 / wall time",
+                       "cpu": _cpu_model()}
+        except Exception as exc:   # reported, never required
+            cpu_all = f"unavailable: {exc}"
     events_total = n_ev * world
     value = events_total / (ms_per_step * 1e-3)
     line = {
@@ -498,9 +595,11 @@ def run_native(args, rank, world, local_rank):
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                      "algorithmic_bytes": stage_bytes[dom], "traffic": measured_traffic(stage_names[dom], D),
                      "traffic_source": "profiles/dram_traffic_pu200_batch8.md, scaled by cells"},
+        "fit_roofline": fit_roofline,
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
     }
     return line
 

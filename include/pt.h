@@ -367,6 +367,14 @@ pt_status pt_align_hits_grad(int32_t n_hits, const float *x, const float *y, con
                              const float *gx_out, const float *gy_out, const float *gz_out, float *gx, float *gy,
                              float *gz, float *grad_shift, float *grad_rot, void *stream);
 
+/* Measurement helper, not part of the method: launches n_threads threads (a
+ * positive multiple of 256) that each run 8 independent chains of `iters`
+ * fused multiply-adds in float64 (fp64 = 1) or float32 (fp64 = 0) and write
+ * one value each to out (device, n_threads elements of that type): 16 *
+ * iters * n_threads flops, to be timed on `stream` for the device's
+ * arithmetic peak. */
+pt_status pt_fma_probe(int32_t fp64, int32_t iters, int32_t n_threads, void *out, void *stream);
+
 /* Synchronises `stream`, then reports counts and device flags.  Returns
  * PT_ERR_CAPACITY or PT_ERR_INPUT when the corresponding flags are set. */
 pt_status pt_read_counts(const void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg,

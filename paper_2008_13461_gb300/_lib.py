@@ -116,7 +116,7 @@ class Counts(C.Structure):
 EXPORTS = ("pt_workspace_size", "pt_build_doublets", "pt_connect_cells", "pt_find_ntuplets",
            "pt_fit_tracks", "pt_fit_tracks_grad", "pt_align_hits", "pt_align_hits_grad",
            "pt_resolve_ambiguities", "pt_track_summary", "pt_vertex_scratch_size", "pt_find_vertices",
-           "pt_read_counts",
+           "pt_fma_probe", "pt_read_counts",
            "pt_hit_order", "pt_status_string", "pt_bin_hits_noalloc")
 
 _lib = None
@@ -161,6 +161,8 @@ def lib(build_if_missing: bool = True):
     L.pt_align_hits.argtypes = [C.c_int32] + [C.c_void_p] * 4 + [C.c_int32] + [C.c_void_p] * 7
     L.pt_align_hits_grad.restype = C.c_int
     L.pt_align_hits_grad.argtypes = [C.c_int32] + [C.c_void_p] * 4 + [C.c_int32] + [C.c_void_p] * 11
+    L.pt_fma_probe.restype = C.c_int
+    L.pt_fma_probe.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]
     L.pt_read_counts.restype = C.c_int
     L.pt_read_counts.argtypes = common + [P(Counts), C.c_void_p]
     L.pt_hit_order.restype = C.c_void_p
@@ -246,6 +248,10 @@ def align_hits_grad(n_hits, x, y, z, module, n_modules, centre, rot, gxo, gyo, g
                     stream) -> None:
     check(lib().pt_align_hits_grad(n_hits, x, y, z, module, n_modules, centre, rot, gxo, gyo, gzo, gx, gy, gz,
                                    gshift, grot, stream), "pt_align_hits_grad")
+
+
+def fma_probe(fp64: bool, iters: int, n_threads: int, out, stream) -> None:
+    check(lib().pt_fma_probe(1 if fp64 else 0, iters, n_threads, out, stream), "pt_fma_probe")
 
 
 def read_counts(ws, ws_bytes, hits, cfg, stream) -> tuple[int, Counts]:
