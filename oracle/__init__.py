@@ -93,6 +93,8 @@ def lib():
         _lib.oracle_fit.argtypes = [C.c_int] + [C.POINTER(C.c_double)] * 3 + [
             C.POINTER(C.c_int), C.POINTER(_FitPar), C.POINTER(C.c_double), C.POINTER(C.c_double),
             C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        _lib.oracle_sym_condition.restype = C.c_double
+        _lib.oracle_sym_condition.argtypes = [C.c_int, C.POINTER(C.c_double)]
         _lib.oracle_run.restype = C.c_int
         _lib.oracle_run.argtypes = [C.POINTER(_Input), C.c_int, C.POINTER(_Result)]
         _lib.oracle_free.restype = None
@@ -133,20 +135,29 @@ def pred(which: str, hits, k: float) -> bool:
 
 def fit(hx, hy, hz, is_disk, fitpar: dict, ms_scale: float = 1.0):
     """Broken-line fit of one track (hits inner to outer).  Returns
-    (params[5], cov[15], chi2, ndf, extra[8])."""
+    (params[5], cov[15], chi2, ndf, extra[10]); extra holds chi2 of the line
+    and circle fits, k0, psi0, tanl0, dk, the arc to the perigee, 0, and the
+    condition numbers of the line and circle normal matrices."""
     n = len(hx)
     hx = np.ascontiguousarray(hx, dtype=np.float64)
     hy = np.ascontiguousarray(hy, dtype=np.float64)
     hz = np.ascontiguousarray(hz, dtype=np.float64)
     dk = np.ascontiguousarray(is_disk, dtype=np.int32)
     fp = make_fitpar(fitpar, ms_scale)
-    p = np.zeros(5); cv = np.zeros(15); chi2 = C.c_double(); ndf = C.c_int(); ex = np.zeros(8)
+    p = np.zeros(5); cv = np.zeros(15); chi2 = C.c_double(); ndf = C.c_int(); ex = np.zeros(10)
     rc = lib().oracle_fit(n, _ptr(hx, C.c_double), _ptr(hy, C.c_double), _ptr(hz, C.c_double),
                           _ptr(dk, C.c_int), C.byref(fp), _ptr(p, C.c_double), _ptr(cv, C.c_double),
                           C.byref(chi2), C.byref(ndf), _ptr(ex, C.c_double))
     if rc != 0:
         raise ValueError("oracle_fit: bad number of hits")
     return p, cv, chi2.value, ndf.value, ex
+
+
+def sym_condition(M) -> float:
+    """2-norm condition number of a symmetric matrix (the oracle's Jacobi
+    eigenvalues)."""
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    return float(lib().oracle_sym_condition(M.shape[0], _ptr(M, C.c_double)))
 
 
 def fit_grad_fd(hx, hy, hz, is_disk, fitpar: dict, gparams, gchi2: float = 0.0, h: float = 2e-5) -> np.ndarray:

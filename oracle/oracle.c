@@ -464,9 +464,56 @@ static void circ_map(double h0x, double h0y, double psi0, double k0, double ds1,
     out[2] = d0;
 }
 
+/* 2-norm condition number max|l| / min|l| of a symmetric n x n matrix
+ * (row-major, n <= OR_NMAX + 1) from its eigenvalues l, found by the cyclic
+ * Jacobi method: plane rotations that zero the off-diagonal entries in turn
+ * until their squared sum is negligible against the diagonal's. */
+double oracle_sym_condition(int n, const double *M) {
+    double a[(OR_NMAX + 1) * (OR_NMAX + 1)];
+    if (n < 1 || n > OR_NMAX + 1) return -1;
+    memcpy(a, M, sizeof(double) * n * n);
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double off = 0, diag = 0;
+        for (int p = 0; p < n; p++)
+            for (int q = 0; q < n; q++) {
+                if (p == q) diag += a[p * n + q] * a[p * n + q];
+                else off += a[p * n + q] * a[p * n + q];
+            }
+        if (off <= 1e-32 * diag) break;
+        for (int p = 0; p < n - 1; p++)
+            for (int q = p + 1; q < n; q++) {
+                const double apq = a[p * n + q];
+                if (apq == 0) continue;
+                /* rotation angle with tan = t zeroing a[p][q]: t solves
+                 * t^2 + 2 theta t - 1 = 0, theta = (a_qq - a_pp) / (2 a_pq) */
+                const double theta = (a[q * n + q] - a[p * n + p]) / (2 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1));
+                const double c = 1 / sqrt(t * t + 1), sn = t * c;
+                for (int k = 0; k < n; k++) {          /* columns p, q */
+                    const double akp = a[k * n + p], akq = a[k * n + q];
+                    a[k * n + p] = c * akp - sn * akq;
+                    a[k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; k++) {          /* rows p, q */
+                    const double apk = a[p * n + k], aqk = a[q * n + k];
+                    a[p * n + k] = c * apk - sn * aqk;
+                    a[q * n + k] = sn * apk + c * aqk;
+                }
+            }
+    }
+    double lo = INFINITY, hi = 0;
+    for (int i = 0; i < n; i++) {
+        const double l = fabs(a[i * n + i]);
+        if (l < lo) lo = l;
+        if (l > hi) hi = l;
+    }
+    return lo > 0 ? hi / lo : INFINITY;
+}
+
 int oracle_fit(int n, const double *hx, const double *hy, const double *hz, const int *is_disk,
                const or_fitpar *fp, double *params, double *cov, double *chi2, int *ndf,
-               double *extra /* optional [8]: chi2_line, chi2_circle, k0, psi0, tanl0, ... */) {
+               double *extra /* optional [10]: chi2_line, chi2_circle, k0, psi0, tanl0, dk, arc, 0,
+                                cond(line normal matrix), cond(circle normal matrix) */) {
     if (n < 3 || n > OR_NMAX) return -1;
     /* 1) pre-fit: circle through hits 0, n/2, n-1 */
     int ia = 0, ib = n / 2, ic = n - 1;
@@ -528,8 +575,7 @@ int oracle_fit(int n, const double *hx, const double *hy, const double *hz, cons
         for (int a = 0; a < 3; a++)
             for (int b = 0; b < 3; b++) A[(i - 1 + a) * n + (i - 1 + b)] += g[a] * g[b] / vg[i];
     }
-    double Aorig[(OR_NMAX + 1) * (OR_NMAX + 1)];
-    memcpy(Aorig, A, sizeof A);
+    const double cond_line = extra ? oracle_sym_condition(n, A) : 0;
     double v[OR_NMAX];
     memcpy(v, rhs, sizeof(double) * n);
     cholesky_solve(n, A, v);
@@ -548,7 +594,6 @@ int oracle_fit(int n, const double *hx, const double *hy, const double *hz, cons
         Cv[0][c] = e[0];
         Cv[1][c] = e[1];
     }
-    (void)Aorig;
     /* 4) circle fit in the transverse plane: unknowns u_0..u_{n-1}, dk */
     int N = n + 1;
     double B[(OR_NMAX + 1) * (OR_NMAX + 1)], x[OR_NMAX + 1];
@@ -565,6 +610,7 @@ int oracle_fit(int n, const double *hx, const double *hy, const double *hz, cons
         for (int a = 0; a < 4; a++)
             for (int b = 0; b < 4; b++) B[idx[a] * N + idx[b]] += h[a] * h[b] / vb[i];
     }
+    const double cond_circle = extra ? oracle_sym_condition(N, B) : 0;
     cholesky_solve(N, B, x);
     double dk = x[n];
     double chi2c = 0;
@@ -649,6 +695,8 @@ int oracle_fit(int n, const double *hx, const double *hy, const double *hz, cons
         extra[5] = dk;
         extra[6] = arc;
         extra[7] = 0;
+        extra[8] = cond_line;
+        extra[9] = cond_circle;
     }
     return 0;
 }

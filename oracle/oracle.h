@@ -74,6 +74,10 @@ typedef struct {
 } or_result;
 
 int oracle_pred(int which, const float *hits /* [k][4] x,y,z,r */, int nh, float k);
+/* 2-norm condition number of a symmetric n x n matrix (row-major), cyclic
+ * Jacobi eigenvalues; -1 for a bad size. */
+double oracle_sym_condition(int n, const double *M);
+
 int oracle_fit(int n, const double *hx, const double *hy, const double *hz, const int *is_disk,
                const or_fitpar *fp, double *params, double *cov, double *chi2, int *ndf,
                double *extra);

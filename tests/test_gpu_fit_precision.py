@@ -54,11 +54,13 @@ def stress():
                     CU.FIT_PARAMS) for h in g64[0]]
     want = (np.array([w[0] for w in W]), np.array([w[1] for w in W]), np.array([w[2] for w in W]),
             np.array([w[3] for w in W]))
-    return g64, g32, want
+    # condition numbers of each track's normal matrices (line, circle)
+    cond = np.array([[w[4][8], w[4][9]] for w in W])
+    return g64, g32, want, cond
 
 
 def test_fp64_solve_matches_the_oracle_on_every_stress_track(stress):
-    g64, _, (WP, WC, WX, WN) = stress
+    g64, _, (WP, WC, WX, WN), _ = stress
     assert len(WP) > 10000
     err = compare_params(g64[1], g64[2], g64[3], g64[4], WP, WC, WX, WN)
     print("float64 solve vs oracle (max):", {k: float(np.max(v)) for k, v in err.items()})
@@ -81,7 +83,7 @@ def _outside(P, CV, X2, WP, WC, WX):
 
 
 def test_fp32_variant_is_characterised(stress):
-    _, g32, (WP, WC, WX, _) = stress
+    _, g32, (WP, WC, WX, _), _ = stress
     P, CV, X2 = g32[1], g32[2], g32[3]
     finite = np.isfinite(P).all(1) & np.isfinite(CV).all(1) & np.isfinite(X2)
     out = _outside(P, CV, X2, WP, WC, WX)
@@ -94,3 +96,21 @@ def test_fp32_variant_is_characterised(stress):
     # usable for most tracks but not for all (measured: 0.7% outside, a few
     # non-finite): the float64 solve is needed for the parity contract
     assert 0.0 < np.mean(out) < 0.02
+
+
+def test_fp32_breakdown_follows_the_condition_number(stress):
+    """Condition-number report per track: the all-float32 variant's
+    departures from the float64 tolerances, by the 2-norm condition number
+    of the worse of each track's two normal matrices (the oracle's)."""
+    _, g32, (WP, WC, WX, _), cond = stress
+    out = _outside(g32[1], g32[2], g32[3], WP, WC, WX)
+    c = cond.max(1)
+    print(f"condition number: p50 {np.percentile(c, 50):.2e} p90 {np.percentile(c, 90):.2e} "
+          f"p99 {np.percentile(c, 99):.2e} max {c.max():.2e}")
+    edges = [1.0, 1e4, 1e6, 1e8, 1e10, 1e12, np.inf]
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        sel = (c >= lo) & (c < hi)
+        if sel.any():
+            print(f"  cond [{lo:.0e}, {hi:.0e}): {sel.sum()} tracks, {out[sel].mean():.2e} outside")
+    low, high = c < np.percentile(c, 50), c >= np.percentile(c, 99)
+    assert out[high].mean() > 10 * out[low].mean()

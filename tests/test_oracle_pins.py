@@ -448,3 +448,27 @@ def test_fit_gradient_of_chi2_vanishes_on_exact_helices():
     P = _helix_points(1 / 60.0, 0.4, 0.8, 0.002, 1.0, [3.0, 7.0, 11.0, 15.5])
     Gr = oracle.fit_grad_fd(P[:, 0], P[:, 1], P[:, 2], [0, 0, 0, 0], CU.FIT_PARAMS, np.zeros(5), 1.0)
     assert np.abs(Gr).max() < 1e-3
+
+
+def test_condition_numbers_match_the_library_eigenvalues():
+    """The oracle's Jacobi condition number against numpy's singular values,
+    on symmetric positive definite matrices up to 9 x 9 spanning 1 to 1e12."""
+    rng = np.random.default_rng(3)
+    assert abs(oracle.sym_condition(np.diag([2.0, 8.0, 0.5])) - 16.0) < 1e-12
+    for n in range(2, 10):
+        for decades in (0, 4, 8, 12):
+            Q, _ = np.linalg.qr(rng.normal(size=(n, n)))
+            lam = np.logspace(0, decades, n)
+            M = (Q * lam) @ Q.T
+            M = 0.5 * (M + M.T)
+            want = np.linalg.cond(M)
+            got = oracle.sym_condition(M)
+            # the smallest eigenvalue carries an error of ~1e-16 lambda_max on
+            # either side: relative error up to ~1e-16 cond
+            assert abs(got - want) <= (1e-9 + 1e-13 * want) * want, (n, decades, got, want)
+
+
+def test_fit_reports_the_condition_of_its_normal_matrices():
+    P = _helix_points(1 / 200.0, 0.3, 0.5, 0.001, 1.0, [3.0, 6.9, 11.0, 15.5])
+    ex = oracle.fit(P[:, 0], P[:, 1], P[:, 2], [0, 0, 0, 0], CU.FIT_PARAMS)[4]
+    assert len(ex) == 10 and ex[8] >= 1.0 and ex[9] >= 1.0 and np.isfinite(ex[8:]).all()
