@@ -431,6 +431,30 @@ def measure_per_event(c, batch):
     return time.perf_counter() - t0
 
 
+# ------------------------------------------------------------ sharding
+def shard_first_event(rank: int, n_ev: int) -> int:
+    """First event of a rank's shard: ranks take consecutive, disjoint blocks
+    of n_ev events (events are independent, so ranks exchange no data)."""
+    return rank * n_ev
+
+
+def max_over_ranks(value: float, world: int, device="cpu") -> float:
+    """The largest value over the ranks (the slowest rank's time)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, ms: float) -> float:
+    """Units per second of the whole job: every rank's units over the
+    slowest rank's time."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 # ---------------------------------------------------------------- native
 def run_native(args, rank, world, local_rank):
     import numpy as np
@@ -440,7 +464,7 @@ def run_native(args, rank, world, local_rank):
 
     workers = max(1, min(16, (os.cpu_count() or 4) // max(1, world)))
     n_ev = args.events
-    batch = E.make_batch(3, n_events=n_ev, first=rank * n_ev, workers=workers)
+    batch = E.make_batch(3, n_events=n_ev, first=shard_first_event(rank, n_ev), workers=workers)
     import torch
     import torch.distributed as dist
     from paper_2008_13461_gb300 import _lib as L
@@ -502,11 +526,7 @@ def run_native(args, rank, world, local_rank):
     clk = clocks.stop() if clocks else None
     step_ms = [e[0].elapsed_time(e[4]) for e in evs]
     stage_ms = [statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i in range(4)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     ms_per_step = total_ms / args.steps
     ctx = Ctx(dev=dev, stream=stream, s=s, ws=ws, nb=nb, h=h, cfg=cfg, cells=cells, edges=edges, tuples=tuples,
               tracks=tracks, flush=flush, counts=counts, pipe=pipe, bufs=bufs, t=t)
@@ -558,8 +578,7 @@ def run_native(args, rank, world, local_rank):
                        "cpu": _cpu_model()}
         except Exception as exc:   # reported, never required
             cpu_all = f"unavailable: {exc}"
-    events_total = n_ev * world
-    value = events_total / (ms_per_step * 1e-3)
+    value = whole_job_rate(n_ev, world, ms_per_step)
     line = {
         "metric": METRIC,
         "value": value,
