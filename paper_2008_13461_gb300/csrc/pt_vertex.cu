@@ -471,13 +471,10 @@ pt_status launch_vertices(const pt_vertex_tracks &in, int32_t n_tracks, int32_t 
     a.rho = a.order + (n_tracks + 1);
     a.root = a.rho + (n_tracks + 1);
     a.out = out;
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_vtx_event, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVtxDynSmem) !=
-            cudaSuccess)
-            return PT_ERR_CUDA;
-        attr = true;
-    }
+    // per device and call (cheap; no shared state between threads or devices)
+    if (cudaFuncSetAttribute(k_vtx_event, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVtxDynSmem) !=
+        cudaSuccess)
+        return PT_ERR_CUDA;
     if (cudaMemsetAsync(w, 0, sizeof(int32_t) * 2 * ((size_t)n_events + 1), s) != cudaSuccess ||
         cudaMemsetAsync(out.status, 0, sizeof(int32_t), s) != cudaSuccess)
         return PT_ERR_CUDA;
