@@ -98,10 +98,10 @@ def test_results_do_not_depend_on_tuning(batch2, oracle2, tuning):
 
 def test_autotune_picks_a_tuning_with_unchanged_results(batch2, oracle2):
     from paper_2008_13461_gb300.autotune import autotune
-    pipe = make_pipeline(CU.cuts_for_config(2))
+    pipe = make_pipeline(CU.cuts_for_config(2), tuning=dict(n_t_bins=32, doublet_lanes=8, n_phi_bins=128))
     t = to_dev(batch2)
     args = (t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
-    space = (("n_t_bins", (8, 32)), ("doublet_lanes", (4, 8)), ("n_phi_bins", (64, 128)))
+    space = (("n_t_bins", (8, 32)), ("doublet_lanes", (4, 8)), ("n_phi_bins", (64, 128)))   # the base is inside
     best, timings = autotune(pipe, *args, reps=1, space=space)   # raises if a tuning changes a count
     assert len(timings) >= 4 and all(v > 0 for v in timings.values())
     assert best["n_t_bins"] in (8, 32) and best["doublet_lanes"] in (4, 8) and best["n_phi_bins"] in (64, 128)
