@@ -20,7 +20,10 @@
  *   pt_fit_tracks_grad its adjoint (gradient with respect to the hits),
  *   pt_align_hits[_grad] per-module alignment of the hits and its adjoint;
  *   pt_resolve_ambiguities  Sec. 3.5 (post-fit ambiguity resolution);
- *   pt_track_summary, pt_find_vertices  Sec. 3.6 (pixel vertices).
+ *   pt_track_summary, pt_find_vertices  Sec. 3.6 (pixel vertices);
+ *   pt_bin_hits_noalloc the binning step without a caller workspace;
+ *   pt_fma_probe       a measurement helper (arithmetic peaks), not part of
+ *                      the method.
  *
  * Conventions shared by every call
  * --------------------------------
