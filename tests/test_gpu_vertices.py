@@ -172,3 +172,21 @@ def test_vertices_do_not_depend_on_the_order_of_the_tracks():
     assert np.array_equal(g1["track_vertex"][perm], g2["track_vertex"])
     assert np.array_equal(g1["ntracks"], g2["ntracks"])
     assert np.allclose(g1["z"], g2["z"], rtol=1e-6, atol=1e-6)
+
+
+def test_an_event_beyond_the_track_limit_is_reported_and_skipped():
+    from paper_2008_13461_gb300 import _lib as L
+    n0 = L.PT_VTX_MAX_TRACKS + 600
+    rng = np.random.default_rng(12)
+    big = dict(ev=np.zeros(n0, np.int32), z0=rng.uniform(-10, 10, n0).astype(np.float32),
+               ez0=np.full(n0, 0.01, np.float32), pt=np.full(n0, 1.0, np.float32),
+               nhits=np.full(n0, 4, np.uint8), keep=np.ones(n0, np.uint8))
+    small = vertex_tracks(13, 1, pileup=5.0)
+    small["ev"] = np.ones_like(small["ev"])
+    d = {k: np.concatenate([big[k], small[k]]) for k in KEYS}
+    g = _gpu(d, 2)
+    assert int(g["status"][0]) & L.PT_VTX_EVENT_TOO_LARGE
+    assert int(g["n"][0]) == 0 and np.all(g["track_vertex"][:n0] == -1)
+    want, vidx = postfit.find_vertices(*(small[k] for k in KEYS), 2, CUTS)   # event 1 alone
+    assert int(g["n"][1]) == len(want[1]) > 0
+    assert np.array_equal(g["track_vertex"][n0:].astype(np.int64), vidx)
