@@ -356,6 +356,22 @@ def test_fit_rigid_limit_is_least_squares():
     res_circ = m - np.polyval([c2, c1, c0], sx)
     want = np.sum(res_line ** 2) / (20e-4) ** 2 + np.sum(res_circ ** 2) / (10e-4) ** 2
     assert abs(chi2 - want) < 1e-3 * want + 1e-6
+    # the line block of the covariance is the regression's: var(slope) =
+    # sigma^2 / Sxx, var(icpt) = sigma^2 (1/n + mean^2 / Sxx), cov = -sigma^2
+    # mean / Sxx, carried to z0 = icpt + slope * arc (arc to the perigee)
+    sig2, n = (20e-4) ** 2, len(sx)
+    sxx = np.sum((sx - sx.mean()) ** 2)
+    v_sl, v_ic, c_si = sig2 / sxx, sig2 * (1 / n + sx.mean() ** 2 / sxx), -sig2 * sx.mean() / sxx
+    # (the residual scattering, 1e-8 of nominal, adds ~5e-6 relative)
+    arc = ex[6]
+    assert abs(cov[5] - v_sl) < 2e-5 * v_sl                                   # (tan lambda, tan lambda)
+    assert abs(cov[12] - (c_si + arc * v_sl)) < 2e-5 * v_ic                    # (z0, tan lambda)
+    assert abs(cov[14] - (v_ic + 2 * arc * c_si + arc ** 2 * v_sl)) < 2e-5 * v_ic   # (z0, z0)
+    # and the curvature's variance is the parabola's: kappa = -(k0 + dk),
+    # dk = 2 c2, var(c2) from (X^T X)^-1 sigma_rphi^2 with X = [1, s, s^2]
+    Xp = np.stack([np.ones_like(sx), sx, sx * sx], 1)
+    v_c2 = np.linalg.inv(Xp.T @ Xp)[2, 2] * (10e-4) ** 2
+    assert abs(cov[0] - 4 * v_c2) < 2e-5 * 4 * v_c2                         # (kappa, kappa)
 
 
 def test_fit_three_hits_has_zero_circle_chi2():
