@@ -87,14 +87,15 @@ def find_vertices(ev, z0, ez0, pt, nhits, keep, n_events: int, cuts: dict | None
                track_vertex=torch.empty(max(1, k), dtype=torch.int32, device=dev),
                status=torch.zeros(1, dtype=torch.int32, device=dev))
     nbytes = L.vertex_scratch_size(k, E)
-    scratch = torch.empty((nbytes + 15) // 16, dtype=torch.int64, device=dev)
+    scratch = torch.empty(2 * ((nbytes + 15) // 16), dtype=torch.int64, device=dev)     # 16-byte units
+    assert scratch.numel() * scratch.element_size() >= nbytes
     trk = L.VertexTracks(ev.data_ptr(), z0.data_ptr(), ez0.data_ptr(), pt.data_ptr(), nhits.data_ptr(),
                          _ptr(keep))
     vc = L.VertexCuts(c["pt_min"], c["ez0_max"], c["dz_cut"], c["chi2_max"], c["split_chi2"], int(c["min_hits"]),
                       int(c["min_tracks"]))
     vo = L.Vertices(*(out[n].data_ptr() for n in ("n", "z", "ez", "chi2", "sumpt2", "ndf", "ntracks",
                                                     "track_vertex", "status")))
-    L.find_vertices(trk, k, E, vc, M, scratch.data_ptr(), scratch.numel() * 16, vo, s)
+    L.find_vertices(trk, k, E, vc, M, scratch.data_ptr(), scratch.numel() * scratch.element_size(), vo, s)
     out["scratch"] = scratch                                   # kept alive until the stream has used it
     res = {n: (t[:E * M].view(E, M) if n in ("z", "ez", "chi2", "sumpt2", "ndf", "ntracks") else t)
            for n, t in out.items()}
