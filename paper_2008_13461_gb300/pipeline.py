@@ -96,6 +96,8 @@ def find_vertices(ev, z0, ez0, pt, nhits, keep, n_events: int, cuts: dict | None
     vo = L.Vertices(*(out[n].data_ptr() for n in ("n", "z", "ez", "chi2", "sumpt2", "ndf", "ntracks",
                                                     "track_vertex", "status")))
     L.find_vertices(trk, k, E, vc, M, scratch.data_ptr(), scratch.numel() * scratch.element_size(), vo, s)
+    if stream is not None:
+        scratch.record_stream(stream)
     out["scratch"] = scratch                                   # kept alive until the stream has used it
     res = {n: (t[:E * M].view(E, M) if n in ("z", "ez", "chi2", "sumpt2", "ndf", "ntracks") else t)
            for n, t in out.items()}
@@ -244,6 +246,8 @@ class Pipeline:
         _, _, tuples, _ = bufs.structs()
         L.resolve_ambiguities(tuples, bufs.trk_tuple.data_ptr(), k, bufs.trk_chi2.data_ptr(),
                               bufs.trk_params.data_ptr() + 3 * 4, 5, nc, n_hits, scratch.data_ptr(), keep.data_ptr(), s)
+        if stream is not None:
+            scratch.record_stream(stream)      # freed here, used by `stream`: keep it until the work is done
         return keep[:k]
 
     def track_summary(self, bufs: Buffers, counts: L.Counts, x, y, z, r, module, ev_off,
