@@ -295,7 +295,7 @@ class Pipeline:
             bufs = self.allocate(x.numel(), ev_off.numel() - 1, cap)
         raise L.PtError(L.PT_ERR_CAPACITY, "pipeline: capacity still exceeded after retries")
 
-    def run_per_event(self, x, y, z, r, module, ev_off_host, bufs_list=None):
+    def run_per_event(self, x, y, z, r, module, ev_off_host):
         """The plain per-event form: the same kernels on one event at a time,
         with a host read of the counts after each stage."""
         out = []
