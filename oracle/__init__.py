@@ -160,12 +160,14 @@ def sym_condition(M) -> float:
     return float(lib().oracle_sym_condition(M.shape[0], _ptr(M, C.c_double)))
 
 
-def fit_grad_fd(hx, hy, hz, is_disk, fitpar: dict, gparams, gchi2: float = 0.0, h: float = 2e-5) -> np.ndarray:
+def fit_grad_fd(hx, hy, hz, is_disk, fitpar: dict, gparams, gchi2: float = 0.0, h: float = 2e-5,
+                ms_scale: float = 1.0) -> np.ndarray:
     """Gradient of  gparams . params + gchi2 * chi2  of the broken-line fit
     (Sec. 3.4) with respect to the hit coordinates, float[3, n] (x, y, z rows):
     the derivative's plain definition evaluated numerically, by Richardson
     extrapolation of central differences of the float64 fit with steps h and
-    h/2 cm (error O(h^4); phi0 differences taken modulo 2 pi)."""
+    h/2 cm (error O(h^4); phi0 differences taken modulo 2 pi).  `ms_scale`
+    scales the scattering variance as in fit()."""
     base = [np.array(a, dtype=np.float64) for a in (hx, hy, hz)]
     gp = np.asarray(gparams, dtype=np.float64)
     n = len(base[0])
@@ -175,8 +177,8 @@ def fit_grad_fd(hx, hy, hz, is_disk, fitpar: dict, gparams, gchi2: float = 0.0, 
         dn = [b.copy() for b in base]
         up[a][i] += step
         dn[a][i] -= step
-        pu, _, cu, _, _ = fit(up[0], up[1], up[2], is_disk, fitpar)
-        pd, _, cd, _, _ = fit(dn[0], dn[1], dn[2], is_disk, fitpar)
+        pu, _, cu, _, _ = fit(up[0], up[1], up[2], is_disk, fitpar, ms_scale)
+        pd, _, cd, _, _ = fit(dn[0], dn[1], dn[2], is_disk, fitpar, ms_scale)
         d = pu - pd
         d[1] = (d[1] + np.pi) % (2 * np.pi) - np.pi
         return (float(np.dot(gp, d)) + gchi2 * (cu - cd)) / (2 * step)

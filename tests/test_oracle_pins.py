@@ -458,6 +458,46 @@ def test_fit_gradient_sum_rules():
             assert abs(rot - (1.0 if o == 1 else 0.0)) < 1e-7 * scale, (n, o, rot)
 
 
+def test_fit_gradient_rigid_limit_is_the_regression_hat_matrix():
+    """With scattering almost off, the s-z line fit of barrel hits is the
+    straight-line regression of z on the arc lengths s (which depend on x and
+    y only), so its z-gradients have closed forms: d tanl/dz_i = (s_i - m)/Sxx,
+    d icpt/dz_i = 1/n - m (s_i - m)/Sxx, z0 = icpt + tanl * arc, and
+    d chi2/dz_i = 2 r_i / sigma_z^2 with r_i the regression residual (the
+    minimum's own gradient, parameters held).  Every hit's entry is checked,
+    so a wrong index, sign or dropped term in the oracle's gradient fails.
+    The step is 2e-3 cm: the fit is linear in z except through the first and
+    last hits' pre-fit dip, which sets the (tiny) scattering variances, and
+    with them 1e12-sized entries of the normal matrix whose rounding a
+    2e-5 cm difference would amplify at those two hits."""
+    rng = np.random.default_rng(5)
+    s = np.array([3.0, 6.9, 11.0, 15.5, 19.0])
+    P = _helix_points(-1 / 80.0, -0.9, -0.6, 0.0, 2.0, s)
+    P[:, 2] += rng.normal(0, 20e-4, 5)
+    nrm = np.stack([-np.sin(-0.9 + 0 * s), np.cos(-0.9 + 0 * s)], 1)
+    P[:, :2] += rng.normal(0, 10e-4, (5, 1)) * nrm
+    _, _, _, _, ex = oracle.fit(P[:, 0], P[:, 1], P[:, 2], [0] * 5, CU.FIT_PARAMS, ms_scale=1e-8)
+    k0 = ex[2]
+    d = P[:, :2] - P[0, :2]
+    dist = np.hypot(d[:, 0], d[:, 1])
+    sx = np.where(dist > 0, 2 * np.arcsin(np.clip(k0 * dist / 2, -1, 1)) / np.where(k0 != 0, k0, 1), 0)
+    n, m = len(sx), sx.mean()
+    sxx = np.sum((sx - m) ** 2)
+    d_slope = (sx - m) / sxx
+    d_icpt = 1.0 / n - m * d_slope
+    slope, icpt = np.polyfit(sx, P[:, 2], 1)
+    resid = P[:, 2] - (slope * sx + icpt)
+    arc = ex[6]
+    want = {2: d_slope, 4: d_icpt + arc * d_slope, "chi2": 2 * resid / (20e-4) ** 2}
+    for o, w in want.items():
+        gp = np.zeros(5)
+        if o != "chi2":
+            gp[o] = 1.0
+        Gr = oracle.fit_grad_fd(P[:, 0], P[:, 1], P[:, 2], [0] * 5, CU.FIT_PARAMS, gp,
+                                1.0 if o == "chi2" else 0.0, h=2e-3, ms_scale=1e-8)
+        assert np.abs(Gr[2] - w).max() < 1e-4 * np.abs(w).max(), (o, Gr[2], w)
+
+
 def test_fit_gradient_of_chi2_vanishes_on_exact_helices():
     """chi2 is zero, its minimum, on the hits of an exact helix, so its
     gradient with respect to the hits vanishes there."""
