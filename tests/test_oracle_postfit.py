@@ -90,6 +90,10 @@ def test_vertices_two_separated_clusters_and_noise():
     assert abs(V[0]["z"] - np.mean(np.float32([1.000, 1.004, 0.998, 1.002]).astype(np.float64))) < 1e-12
     assert abs(V[0]["ez"] - 1 / np.sqrt(4 * w)) < 1e-12
     assert V[0]["sumpt2"] == 16.0 and V[1]["sumpt2"] == 3.0
+    # chi2 = sum of squared pulls about the mean, ndf = n - 1, by hand
+    zb = np.float32([-3.0, -3.006, -2.995]).astype(np.float64)
+    assert abs(V[1]["chi2"] - w * np.sum((zb - zb.mean()) ** 2)) < 1e-9 * V[1]["chi2"]
+    assert V[0]["ndf"] == 3 and V[1]["ndf"] == 2
     assert vi.tolist() == [0, 0, 0, 0, 1, 1, 1, -1, -1, -1, -1, -1]
 
 
