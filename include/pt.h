@@ -33,7 +33,11 @@
  *  - `ws` is a caller-allocated device workspace of at least
  *    pt_workspace_size() bytes, 256-byte aligned.  It carries state from one
  *    call to the next: the four calls must receive the same ws, hits and
- *    config, in order.
+ *    config, in order.  Each output array's pointer is checked (non-NULL
+ *    while its capacity is positive) by the call that writes it; later calls
+ *    that read it (cells in pt_connect_cells and pt_find_ntuplets, edges in
+ *    pt_find_ntuplets, tuples in pt_fit_tracks) take the structs as the
+ *    earlier calls received them and do not check them again.
  *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
  *    default stream) and never synchronise, so a sequence of calls can be
  *    captured in a CUDA graph.  Argument errors are returned synchronously;
