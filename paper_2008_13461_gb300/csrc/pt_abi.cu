@@ -360,12 +360,12 @@ pt_status pt_resolve_ambiguities(const pt_tuples *tuples, const int32_t *track_t
                                  int32_t n_hits, uint32_t *scratch, uint8_t *keep, void *stream) {
     if (n_tracks < 0 || n_cells < 0 || n_hits < 0 || tip_stride < 1) return PT_ERR_INVALID_ARG;
     if (n_tracks == 0) return PT_OK;
+    const int64_t n_scratch = (int64_t)n_cells + n_hits;      // both up to 2^31 - 1: sum in 64 bits
     if (!tuples || !tuples->hits || !tuples->cells || !tuples->n || !track_tuple || !chi2 || !tip || !keep ||
-        (!scratch && n_cells + n_hits > 0))
+        (!scratch && n_scratch > 0))
         return PT_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    if (n_cells + n_hits > 0 &&
-        cudaMemsetAsync(scratch, 0xff, sizeof(uint32_t) * ((size_t)n_cells + (size_t)n_hits), s) != cudaSuccess)
+    if (n_scratch > 0 && cudaMemsetAsync(scratch, 0xff, sizeof(uint32_t) * (size_t)n_scratch, s) != cudaSuccess)
         return PT_ERR_CUDA;
     launch_ambiguities(tuples->hits, tuples->cells, tuples->n, track_tuple, n_tracks, chi2, tip, tip_stride, n_cells,
                        n_hits, scratch, keep, align_grid(n_tracks), s);
