@@ -393,24 +393,35 @@ def measure_differentiable(c, args):
             "note": "gradient of a loss of all track parameters and chi2 with respect to every hit"}
 
 
-def measure_per_event(c, batch):
+def grow_capacity(cap: dict, need: dict) -> dict:
+    """Capacities after an overflow: the sizes needed plus a quarter and a
+    margin, never smaller than before."""
+    return {k: max(cap[k], int(need[k] * 1.25) + 1024) for k in cap}
+
+
+def measure_per_event(c, batch, max_retries: int = 4):
     """Seconds for the plain per-event GPU form over the batch: the same
     kernels one event at a time, with a host read of the counts after every
-    stage."""
+    stage.  The per-event buffers start at 1/8 of the batch's capacities and
+    grow until every event of the batch fits (an untimed pass, which also
+    warms up); the timed pass then runs on them."""
     import numpy as np
     import torch
     from paper_2008_13461_gb300 import _lib as L
     ev_host = batch["ev_off"]
     sizes = np.diff(ev_host)
-    cap = {k: max(v // 8, 1 << 20) for k, v in c.bufs.capacity.items()}
-    ebufs = c.pipe.allocate(int(sizes.max()), 1, cap)
-    ecfg = c.pipe._cfg(ebufs.capacity)
-    ec, ee, et, ek = ebufs.structs()
-    ews, enb = ebufs.ws.data_ptr(), ebufs.ws.numel()
     offs = [torch.tensor([0, int(n)], dtype=torch.int32, device=c.dev) for n in sizes]
     t, s = c.t, c.s
 
-    def one_pass():
+    def setup(cap):
+        ebufs = c.pipe.allocate(int(sizes.max()), 1, cap)
+        return ebufs, c.pipe._cfg(ebufs.capacity), ebufs.structs()
+
+    def one_pass(env):
+        """Every event through the four calls; (all fitted, sizes needed)."""
+        ebufs, ecfg, (ec, ee, et, ek) = env
+        ews, enb = ebufs.ws.data_ptr(), ebufs.ws.numel()
+        ok, need = True, dict.fromkeys(("cells", "edges", "tuples", "tracks"), 0)
         for e in range(len(sizes)):
             a, b = int(ev_host[e]), int(ev_host[e + 1])
             eh = c.pipe._hits(t["x"][a:b], t["y"][a:b], t["z"][a:b], t["r"][a:b], t["module"][a:b], offs[e])
@@ -421,14 +432,31 @@ def measure_per_event(c, batch):
             L.find_ntuplets(ews, enb, eh, ecfg, ec, ee, et, s)
             L.read_counts(ews, enb, eh, ecfg, s)
             L.fit_tracks(ews, enb, eh, ecfg, et, ek, s)
-            stc, _ = L.read_counts(ews, enb, eh, ecfg, s)
-            assert stc == L.PT_OK
+            stc, n = L.read_counts(ews, enb, eh, ecfg, s)     # the flags of all four calls of this event
+            if stc == L.PT_ERR_CAPACITY:
+                ok = False
+            elif stc != L.PT_OK:
+                raise L.PtError(stc, f"per-event form, event {e}")
+            for k, v in (("cells", n.n_cells), ("edges", n.n_edges), ("tuples", n.n_tuples),
+                         ("tracks", n.n_tracks)):
+                need[k] = max(need[k], int(v))
+        return ok, need
 
-    one_pass()
+    cap = {k: max(v // 8, 1 << 20) for k, v in c.bufs.capacity.items()}
+    env = setup(cap)
+    for _ in range(max_retries + 1):
+        ok, need = one_pass(env)
+        if ok:
+            break
+        cap = grow_capacity(cap, need)
+        env = setup(cap)
+    else:
+        raise L.PtError(L.PT_ERR_CAPACITY, "per-event form: capacity still exceeded after retries")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    one_pass()
+    ok, _ = one_pass(env)
     torch.cuda.synchronize()
+    assert ok, "per-event form: an event overflowed buffers it fitted before"
     return time.perf_counter() - t0
 
 

@@ -24,3 +24,90 @@ def test_algorithmic_bytes_per_stage():
     assert ab["fishbone"] == 9 * 1000
     assert ab["connect"] == 13 * 1000 + 8 * 50
     assert ab["fit"] == 36 * 10 + 12 * 3.5 * 10 + 88 * 10
+
+
+class _FakeBufs:
+    def __init__(self, capacity):
+        import torch
+        self.capacity = dict(capacity)
+        self.ws = torch.zeros(16, dtype=torch.uint8)
+
+    def structs(self):
+        return ("cells", "edges", "tuples", "tracks")
+
+
+class _FakePipe:
+    """allocate / _cfg / _hits of the pipeline, recording the capacities."""
+
+    def __init__(self):
+        self.allocated = []
+
+    def allocate(self, n_hits, n_events, cap):
+        self.allocated.append(dict(cap))
+        return _FakeBufs(cap)
+
+    def _cfg(self, cap):
+        return dict(cap)
+
+    def _hits(self, x, *rest):
+        return int(x.numel())
+
+
+def _per_event_setup(monkeypatch, ev_off, per_hit, fail_status=None):
+    """A fake library whose events need `per_hit` x hits of every capacity
+    and report PT_ERR_CAPACITY when a buffer is smaller."""
+    import numpy as np
+    import torch
+    from paper_2008_13461_gb300 import _lib as L
+    calls = []
+    for name in ("build_doublets", "connect_cells", "find_ntuplets", "fit_tracks"):
+        monkeypatch.setattr(L, name, lambda *a, _n=name: calls.append(_n))
+
+    def read_counts(ws, nb, n_hits, cfg, s):
+        c = L.Counts()
+        c.n_cells, c.n_edges, c.n_tuples, c.n_tracks = (per_hit * n_hits,) * 4
+        if fail_status is not None:
+            return fail_status, c
+        over = any(per_hit * n_hits > cfg[k] for k in ("cells", "edges", "tuples", "tracks"))
+        return (L.PT_ERR_CAPACITY if over else L.PT_OK), c
+
+    monkeypatch.setattr(L, "read_counts", read_counts)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    n = int(ev_off[-1])
+    t = {k: torch.zeros(n) for k in ("x", "y", "z", "r", "module")}
+    pipe = _FakePipe()
+    ctx = bench.Ctx(dev="cpu", t=t, s=0, pipe=pipe,
+                    bufs=_FakeBufs({k: per_hit * n for k in ("cells", "edges", "tuples", "tracks")}))
+    return ctx, {"ev_off": np.asarray(ev_off)}, pipe, calls
+
+
+def test_per_event_form_grows_its_buffers_until_every_event_fits(monkeypatch):
+    # a batch of 3 events, the middle one large: 1/8 of the batch's
+    # capacities (and the 2^20 floor) is too small for it
+    ctx, batch, pipe, calls = _per_event_setup(monkeypatch, [0, 100, 5000, 5100], per_hit=1000)
+    sec = bench.measure_per_event(ctx, batch)
+    assert sec >= 0.0
+    assert pipe.allocated[0]["cells"] == max(1000 * 5100 // 8, 1 << 20)
+    final = pipe.allocated[-1]
+    assert all(v >= 1000 * 4900 for v in final.values())          # the largest event fits
+    assert len(pipe.allocated) == 2                                 # one growth step sufficed
+    assert calls[:4] == ["build_doublets", "connect_cells", "find_ntuplets", "fit_tracks"]
+
+
+def test_per_event_form_keeps_buffers_that_fit(monkeypatch):
+    ctx, batch, pipe, _ = _per_event_setup(monkeypatch, [0, 100, 200], per_hit=10)
+    bench.measure_per_event(ctx, batch)
+    assert len(pipe.allocated) == 1
+
+
+def test_per_event_form_raises_on_other_errors(monkeypatch):
+    import pytest
+    from paper_2008_13461_gb300 import _lib as L
+    ctx, batch, _, _ = _per_event_setup(monkeypatch, [0, 100], per_hit=10, fail_status=L.PT_ERR_INPUT)
+    with pytest.raises(L.PtError):
+        bench.measure_per_event(ctx, batch)
+
+
+def test_grow_capacity_never_shrinks():
+    cap = {"cells": 100, "edges": 5000}
+    assert bench.grow_capacity(cap, {"cells": 1000, "edges": 10}) == {"cells": 2274, "edges": 5000}
