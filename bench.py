@@ -62,7 +62,7 @@ def _time_oracle(sample, repeats):
     times = []
     for _ in range(repeats):
         t = time.perf_counter()
-        oracle.run(sample, CU.cuts_for_config(3), CU.FIT_PARAMS, G.module_layer_table(), [0] * 4 + [1] * 6)
+        oracle.run(sample, CU.cuts_for("pu200-batch64"), CU.FIT_PARAMS, G.module_layer_table(), [0] * 4 + [1] * 6)
         times.append(time.perf_counter() - t)
     return times
 
@@ -73,7 +73,7 @@ def _oracle_sector_worker(sample):
     from synth import cuts as CU
     from synth import geometry as G
     t = time.perf_counter()
-    oracle.run(sample, CU.cuts_for_config(3), CU.FIT_PARAMS, G.module_layer_table(), [0] * 4 + [1] * 6)
+    oracle.run(sample, CU.cuts_for("pu200-batch64"), CU.FIT_PARAMS, G.module_layer_table(), [0] * 4 + [1] * 6)
     return time.perf_counter() - t
 
 
@@ -493,7 +493,7 @@ def run_native(args, rank, world, local_rank):
 
     workers = max(1, min(16, (os.cpu_count() or 4) // max(1, world)))
     n_ev = args.events
-    batch = E.make_batch(3, n_events=n_ev, first=shard_first_event(rank, n_ev), workers=workers)
+    batch = E.make_batch("pu200-batch64", n_events=n_ev, first=shard_first_event(rank, n_ev), workers=workers)
     import torch
     import torch.distributed as dist
     from paper_2008_13461_gb300 import _lib as L
@@ -501,7 +501,7 @@ def run_native(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    pipe = Pipeline(G.layers(), G.module_layer_table(), CU.cuts_for_config(3), CU.FIT_PARAMS, device=dev)
+    pipe = Pipeline(G.layers(), G.module_layer_table(), CU.cuts_for("pu200-batch64"), CU.FIT_PARAMS, device=dev)
     t = {k: torch.as_tensor(batch[k]).to(dev) for k in ("x", "y", "z", "r", "module", "ev_off")}
     args6 = (t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
     tune = "defaults"
@@ -656,7 +656,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     from synth import events as E
-    batch = E.make_batch(3, n_events=1)
+    batch = E.make_batch("pu200-batch64", n_events=1)
     sample = _oracle_sample(batch)
     times = _time_oracle(sample, repeats=args.warmup + args.steps)[args.warmup:]
     value = args.steps / (SECTOR * sum(times))

@@ -90,12 +90,18 @@ def make_cuts(pt_min: float = 0.5, barrel_only: bool = False, min_hits: int = 3,
                 min_hits=int(min_hits), pt_min=float(pt_min))
 
 
-def cuts_for_config(k: int) -> dict:
-    if k == 1:
+def cuts_for(workload: str) -> dict:
+    """The cut set of a synthetic workload (by its name): the noiseless
+    barrel helices above 1 GeV take barrel pairs and a 0.9 GeV threshold,
+    the stress workload with tracks down to 0.3 GeV a 0.3 GeV threshold, the
+    pileup workloads 0.5 GeV."""
+    if workload == "barrel-50-helices":
         return make_cuts(pt_min=0.9, barrel_only=True)
-    if k == 5:
+    if workload == "pu200-stress-batch256":
         return make_cuts(pt_min=0.3)
-    return make_cuts(pt_min=0.5)
+    if workload in ("pu50-ttbar-like", "pu200-batch64", "pu50-batch32"):
+        return make_cuts(pt_min=0.5)
+    raise KeyError(f"no cut set for workload {workload!r}")
 
 
 # Fit constants (measurement errors and material, matching the simulation).

@@ -48,7 +48,7 @@ def rho_of_pt(pt_gev, bz=BZ_TESLA):
 @dataclasses.dataclass(frozen=True)
 class EventConfig:
     name: str
-    index: int                      # configuration number k for seeding
+    index: int                      # seeds the workload's events
     n_events: int
     pileup: float                   # mean number of pileup vertices
     pileup_poisson: bool
@@ -68,17 +68,18 @@ class EventConfig:
     ms_skip_first: bool = False     # no scattering at a track's first hit
 
 
-CONFIGS = {
-    1: EventConfig("barrel-50-helices", 1, 1, 0, False, pt_min=1.0, pt_max=10.0,
-                   pt_spectrum="loguniform", eta_max=2.0, barrel_only=True,
-                   overlaps=False, multiple_scattering=False, vertex_at_origin=True,
-                   fixed_tracks=50),
-    2: EventConfig("pu50-ttbar-like", 2, 1, 50, False, hard_tracks=60.0, noise_frac=0.02),
-    3: EventConfig("pu200-batch64", 3, 64, 200, True, hard_tracks=60.0, noise_frac=0.02),
-    4: EventConfig("pu50-batch32", 4, 32, 50, False, hard_tracks=60.0, noise_frac=0.02),
-    5: EventConfig("pu200-stress-batch256", 5, 256, 200, True, hard_tracks=60.0,
-                   pt_min=0.3, noise_frac=0.05, ineff=0.10),
-}
+# the synthetic workloads by name; each index only seeds its events
+WORKLOADS = {c.name: c for c in (
+    EventConfig("barrel-50-helices", 1, 1, 0, False, pt_min=1.0, pt_max=10.0,
+                pt_spectrum="loguniform", eta_max=2.0, barrel_only=True,
+                overlaps=False, multiple_scattering=False, vertex_at_origin=True,
+                fixed_tracks=50),
+    EventConfig("pu50-ttbar-like", 2, 1, 50, False, hard_tracks=60.0, noise_frac=0.02),
+    EventConfig("pu200-batch64", 3, 64, 200, True, hard_tracks=60.0, noise_frac=0.02),
+    EventConfig("pu50-batch32", 4, 32, 50, False, hard_tracks=60.0, noise_frac=0.02),
+    EventConfig("pu200-stress-batch256", 5, 256, 200, True, hard_tracks=60.0,
+                pt_min=0.3, noise_frac=0.05, ineff=0.10),
+)}
 
 
 def snap(v):
@@ -397,16 +398,17 @@ def _make_event_args(args):
     return make_event(*args)
 
 
-def make_batch(cfg: EventConfig | int, n_events: int | None = None, first: int = 0,
+def make_batch(cfg: EventConfig | str, n_events: int | None = None, first: int = 0,
                workers: int = 0) -> dict:
     """Concatenate events first .. first+n_events-1 into one SoA batch.
 
     Returns x, y, z, r (float32), module (int32), ev_off (int32[N+1]) plus
     truth: layer, track (index into the batch-wide track arrays, -1 noise),
     trk_* arrays.  workers > 1 generates events in a spawn-started process
-    pool (safe before or after CUDA initialisation in the caller)."""
-    if isinstance(cfg, int):
-        cfg = CONFIGS[cfg]
+    pool (safe before or after CUDA initialisation in the caller).  `cfg`
+    is a workload or its name (a key of WORKLOADS)."""
+    if isinstance(cfg, str):
+        cfg = WORKLOADS[cfg]
     n = cfg.n_events if n_events is None else n_events
     if workers > 1 and n > 1:
         import concurrent.futures as cf

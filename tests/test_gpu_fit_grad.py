@@ -1,6 +1,6 @@
 """Gradients of the broken-line fit (the adjoint kernel, Sec. 3.4
-differentiated) and of the per-module hit alignment, on PU50 events
-(configuration 4): against the oracle's float64 gradient, exact sum rules,
+differentiated) and of the per-module hit alignment, on two events of the
+pileup-50 workload: against the oracle's float64 gradient, exact sum rules,
 and finite differences of the GPU fit itself."""
 import numpy as np
 import pytest
@@ -19,8 +19,8 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def run4():
     from paper_2008_13461_gb300.autograd import DifferentiableFit
-    b = E.make_batch(4, n_events=2)
-    cuts = CU.cuts_for_config(4)
+    b = E.make_batch("pu50-batch32", n_events=2)
+    cuts = CU.cuts_for("pu50-batch32")
     pipe = make_pipeline(cuts)
     t = to_dev(b)
     res, bufs = pipe.run(t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])

@@ -40,8 +40,8 @@ def _gpu_tracks(b, cuts, fp32):
 
 @pytest.fixture(scope="module")
 def stress():
-    b = E.make_batch(5, n_events=1)
-    cuts = CU.cuts_for_config(5)
+    b = E.make_batch("pu200-stress-batch256", n_events=1)
+    cuts = CU.cuts_for("pu200-stress-batch256")
     g64 = _gpu_tracks(b, cuts, 0)
     g32 = _gpu_tracks(b, cuts, 1)
     # the same tracks (their order follows atomics): put g32 in g64's order

@@ -23,17 +23,17 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture(scope="module")
 def batch2():
-    return E.make_batch(2)
+    return E.make_batch("pu50-ttbar-like")
 
 
 @pytest.fixture(scope="module")
 def oracle2(batch2):
-    return oracle_run(batch2, CU.cuts_for_config(2))
+    return oracle_run(batch2, CU.cuts_for("pu50-ttbar-like"))
 
 
 def test_config1_noiseless_barrel():
-    b = E.make_batch(1)
-    cuts = CU.cuts_for_config(1)
+    b = E.make_batch("barrel-50-helices")
+    cuts = CU.cuts_for("barrel-50-helices")
     res = gpu_run(b, cuts)
     want = oracle_run(b, cuts)
     compare_sets(res, want)
@@ -42,11 +42,11 @@ def test_config1_noiseless_barrel():
 
 
 def test_config2_pu50(batch2, oracle2):
-    res = gpu_run(batch2, CU.cuts_for_config(2))
+    res = gpu_run(batch2, CU.cuts_for("pu50-ttbar-like"))
     nc, ne, nt = compare_sets(res, oracle2)
     err = compare_tracks(res, oracle2)
     assert nc > 50000 and nt > 1000
-    print("config 2 fit error (max, p99):", err)
+    print("pu50-ttbar-like fit error (max, p99):", err)
 
 
 def _concat(events):
@@ -65,12 +65,12 @@ def _slice(b, e):
 
 
 def test_ragged_batch_with_empty_and_tiny_events():
-    b4 = E.make_batch(4, n_events=3)
+    b4 = E.make_batch("pu50-batch32", n_events=3)
     evs = [_slice(b4, 0), _slice(b4, 1), _slice(b4, 2)]
     empty = {k: v[:0] for k, v in evs[0].items()}
     one = {k: v[:1] for k, v in evs[1].items()}
     batch = _concat([empty, evs[0], one, evs[1], empty, empty, evs[2], one])
-    cuts = CU.cuts_for_config(4)
+    cuts = CU.cuts_for("pu50-batch32")
     res = gpu_run(batch, cuts)
     want = oracle_run(batch, cuts)
     compare_sets(res, want)
@@ -81,7 +81,7 @@ def test_all_empty_batch():
     batch = {k: np.zeros(0, dtype=np.float32) for k in ("x", "y", "z", "r")}
     batch["module"] = np.zeros(0, dtype=np.int32)
     batch["ev_off"] = np.zeros(3, dtype=np.int32)
-    res = gpu_run(batch, CU.cuts_for_config(2))
+    res = gpu_run(batch, CU.cuts_for("pu50-ttbar-like"))
     assert res.counts.n_cells == 0 and res.counts.n_tracks == 0
 
 
@@ -91,14 +91,14 @@ def test_all_empty_batch():
     dict(n_phi_bins=64, n_t_bins=8, doublet_lanes=16, connect_lanes=16, blocks_per_sm=16),
 ])
 def test_results_do_not_depend_on_tuning(batch2, oracle2, tuning):
-    res = gpu_run(batch2, CU.cuts_for_config(2), tuning=tuning)
+    res = gpu_run(batch2, CU.cuts_for("pu50-ttbar-like"), tuning=tuning)
     compare_sets(res, oracle2)
     compare_tracks(res, oracle2)
 
 
 def test_autotune_picks_a_tuning_with_unchanged_results(batch2, oracle2):
     from paper_2008_13461_gb300.autotune import autotune
-    pipe = make_pipeline(CU.cuts_for_config(2), tuning=dict(n_t_bins=32, doublet_lanes=8, n_phi_bins=128))
+    pipe = make_pipeline(CU.cuts_for("pu50-ttbar-like"), tuning=dict(n_t_bins=32, doublet_lanes=8, n_phi_bins=128))
     t = to_dev(batch2)
     args = (t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
     space = (("n_t_bins", (8, 32)), ("doublet_lanes", (4, 8)), ("n_phi_bins", (64, 128)))   # the base is inside
@@ -112,7 +112,7 @@ def test_autotune_picks_a_tuning_with_unchanged_results(batch2, oracle2):
 
 def test_capacity_overflow_is_reported_then_retried(batch2, oracle2):
     from paper_2008_13461_gb300 import _lib as L
-    cuts = CU.cuts_for_config(2)
+    cuts = CU.cuts_for("pu50-ttbar-like")
     pipe = make_pipeline(cuts)
     t = to_dev(batch2)
     args = (t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
@@ -128,7 +128,7 @@ def test_capacity_overflow_is_reported_then_retried(batch2, oracle2):
 
 def test_input_contract_violations_are_flagged(batch2):
     from paper_2008_13461_gb300 import _lib as L
-    cuts = CU.cuts_for_config(2)
+    cuts = CU.cuts_for("pu50-ttbar-like")
     pipe = make_pipeline(cuts)
     for what in ("offgrid", "module", "envelope"):
         b = {k: np.array(v, copy=True) for k, v in batch2.items() if k in ("x", "y", "z", "r", "module", "ev_off")}
@@ -148,7 +148,7 @@ def test_input_contract_violations_are_flagged(batch2):
 
 def test_invalid_arguments_are_rejected_on_the_host(batch2):
     from paper_2008_13461_gb300 import _lib as L
-    cuts = CU.cuts_for_config(2)
+    cuts = CU.cuts_for("pu50-ttbar-like")
     pipe = make_pipeline(cuts)
     t = to_dev(batch2)
     bufs = pipe.allocate(t["x"].numel(), 1)
@@ -177,8 +177,8 @@ def test_invalid_arguments_are_rejected_on_the_host(batch2):
 # ------------------------------------------------------ full PU200 batch
 @pytest.fixture(scope="module")
 def pu200():
-    b = E.make_batch(3)
-    cuts = CU.cuts_for_config(3)
+    b = E.make_batch("pu200-batch64")
+    cuts = CU.cuts_for("pu200-batch64")
     res = gpu_run(b, cuts)
     return b, cuts, res
 

@@ -30,8 +30,8 @@ def _gpu_ambiguities(hits8, cells8, n, track_tuple, chi2, tip, n_cells, n_hits):
 
 
 def test_ambiguity_resolution_matches_the_oracle():
-    b = E.make_batch(2)
-    want = oracle_run(b, CU.cuts_for_config(2))
+    b = E.make_batch("pu50-ttbar-like")
+    want = oracle_run(b, CU.cuts_for("pu50-ttbar-like"))
     T = len(want["tuple_n"])
     cells8 = np.full((T, 8), -1, np.int32)
     cells8[:, :want["tuple_cells"].shape[1]] = want["tuple_cells"]
@@ -46,8 +46,8 @@ def test_ambiguity_resolution_matches_the_oracle():
 
 
 def test_ambiguity_resolution_of_the_pipeline_tracks_obeys_the_rule():
-    b = E.make_batch(2)
-    res = gpu_run(b, CU.cuts_for_config(2))
+    b = E.make_batch("pu50-ttbar-like")
+    res = gpu_run(b, CU.cuts_for("pu50-ttbar-like"))
     from paper_2008_13461_gb300 import _lib as L
     K, nc, nh = res.counts.n_tracks, res.counts.n_cells, len(b["x"])
     scratch = torch.empty(nc + nh, dtype=torch.int32, device="cuda:0")

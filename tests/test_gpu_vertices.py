@@ -113,8 +113,8 @@ def test_vertices_edge_cases():
 
 
 def test_track_summary_of_the_pipeline_tracks_matches_the_oracle():
-    b = E.make_batch(4, n_events=2)                       # two pileup-50 events
-    cuts = CU.cuts_for_config(4)
+    b = E.make_batch("pu50-batch32", n_events=2)                       # two pileup-50 events
+    cuts = CU.cuts_for("pu50-batch32")
     want = oracle_run(b, cuts)
     pipe = make_pipeline(cuts)
     t = to_dev(b)
@@ -141,8 +141,8 @@ def test_track_summary_of_the_pipeline_tracks_matches_the_oracle():
 def test_vertices_of_the_pipeline_tracks():
     """Sec. 3.5 + 3.6 on the fitted tracks of pileup events: every vertex's
     z is the weighted mean of the tracks assigned to it."""
-    b = E.make_batch(4, n_events=2)
-    pipe = make_pipeline(CU.cuts_for_config(4))
+    b = E.make_batch("pu50-batch32", n_events=2)
+    pipe = make_pipeline(CU.cuts_for("pu50-batch32"))
     t = to_dev(b)
     res, bufs = pipe.run(t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
     v, sm = pipe.find_vertices(bufs, res.counts, t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])

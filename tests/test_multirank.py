@@ -28,7 +28,7 @@ def _rank(rank, world, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     n_ev = 2
     first = bench.shard_first_event(rank, n_ev)
-    b = E.make_batch(2, n_events=n_ev, first=first)
+    b = E.make_batch("pu50-ttbar-like", n_events=n_ev, first=first)
     slowest = bench.max_over_ranks(10.0 + 5.0 * rank, world)
     q.put((rank, first, int(b["x"].size), float(b["x"][:8].sum()), slowest))
     dist.barrier()

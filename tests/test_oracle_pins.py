@@ -160,14 +160,14 @@ def test_predicate_meaning(name):
 
 # ------------------------------------------------- graph vs brute force
 def _small_event():
-    cfg = dataclasses.replace(E.CONFIGS[2], name="small", index=90, pileup=0, hard_tracks=0,
+    cfg = dataclasses.replace(E.WORKLOADS["pu50-ttbar-like"], name="small", index=90, pileup=0, hard_tracks=0,
                               fixed_tracks=40, noise_frac=0.15)
     return E.make_batch(cfg)
 
 
 def test_graph_stages_against_brute_force():
     b = _small_event()
-    cuts = CU.cuts_for_config(2)
+    cuts = CU.cuts_for("pu50-ttbar-like")
     ml = G.module_layer_table()
     res = oracle.run(b, cuts, CU.FIT_PARAMS, ml, DISK, stage=3)
     lay = ml[b["module"]]
@@ -255,11 +255,11 @@ def test_cleaning_keeps_only_the_quadruplet():
     """A lone barrel track crossing all four layers yields the quadruplet
     B1B2B3B4 and, through the skip pairs, the triplets B1B3B4 and B1B2B4, which
     share a cell with it; only the quadruplet survives (Sec. 3.3)."""
-    cfg = dataclasses.replace(E.CONFIGS[1], name="one", index=91, fixed_tracks=1, eta_max=0.3,
+    cfg = dataclasses.replace(E.WORKLOADS["barrel-50-helices"], name="one", index=91, fixed_tracks=1, eta_max=0.3,
                               pt_min=5.0, pt_max=6.0)
     b = E.make_batch(cfg)
     assert b["x"].size == 4
-    res = oracle.run(b, CU.cuts_for_config(1), CU.FIT_PARAMS, G.module_layer_table(), DISK, stage=3)
+    res = oracle.run(b, CU.cuts_for("barrel-50-helices"), CU.FIT_PARAMS, G.module_layer_table(), DISK, stage=3)
     lay = G.module_layer_table()[b["module"]]
     seqs = sorted(tuple(int(lay[h]) for h in res["tuple_hits"][t, :res["tuple_n"][t]])
                   for t in range(len(res["tuple_n"])))
@@ -270,10 +270,11 @@ def test_cleaning_keeps_only_the_quadruplet():
 
 
 def test_full_finding_on_noiseless_helices():
-    """Config 1: every generated track leaving >= 3 hits is found exactly once
-    as a tuple holding all its hits; no surviving tuple mixes tracks."""
-    b = E.make_batch(1)
-    res = oracle.run(b, CU.cuts_for_config(1), CU.FIT_PARAMS, G.module_layer_table(), DISK, stage=4)
+    """50 noiseless barrel helices: every generated track leaving >= 3 hits
+    is found exactly once as a tuple holding all its hits; no surviving tuple
+    mixes tracks."""
+    b = E.make_batch("barrel-50-helices")
+    res = oracle.run(b, CU.cuts_for("barrel-50-helices"), CU.FIT_PARAMS, G.module_layer_table(), DISK, stage=4)
     tid = b["track"]
     counts = np.bincount(tid[tid >= 0], minlength=b["trk_pt"].size)
     want = {t for t in range(counts.size) if counts[t] >= 3}
@@ -386,9 +387,9 @@ def test_fit_pulls_on_scattered_tracks():
     """Tracks simulated with scattering kinks at inner hits: residuals of the
     fitted parameters divided by their fitted errors are N(0,1) and chi2
     averages ndf (tracks matched to one simulated particle)."""
-    cfg = dataclasses.replace(E.CONFIGS[2], ms_skip_first=True, noise_frac=0.0, overlaps=False)
+    cfg = dataclasses.replace(E.WORKLOADS["pu50-ttbar-like"], ms_skip_first=True, noise_frac=0.0, overlaps=False)
     b = E.make_batch(cfg)
-    res = oracle.run(b, CU.cuts_for_config(2), CU.FIT_PARAMS, G.module_layer_table(), DISK, stage=4)
+    res = oracle.run(b, CU.cuts_for("pu50-ttbar-like"), CU.FIT_PARAMS, G.module_layer_table(), DISK, stage=4)
     tt = res["track_tuple"]
     n = res["tuple_n"][tt]
     Hh = res["tuple_hits"][tt]

@@ -64,10 +64,10 @@ def _check(batch, pipe, t, ref_order):
 
 
 def test_noalloc_binning_matches_the_workspace_path_on_consecutive_calls():
-    b2 = E.make_batch(2)
-    pipe2, t2, ref2 = _reference_order(b2, CU.cuts_for_config(2))
-    b4 = E.make_batch(4, n_events=3)
-    pipe4, t4, ref4 = _reference_order(b4, CU.cuts_for_config(4))
+    b2 = E.make_batch("pu50-ttbar-like")
+    pipe2, t2, ref2 = _reference_order(b2, CU.cuts_for("pu50-ttbar-like"))
+    b4 = E.make_batch("pu50-batch32", n_events=3)
+    pipe4, t4, ref4 = _reference_order(b4, CU.cuts_for("pu50-batch32"))
     _check(b2, pipe2, t2, ref2)     # first call
     _check(b4, pipe4, t4, ref4)     # second call: different sizes, same fixed array
     _check(b2, pipe2, t2, ref2)     # third call: stale contents of the array must not matter
@@ -75,8 +75,8 @@ def test_noalloc_binning_matches_the_workspace_path_on_consecutive_calls():
 
 def test_noalloc_rejects_problems_beyond_its_fixed_scratch():
     from paper_2008_13461_gb300 import _lib as L
-    b = E.make_batch(1)
-    pipe = make_pipeline(CU.cuts_for_config(1))
+    b = E.make_batch("barrel-50-helices")
+    pipe = make_pipeline(CU.cuts_for("barrel-50-helices"))
     t = to_dev(b)
     hits = pipe._hits(t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
     hits.n_hits = (1 << 20) + 1          # rejected on the host, before any launch
