@@ -632,6 +632,7 @@ def run_native(args, rank, world, local_rank):
                             "exact_fallbacks": counts.n_exact_fallbacks},
         "stage_ms": dict(zip(stage_names, stage_ms)),
         "graph_ms_per_step": graph_ms,
+        "graph_events_per_s": (n_ev / (graph_ms * 1e-3)) if isinstance(graph_ms, float) else graph_ms,
         "per_event_form": per_event_s if isinstance(per_event_s, str) else {
             "events_per_s": n_ev / per_event_s,
             "note": "same kernels one event at a time, host read of counts after every stage"},
