@@ -180,3 +180,26 @@ def test_read_counts_and_hit_order_check_the_workspace():
         L.PT_ERR_INVALID_ARG
     assert lib.pt_hit_order(WS, nbytes - 1, C.byref(hits), C.byref(cfg)) is None
     assert lib.pt_hit_order(WS, nbytes, C.byref(hits), C.byref(cfg)) is not None      # host arithmetic only
+
+
+def test_allocation_free_binning_checks_its_arguments_and_limits():
+    cfg, hits, _ = _valid()
+    lib = L.lib()
+    g = cfg.geometry
+
+    def call(h=hits, geo=g, nphi=96, nt=48, binned=PTR, order=PTR, off=PTR, flags=PTR):
+        return lib.pt_bin_hits_noalloc(C.byref(h), C.byref(geo), nphi, nt, binned, order, off, flags, None)
+
+    bad = L.PT_ERR_INVALID_ARG
+    assert call(binned=None) == bad and call(order=None) == bad and call(off=None) == bad and call(flags=None) == bad
+    assert call(binned=PTR + 8) == bad                                   # float4 rows: 16-byte aligned
+    assert call(nphi=15) == bad and call(nphi=1025) == bad and call(nt=0) == bad and call(nt=65) == bad
+    assert call(h=L.Hits(PTR, PTR, PTR, PTR, PTR, None, 5000, 2)) == bad
+    assert call(h=L.Hits(PTR, None, PTR, PTR, PTR, PTR, 5000, 2)) == bad
+    assert call(h=L.Hits(PTR, PTR, PTR, PTR, PTR, PTR, 5000, 0)) == bad
+    geo = L.Geometry.from_buffer_copy(g)
+    geo.layer[3].zmin, geo.layer[3].zmax = 5.0, -5.0
+    assert call(geo=geo) == bad
+    # beyond the fixed scratch: 2^20 hits, 2^22 tiles
+    assert call(h=L.Hits(PTR, PTR, PTR, PTR, PTR, PTR, (1 << 20) + 1, 2)) == L.PT_ERR_TOO_LARGE
+    assert call(h=L.Hits(PTR, PTR, PTR, PTR, PTR, PTR, 5000, 100), nphi=96, nt=48) == L.PT_ERR_TOO_LARGE
