@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
-def run4():
+def pu50_pair():
     from paper_2008_13461_gb300.autograd import DifferentiableFit
     b = E.make_batch("pu50-batch32", n_events=2)
     cuts = CU.cuts_for("pu50-batch32")
@@ -58,16 +58,16 @@ def _loss_grads(df, t, gp, gc):
     return params.detach(), chi2.detach(), x.grad.cpu().numpy(), y.grad.cpu().numpy(), z.grad.cpu().numpy()
 
 
-def test_refit_reproduces_the_pipeline_fit(run4):
-    b, t, hits, df = run4
+def test_refit_reproduces_the_pipeline_fit(pu50_pair):
+    b, t, hits, df = pu50_pair
     params, chi2 = df.fit(t["x"], t["y"], t["z"])
     assert params.shape[0] == len(hits)
     p2, c2 = df.fit(t["x"], t["y"], t["z"])          # same tracks, same order
     assert torch.equal(params, p2) and torch.equal(chi2, c2)
 
 
-def test_adjoint_matches_the_oracle_gradient(run4):
-    b, t, hits, df = run4
+def test_adjoint_matches_the_oracle_gradient(pu50_pair):
+    b, t, hits, df = pu50_pair
     rng = np.random.default_rng(5)
     pick = _disjoint(hits, rng, 120)
     K = len(hits)
@@ -91,8 +91,8 @@ def test_adjoint_matches_the_oracle_gradient(run4):
     assert worst < 1e-5
 
 
-def test_adjoint_obeys_the_sum_rules(run4):
-    b, t, hits, df = run4
+def test_adjoint_obeys_the_sum_rules(pu50_pair):
+    b, t, hits, df = pu50_pair
     K = len(hits)
     dev = t["x"].device
     x = t["x"].cpu().numpy().astype(np.float64)
@@ -114,8 +114,8 @@ def test_adjoint_obeys_the_sum_rules(run4):
         assert abs(rot - (K if o == 1 else 0.0)) < 1e-4 * scale, (o, rot)
 
 
-def test_adjoint_matches_finite_differences_of_the_gpu_fit(run4):
-    b, t, hits, df = run4
+def test_adjoint_matches_finite_differences_of_the_gpu_fit(pu50_pair):
+    b, t, hits, df = pu50_pair
     rng = np.random.default_rng(9)
     K = len(hits)
     dev = t["x"].device
@@ -141,8 +141,8 @@ def test_adjoint_matches_finite_differences_of_the_gpu_fit(run4):
             assert abs(fd - g[h]) <= 2e-2 * abs(g[h]) + 2e-2, (int(h), axis, fd, float(g[h]))
 
 
-def test_alignment_gradient_matches_the_oracle(run4):
-    b, t, hits, df = run4
+def test_alignment_gradient_matches_the_oracle(pu50_pair):
+    b, t, hits, df = pu50_pair
     dev = t["x"].device
     nm = G.N_MODULES
     K = len(hits)

@@ -22,16 +22,16 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
-def batch2():
+def pu50():
     return E.make_batch("pu50-ttbar-like")
 
 
 @pytest.fixture(scope="module")
-def oracle2(batch2):
-    return oracle_run(batch2, CU.cuts_for("pu50-ttbar-like"))
+def pu50_oracle(pu50):
+    return oracle_run(pu50, CU.cuts_for("pu50-ttbar-like"))
 
 
-def test_config1_noiseless_barrel():
+def test_noiseless_barrel_helices():
     b = E.make_batch("barrel-50-helices")
     cuts = CU.cuts_for("barrel-50-helices")
     res = gpu_run(b, cuts)
@@ -41,10 +41,10 @@ def test_config1_noiseless_barrel():
     assert res.counts.n_tracks > 30
 
 
-def test_config2_pu50(batch2, oracle2):
-    res = gpu_run(batch2, CU.cuts_for("pu50-ttbar-like"))
-    nc, ne, nt = compare_sets(res, oracle2)
-    err = compare_tracks(res, oracle2)
+def test_pu50_event(pu50, pu50_oracle):
+    res = gpu_run(pu50, CU.cuts_for("pu50-ttbar-like"))
+    nc, ne, nt = compare_sets(res, pu50_oracle)
+    err = compare_tracks(res, pu50_oracle)
     assert nc > 50000 and nt > 1000
     print("pu50-ttbar-like fit error (max, p99):", err)
 
@@ -65,8 +65,8 @@ def _slice(b, e):
 
 
 def test_ragged_batch_with_empty_and_tiny_events():
-    b4 = E.make_batch("pu50-batch32", n_events=3)
-    evs = [_slice(b4, 0), _slice(b4, 1), _slice(b4, 2)]
+    b32 = E.make_batch("pu50-batch32", n_events=3)
+    evs = [_slice(b32, 0), _slice(b32, 1), _slice(b32, 2)]
     empty = {k: v[:0] for k, v in evs[0].items()}
     one = {k: v[:1] for k, v in evs[1].items()}
     batch = _concat([empty, evs[0], one, evs[1], empty, empty, evs[2], one])
@@ -90,16 +90,16 @@ def test_all_empty_batch():
     dict(n_phi_bins=1024, n_t_bins=64, doublet_lanes=32, connect_lanes=32, blocks_per_sm=2),
     dict(n_phi_bins=64, n_t_bins=8, doublet_lanes=16, connect_lanes=16, blocks_per_sm=16),
 ])
-def test_results_do_not_depend_on_tuning(batch2, oracle2, tuning):
-    res = gpu_run(batch2, CU.cuts_for("pu50-ttbar-like"), tuning=tuning)
-    compare_sets(res, oracle2)
-    compare_tracks(res, oracle2)
+def test_results_do_not_depend_on_tuning(pu50, pu50_oracle, tuning):
+    res = gpu_run(pu50, CU.cuts_for("pu50-ttbar-like"), tuning=tuning)
+    compare_sets(res, pu50_oracle)
+    compare_tracks(res, pu50_oracle)
 
 
-def test_autotune_picks_a_tuning_with_unchanged_results(batch2, oracle2):
+def test_autotune_picks_a_tuning_with_unchanged_results(pu50, pu50_oracle):
     from paper_2008_13461_gb300.autotune import autotune
     pipe = make_pipeline(CU.cuts_for("pu50-ttbar-like"), tuning=dict(n_t_bins=32, doublet_lanes=8, n_phi_bins=128))
-    t = to_dev(batch2)
+    t = to_dev(pu50)
     args = (t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
     space = (("n_t_bins", (8, 32)), ("doublet_lanes", (4, 8)), ("n_phi_bins", (64, 128)))   # the base is inside
     best, timings = autotune(pipe, *args, reps=1, space=space)   # raises if a tuning changes a count
@@ -107,31 +107,31 @@ def test_autotune_picks_a_tuning_with_unchanged_results(batch2, oracle2):
     assert best["n_t_bins"] in (8, 32) and best["doublet_lanes"] in (4, 8) and best["n_phi_bins"] in (64, 128)
     pipe.set_tuning(best)
     res, _ = pipe.run(*args)
-    compare_sets(res, oracle2)
+    compare_sets(res, pu50_oracle)
 
 
-def test_capacity_overflow_is_reported_then_retried(batch2, oracle2):
+def test_capacity_overflow_is_reported_then_retried(pu50, pu50_oracle):
     from paper_2008_13461_gb300 import _lib as L
     cuts = CU.cuts_for("pu50-ttbar-like")
     pipe = make_pipeline(cuts)
-    t = to_dev(batch2)
+    t = to_dev(pu50)
     args = (t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
     bufs = pipe.allocate(t["x"].numel(), 1, dict(cells=1000, edges=10, tuples=10, tracks=10))
     pipe.launch(bufs, *args)
     st, c = pipe.counts(bufs, *args)
     assert st == L.PT_ERR_CAPACITY
     assert c.flags & L.FLAG_CELLS
-    assert c.n_cells == len(oracle2["cells"])      # counting continues past the capacity
+    assert c.n_cells == len(pu50_oracle["cells"])      # counting continues past the capacity
     res, _ = pipe.run(*args, bufs=bufs)             # grows the buffers and reruns
-    compare_sets(res, oracle2)
+    compare_sets(res, pu50_oracle)
 
 
-def test_input_contract_violations_are_flagged(batch2):
+def test_input_contract_violations_are_flagged(pu50):
     from paper_2008_13461_gb300 import _lib as L
     cuts = CU.cuts_for("pu50-ttbar-like")
     pipe = make_pipeline(cuts)
     for what in ("offgrid", "module", "envelope"):
-        b = {k: np.array(v, copy=True) for k, v in batch2.items() if k in ("x", "y", "z", "r", "module", "ev_off")}
+        b = {k: np.array(v, copy=True) for k, v in pu50.items() if k in ("x", "y", "z", "r", "module", "ev_off")}
         if what == "offgrid":
             b["x"][5] = np.float32(b["x"][5]) + np.float32(1e-6)
         elif what == "module":
@@ -146,11 +146,11 @@ def test_input_contract_violations_are_flagged(batch2):
         assert st == L.PT_ERR_INPUT and c.flags & L.FLAG_INPUT, what
 
 
-def test_invalid_arguments_are_rejected_on_the_host(batch2):
+def test_invalid_arguments_are_rejected_on_the_host(pu50):
     from paper_2008_13461_gb300 import _lib as L
     cuts = CU.cuts_for("pu50-ttbar-like")
     pipe = make_pipeline(cuts)
-    t = to_dev(batch2)
+    t = to_dev(pu50)
     bufs = pipe.allocate(t["x"].numel(), 1)
     h = pipe._hits(t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
     cfg = pipe._cfg(bufs.capacity)
