@@ -272,7 +272,8 @@ class Ctx:
 
 
 def measure_graph(c, args):
-    """Median time of a CUDA-graph replay of the four stages."""
+    """Median time of a CUDA-graph replay of the four stages (L2 flushed
+    before each; 3 warm-up replays, then at least 20 timed)."""
     import torch
     from paper_2008_13461_gb300 import _lib as L
     try:
@@ -290,13 +291,14 @@ def measure_graph(c, args):
         torch.cuda.synchronize()
         ge = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         gms = []
-        for _ in range(max(3, args.steps // 2)):
+        for k in range(3 + max(20, args.steps)):        # 3 warm-up replays, then at least 20 timed
             c.flush.zero_()
             ge[0].record(c.stream)
             g.replay()
             ge[1].record(c.stream)
             torch.cuda.synchronize()
-            gms.append(ge[0].elapsed_time(ge[1]))
+            if k >= 3:
+                gms.append(ge[0].elapsed_time(ge[1]))
         st, c3 = L.read_counts(c.ws, c.nb, c.h, c.cfg, c.s)
         assert st == L.PT_OK and c3.n_tracks == c.counts.n_tracks
         return statistics.median(gms)
