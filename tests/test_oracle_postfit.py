@@ -153,3 +153,137 @@ def test_vertices_do_not_depend_on_the_order_of_the_tracks():
     for a, b in zip(v1, v2):                                # the sums only change their order
         assert [len(v["tracks"]) for v in a] == [len(v["tracks"]) for v in b]
         assert np.allclose([v["z"] for v in a], [v["z"] for v in b], rtol=0, atol=1e-12)
+
+
+def _vertices_by_definition(ev, z0, ez0, pt, nh, keep, n_events, cuts):
+    """The vertex finder's rules as plain per-pair loops (float32 scalars for
+    the cuts, tuple keys for the orders, union-find for the groups): the
+    track sets of the vertices of each event, split included, as a sorted
+    list of tuples, and the order of the vertices by sum pT^2."""
+    f = np.float32
+    dzc, c2m = f(cuts["dz_cut"]), f(cuts["chi2_max"])
+    out = []
+    for e in range(n_events):
+        ids = [i for i in range(len(z0)) if ev[i] == e and keep[i] and nh[i] >= cuts["min_hits"]
+               and f(pt[i]) > f(cuts["pt_min"]) and f(0) < f(ez0[i]) < f(cuts["ez0_max"]) and np.isfinite(z0[i])]
+
+        def compat(i, j):
+            dz = f(z0[i]) - f(z0[j])
+            return abs(dz) < dzc and dz * dz < c2m * (f(ez0[i]) * f(ez0[i]) + f(ez0[j]) * f(ez0[j]))
+
+        rho = {i: 1 + sum(compat(i, j) for j in ids if j != i) for i in ids}
+        rank = {i: (-rho[i], f(z0[i]), i) for i in ids}              # smaller tuple = higher rank
+        parent = {}
+        for i in ids:
+            up = [j for j in ids if j != i and compat(i, j) and rank[j] < rank[i]]
+            parent[i] = min(up, key=lambda j: (abs(f(z0[i]) - f(z0[j])), f(z0[j]), j)) if up else i
+        root = {i: i for i in ids}                                  # union-find over the links
+
+        def find(i):
+            while root[i] != i:
+                root[i] = root[root[i]]
+                i = root[i]
+            return i
+
+        for i in ids:
+            a, b = find(i), find(parent[i])
+            if a != b:
+                root[a] = b
+        groups = {}
+        for i in ids:
+            groups.setdefault(find(i), []).append(i)
+        verts = []
+        for members in groups.values():
+            r = next(i for i in members if parent[i] == i)           # the group's root: links only go up
+            if rho[r] <= 1 or len(members) < cuts["min_tracks"]:
+                continue
+            members = sorted(members)
+            zz = np.array([float(f(z0[i])) for i in members])
+            ww = np.array([1.0 / float(f(ez0[i])) ** 2 for i in members])
+            z = float(np.sum(ww * zz) / np.sum(ww))
+            chi2 = float(np.sum(ww * (zz - z) ** 2))
+            parts = [members]
+            if len(members) > 1 and chi2 / (len(members) - 1) > float(f(cuts["split_chi2"])):
+                side = [int(zi >= z) for zi in zz]                  # 1: at or above the mean
+                if 0 < sum(side) < len(side):
+                    for it in range(20):
+                        c = [float(np.sum(ww[[s == k for s in side]] * zz[[s == k for s in side]]) /
+                                   np.sum(ww[[s == k for s in side]])) for k in (0, 1)]
+                        new = [int(abs(zi - c[1]) < abs(zi - c[0])) for zi in zz]
+                        if new == side and it > 0:
+                            break
+                        side = new
+                        if sum(side) in (0, len(side)):
+                            break
+                    lo = [m for m, s in zip(members, side) if s == 0]
+                    hi = [m for m, s in zip(members, side) if s == 1]
+                    if len(lo) >= cuts["min_tracks"] and len(hi) >= cuts["min_tracks"]:
+                        parts = [lo, hi]
+            for part in parts:
+                zp = np.array([float(f(z0[i])) for i in part])
+                wp = np.array([1.0 / float(f(ez0[i])) ** 2 for i in part])
+                verts.append((-float(np.sum(np.float64(f(pt[part])) ** 2)), float(np.sum(wp * zp) / np.sum(wp)),
+                              tuple(part)))
+        out.append([v[2] for v in sorted(verts)])
+    return out
+
+
+def test_vertices_match_the_rules_written_as_pair_loops():
+    """Random small events, with z0 values on a coarse grid so that ties of
+    z0 (and of distances) occur and the tie-breaks decide: the oracle's
+    vectorised finder gives the vertices of the pair-loop definition, in the
+    same order."""
+    rng = np.random.default_rng(12)
+    for trial in range(30):
+        n_events = 3
+        K = int(rng.integers(0, 60))
+        ev = rng.integers(0, n_events, K)
+        centres = rng.uniform(-1.0, 1.0, 4)
+        z0 = np.float32(np.round((centres[rng.integers(0, 4, K)] + rng.normal(0, 0.02, K)) * 500) / 500)
+        ez0 = np.float32(rng.choice([0.004, 0.008, 0.012], K))
+        pt = np.float32(rng.uniform(0.3, 3.0, K))
+        nh = rng.integers(3, 6, K)
+        keep = rng.uniform(size=K) < 0.9
+        cuts = dict(VCUTS, dz_cut=float(rng.choice([0.02, 0.05, 0.1])), chi2_max=float(rng.choice([4.0, 9.0, 25.0])),
+                    split_chi2=float(rng.choice([2.0, 9.0])), min_tracks=int(rng.integers(1, 4)))
+        V, _ = postfit.find_vertices(ev, z0, ez0, pt, nh, keep, n_events, cuts)
+        want = _vertices_by_definition(ev, z0, ez0, pt, nh, keep, n_events, cuts)
+        got = [[tuple(v["tracks"]) for v in vs] for vs in V]
+        assert got == want, (trial, got, want)
+
+
+def test_a_bridge_track_at_equal_distance_joins_the_cluster_with_the_smaller_z0():
+    """Two clusters of six tracks (z0 = 0..5 u and 15..20 u, u = 2^-7 cm,
+    dz_cut = 6 u: every pair inside a cluster is compatible) and one track B
+    at 10 u, compatible only with the two clusters' inner edges (5 u and
+    15 u, both at 5 u from it).  Those two edge tracks have the largest
+    density of their clusters (7, with B) and are not compatible with each
+    other, so they are the two roots; B's nearest higher-ranked tracks are
+    both at 5 u and the tie goes to the smaller z0: B joins the lower
+    cluster.  Both the pair-loop definition and the oracle say so."""
+    u = 2.0 ** -7
+    zs = [k * u for k in range(6)] + [10 * u] + [k * u for k in range(15, 21)]
+    ev, z0, ez, pt, nh, keep = _tracks(zs, ez=0.01)
+    cuts = dict(VCUTS, dz_cut=6 * u, chi2_max=1e4, min_tracks=2, split_chi2=1e9)   # no split to mask the links
+    V, vi = postfit.find_vertices(ev, z0, ez, pt, nh, keep, 1, cuts)
+    groups = sorted(tuple(v["tracks"]) for v in V[0])
+    assert groups == [(0, 1, 2, 3, 4, 5, 6), (7, 8, 9, 10, 11, 12)]
+    assert _vertices_by_definition(ev, z0, ez, pt, nh, keep, 1, cuts) == [[tuple(v["tracks"]) for v in V[0]]]
+
+
+def test_equal_densities_rank_by_the_smaller_z0():
+    """u = 2^-7 cm, dz_cut = 6 u.  P' (-4 u), P (0) and X (2 u) form a short
+    chain; X is also compatible with Q (7 u), the densest track of a cluster
+    Q, R at 7..12 u.  P and X both have density 3, and P ranks above X
+    because its z0 is smaller, so X links to its nearest higher-ranked
+    track, P (2 u away, Q is 5 u away): two vertices, {P', P, X} and the
+    cluster.  (Were the larger z0 to rank higher, X would link to Q and P to
+    X, and everything would form one vertex; the split is switched off so
+    that it cannot undo that.)"""
+    u = 2.0 ** -7
+    zs = [-4 * u, 0.0, 2 * u] + [k * u for k in range(7, 13)]
+    ev, z0, ez, pt, nh, keep = _tracks(zs, ez=0.01)
+    cuts = dict(VCUTS, dz_cut=6 * u, chi2_max=1e4, min_tracks=2, split_chi2=1e9)   # no split to mask the links
+    V, vi = postfit.find_vertices(ev, z0, ez, pt, nh, keep, 1, cuts)
+    assert sorted(tuple(v["tracks"]) for v in V[0]) == [(0, 1, 2), (3, 4, 5, 6, 7, 8)]
+    assert _vertices_by_definition(ev, z0, ez, pt, nh, keep, 1, cuts) == [[tuple(v["tracks"]) for v in V[0]]]
