@@ -287,3 +287,31 @@ def test_equal_densities_rank_by_the_smaller_z0():
     V, vi = postfit.find_vertices(ev, z0, ez, pt, nh, keep, 1, cuts)
     assert sorted(tuple(v["tracks"]) for v in V[0]) == [(0, 1, 2), (3, 4, 5, 6, 7, 8)]
     assert _vertices_by_definition(ev, z0, ez, pt, nh, keep, 1, cuts) == [[tuple(v["tracks"]) for v in V[0]]]
+
+
+def test_ambiguity_resolution_matches_its_rules_written_as_pair_loops():
+    """Random n-tuplets over few hits (so cells and hits are shared a lot),
+    chi2 and |tip| on coarse grids (so ties occur), a few NaN chi2: the
+    oracle's keep flags equal the two rules evaluated pair by pair."""
+    rng = np.random.default_rng(4)
+    for trial in range(40):
+        T = int(rng.integers(1, 40))
+        rows = [list(rng.choice(12, size=int(rng.integers(3, 6)), replace=False)) for _ in range(T)]
+        H, Cc, n = _tuples(rows)
+        tt = rng.permutation(T)[:int(rng.integers(1, T + 1))]      # the tuples that became tracks
+        chi2 = np.float32(rng.integers(0, 4, len(tt)) * 0.5)
+        chi2[rng.uniform(size=len(tt)) < 0.1] = np.nan
+        tip = np.float32(rng.integers(-3, 4, len(tt)) * 0.01)
+        keep = postfit.resolve_ambiguities(H, Cc, n, tt, chi2, tip)
+
+        def key(v):
+            return float("inf") if not (v >= 0) else float(v)
+
+        cells = [set(Cc[t, :n[t] - 1].tolist()) for t in tt]
+        hits = [set(H[t, :n[t]].tolist()) for t in tt]
+        K = len(tt)
+        k1 = [all(key(chi2[k]) <= key(chi2[j]) for j in range(K) if cells[k] & cells[j]) for k in range(K)]
+        want = [k1[k] and (n[tt[k]] != 3 or all(abs(float(tip[k])) <= abs(float(tip[j])) for j in range(K)
+                                                if k1[j] and n[tt[j]] == 3 and hits[k] & hits[j]))
+                for k in range(K)]
+        assert keep.tolist() == want, trial
