@@ -156,7 +156,8 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "window": "nvidia-smi every 200 ms from the first warm-up step to the end of the timed steps"}
 
 
 # ------------------------------------------------------------------ bytes
@@ -537,6 +538,10 @@ def run_native(args, rank, world, local_rank):
             if evs:
                 evs[i + 1].record(stream)
 
+    # the clock sampler starts with the warm-up steps (the same work as the
+    # timed ones): nvidia-smi takes a few hundred ms to report its first
+    # sample, longer than the timed steps of a short run
+    clocks = Clocks(local_rank) if rank == 0 else None
     for _ in range(args.warmup):
         flush.zero_()
         step()
@@ -547,7 +552,6 @@ def run_native(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(local_rank) if rank == 0 else None
     for k in range(args.steps):
         flush.zero_()
         step(evs[k])
