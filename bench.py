@@ -118,12 +118,12 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, tmp_dir: str | None = None):
         self.proc = None
         self.path = None
         self.idx = gpu_index
         try:
-            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            fd, self.path = tempfile.mkstemp(suffix=".csv", dir=tmp_dir)
             os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
@@ -131,6 +131,11 @@ class Clocks:
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            if getattr(self, "f", None):
+                self.f.close()
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+            self.path = None
 
     def stop(self):
         if self.proc is None:

@@ -111,3 +111,33 @@ def test_per_event_form_raises_on_other_errors(monkeypatch):
 def test_grow_capacity_never_shrinks():
     cap = {"cells": 100, "edges": 5000}
     assert bench.grow_capacity(cap, {"cells": 1000, "edges": 10}) == {"cells": 2274, "edges": 5000}
+
+
+def test_clock_sampler_parses_nvidia_smi_lines(tmp_path, monkeypatch):
+    """The sampler's reading of nvidia-smi's CSV (a stand-in script prints
+    three samples in the same format and keeps running until stopped)."""
+    import os
+    import time
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '0, 2070, 2070, 910.2, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo '0, 2055, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active'\n"
+                    "echo '0, 2070, 2070, 1001.7, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active'\n"
+                    "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ['PATH']}")
+    c = bench.Clocks(0, tmp_dir=str(tmp_path))
+    for _ in range(100):                       # until the three lines are written
+        with open(c.path) as fh:
+            if fh.read().count("\n") >= 3:
+                break
+        time.sleep(0.05)
+    got = c.stop()
+    assert got["samples"] == 3 and got["sm_mhz"] == 2070.0 and got["sm_max_mhz"] == 2070.0
+    assert got["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_without_nvidia_smi_reports_nothing(monkeypatch, tmp_path):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    assert bench.Clocks(0, tmp_dir=str(tmp_path)).stop() is None
+    assert list(tmp_path.iterdir()) == []           # its sample file is removed
