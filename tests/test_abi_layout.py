@@ -72,3 +72,35 @@ def test_struct_matches_the_header(c_layout, cname):
 def test_constants_match_the_header(c_layout):
     for name, v in CONSTANTS.items():
         assert v == c_layout[("const", name)], name
+
+
+def test_oracle_binding_matches_its_header(tmp_path):
+    """The same check for the oracle's ctypes mirror of oracle/oracle.h (a
+    drifted field there would feed the oracle wrong cuts or read its results
+    from the wrong offsets)."""
+    import oracle
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"or_pair": oracle._Pair, "or_region": oracle._Region, "or_cuts": oracle._Cuts,
+               "or_fitpar": oracle._FitPar, "or_input": oracle._Input, "or_tuple": oracle._Tuple,
+               "or_result": oracle._Result}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", "#include <stdint.h>", '#include "oracle.h"',
+             "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("size {cname} %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("off {cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src, exe = tmp_path / "olayout.c", tmp_path / "olayout"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run([cc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "oracle"), str(src), "-o", str(exe)],
+                   check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        kind, *key, val = ln.split()
+        got[(kind, *key)] = int(val)
+    for cname, cls in structs.items():
+        assert C.sizeof(cls) == got[("size", cname)], cname
+        for f, _ in cls._fields_:
+            assert getattr(cls, f).offset == got[("off", cname, f)], f"{cname}.{f}"
