@@ -1,7 +1,8 @@
 """The ctypes binding mirrors include/pt.h: every struct's size and every
 field's offset, and the status codes, flags and limits, as a C compiler lays
 them out from the header itself.  A field added, reordered or retyped on one
-side only fails here, on the CPU, before any call reaches a kernel."""
+side only fails here, on the CPU, before any call reaches a kernel.  The
+oracle's own binding is checked against oracle/oracle.h the same way."""
 import ctypes as C
 import os
 import shutil
