@@ -9,7 +9,6 @@ the count read-back and grows the buffers when a capacity was exceeded.
 """
 from __future__ import annotations
 
-import ctypes as C
 import dataclasses
 
 import torch

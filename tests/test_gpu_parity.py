@@ -15,8 +15,7 @@ from synth import cuts as CU
 from synth import events as E
 from synth import geometry as G
 
-from parity import (compare_params, compare_sets, compare_tracks, gpu_run, gpu_sets, make_pipeline,
-                    oracle_run, to_dev)
+from parity import compare_params, compare_sets, compare_tracks, gpu_run, make_pipeline, oracle_run, to_dev
 
 pytestmark = pytest.mark.gpu
 

@@ -14,7 +14,7 @@ from synth import cuts as CU
 from synth import events as E
 from synth.vertices import vertex_tracks
 
-from parity import gpu_run, make_pipeline, oracle_run, to_dev
+from parity import make_pipeline, oracle_run, to_dev
 
 pytestmark = pytest.mark.gpu
 
