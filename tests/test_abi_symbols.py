@@ -67,3 +67,22 @@ def test_post_fit_entry_points_reject_bad_arguments_without_gpu():
                                 None, None, None, None, None, None) == bad
     assert lib.pt_resolve_ambiguities(C.byref(L.Tuples()), None, -1, None, None, 5, 0, 0, None, None, None) == bad
     assert lib.pt_align_hits(10, None, None, None, None, 0, None, None, None, None, None, None, None) == bad
+
+
+def test_a_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No fallback: without the CUDA library (and without a way to build it)
+    the binding raises instead of running anything else."""
+    import pytest
+    from paper_2008_13461_gb300 import _lib, build
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "libpt_gb300.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        _lib.lib(build_if_missing=False)
+
+    def no_compiler():
+        raise RuntimeError("nvcc not found")
+
+    monkeypatch.setattr(build, "_stale", lambda: True)
+    monkeypatch.setattr(build, "nvcc", no_compiler)
+    with pytest.raises(RuntimeError, match="nvcc"):
+        _lib.lib()
