@@ -673,7 +673,7 @@ def run_reference(args, rank, world):
     times = _time_oracle(sample, repeats=args.warmup + args.steps)[args.warmup:]
     value = args.steps / (SECTOR * sum(times))
     cpu = {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
-           "sample": _cpu_desc(int(sample["x"].size))}
+           "sample": _cpu_desc(int(sample["x"].size)), "cpu": _cpu_model()}
     return {
         "impl": "reference",
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
