@@ -141,3 +141,22 @@ def test_clock_sampler_without_nvidia_smi_reports_nothing(monkeypatch, tmp_path)
     monkeypatch.setenv("PATH", str(tmp_path))
     assert bench.Clocks(0, tmp_dir=str(tmp_path)).stop() is None
     assert list(tmp_path.iterdir()) == []           # its sample file is removed
+
+
+def test_kernel_source_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
+    """The key that ties the committed traffic summary to the kernels: a
+    comment edit keeps it, a code edit changes it."""
+    import os
+    import shutil
+    for sub in ("include", os.path.join("paper_2008_13461_gb300", "csrc")):
+        shutil.copytree(os.path.join(bench.ROOT, sub), tmp_path / sub)
+    real = bench.kernel_source_hash()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    assert h0 == real                                 # the copy hashes like the tree
+    f = tmp_path / "paper_2008_13461_gb300" / "csrc" / "pt_connect.cu"
+    src = f.read_text()
+    f.write_text("// a new comment line\n" + src.replace("\n", "\n/* block comment */\n", 1))
+    assert bench.kernel_source_hash() == h0
+    f.write_text(src.replace("kCaQueue", "kCaQueueX"))
+    assert bench.kernel_source_hash() != h0
