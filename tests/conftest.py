@@ -7,5 +7,9 @@ if ROOT not in sys.path:
 
 
 def pytest_configure(config):
+    # temporary files of the tests stay inside the repository, whatever the
+    # working directory
+    if not config.option.basetemp:
+        config.option.basetemp = os.path.join(ROOT, ".pytest_tmp")
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running")
