@@ -1,0 +1,62 @@
+"""Host logic of Pipeline.run without a GPU: the capacity retry grows the
+buffers to what the counters asked for, and every other device status
+raises (the library's calls are replaced by stand-ins)."""
+import pytest
+import torch
+
+from paper_2008_13461_gb300 import _lib as L
+from paper_2008_13461_gb300.pipeline import Pipeline
+from synth import cuts as CU
+from synth import geometry as G
+
+
+def _pipe(monkeypatch, statuses, need):
+    pipe = Pipeline(G.layers(), G.module_layer_table(), CU.cuts_for("pu50-ttbar-like"), CU.FIT_PARAMS,
+                    device="cpu")
+    allocated, seq = [], iter(statuses)
+
+    class Bufs:
+        def __init__(self, cap):
+            self.capacity = dict(cap)
+
+    def allocate(n_hits, n_events, capacity=None):
+        cap = dict(capacity or pipe.default_capacity(n_hits))
+        allocated.append(cap)
+        return Bufs(cap)
+
+    def counts(bufs, *hits, stream=None):
+        c = L.Counts()
+        c.n_cells, c.n_edges, c.n_tuples, c.n_tracks = need["cells"], need["edges"], need["tuples"], need["tracks"]
+        c.flags = 0
+        return next(seq), c
+
+    monkeypatch.setattr(pipe, "allocate", allocate)
+    monkeypatch.setattr(pipe, "launch", lambda *a, **k: None)
+    monkeypatch.setattr(pipe, "counts", counts)
+    monkeypatch.setattr(pipe, "result", lambda bufs, c, *hits: ("result", bufs.capacity))
+    hits = [torch.zeros(100) for _ in range(4)] + [torch.zeros(100, dtype=torch.int32),
+                                                   torch.tensor([0, 100], dtype=torch.int32)]
+    return pipe, hits, allocated
+
+
+def test_capacity_overflow_grows_the_buffers_and_retries(monkeypatch):
+    need = dict(cells=10 ** 6, edges=10, tuples=20, tracks=30)
+    pipe, hits, allocated = _pipe(monkeypatch, [L.PT_ERR_CAPACITY, L.PT_OK], need)
+    (tag, cap), _ = pipe.run(*hits)
+    assert tag == "result" and len(allocated) == 2
+    first = allocated[0]
+    assert cap["cells"] == int(10 ** 6 * 1.25) + 1024                  # grown to the count asked for
+    assert all(cap[k] == first[k] for k in ("edges", "tuples", "tracks"))   # never shrunk
+
+
+def test_other_device_errors_raise(monkeypatch):
+    pipe, hits, _ = _pipe(monkeypatch, [L.PT_ERR_INPUT], dict(cells=0, edges=0, tuples=0, tracks=0))
+    with pytest.raises(L.PtError):
+        pipe.run(*hits)
+
+
+def test_retries_are_bounded(monkeypatch):
+    pipe, hits, allocated = _pipe(monkeypatch, [L.PT_ERR_CAPACITY] * 10, dict(cells=5, edges=5, tuples=5, tracks=5))
+    with pytest.raises(L.PtError):
+        pipe.run(*hits, max_retries=2)
+    assert len(allocated) == 4                                          # the first buffers and 3 retries
