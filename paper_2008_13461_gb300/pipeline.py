@@ -68,13 +68,13 @@ def find_vertices(ev, z0, ez0, pt, nhits, keep, n_events: int, cuts: dict | None
     decreasing sum pT^2), track_vertex[n_tracks] and status[1] (PT_VTX_*)."""
     c = dict(DEFAULT_VERTEX_CUTS, **(cuts or {}))
     dev = z0.device
-    s = (stream or torch.cuda.current_stream(dev)).cuda_stream
     k = z0.numel()
     for t, dt in ((ev, torch.int32), (z0, torch.float32), (ez0, torch.float32), (pt, torch.float32),
                   (nhits, torch.uint8)) + (((keep, torch.uint8),) if keep is not None else ()):
         if t.dtype != dt or not t.is_contiguous() or t.numel() != k:
             raise ValueError("find_vertices: per-track tensors must be contiguous, of equal length and dtypes "
                              "int32 / float32 x3 / uint8 / uint8")
+    s = (stream or torch.cuda.current_stream(dev)).cuda_stream
     E, M = n_events, max_vertices
     out = dict(n=torch.empty(max(1, E), dtype=torch.int32, device=dev),
                z=torch.empty(max(1, E * M), dtype=torch.float32, device=dev),

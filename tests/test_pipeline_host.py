@@ -60,3 +60,18 @@ def test_retries_are_bounded(monkeypatch):
     with pytest.raises(L.PtError):
         pipe.run(*hits, max_retries=2)
     assert len(allocated) == 4                                          # the first buffers and 3 retries
+
+
+def test_find_vertices_checks_its_tensors_before_any_call():
+    from paper_2008_13461_gb300.pipeline import find_vertices
+    k = 8
+    good = dict(ev=torch.zeros(k, dtype=torch.int32), z0=torch.zeros(k), ez0=torch.ones(k), pt=torch.ones(k),
+                nhits=torch.full((k,), 4, dtype=torch.uint8), keep=torch.ones(k, dtype=torch.uint8))
+    order = ("ev", "z0", "ez0", "pt", "nhits", "keep")
+    for name, bad in (("z0", torch.zeros(k, dtype=torch.float64)),       # wrong dtype
+                      ("ev", torch.zeros(2 * k, dtype=torch.int32)[::2]),  # not contiguous
+                      ("pt", torch.ones(k + 1)),                           # wrong length
+                      ("keep", torch.ones(k, dtype=torch.bool))):          # keep must be uint8
+        args = dict(good, **{name: bad})
+        with pytest.raises(ValueError):
+            find_vertices(*(args[n] for n in order), 1)
