@@ -282,13 +282,15 @@ class Pipeline:
         Returns (Result, Buffers)."""
         if bufs is None:
             bufs = self.allocate(x.numel(), ev_off.numel() - 1)
-        for _ in range(max_retries + 1):
+        for attempt in range(max_retries + 1):
             self.launch(bufs, x, y, z, r, module, ev_off)
             st, c = self.counts(bufs, x, y, z, r, module, ev_off)
             if st == L.PT_OK:
                 return self.result(bufs, c, x, y, z, r, module, ev_off), bufs
             if st != L.PT_ERR_CAPACITY:
                 raise L.PtError(st, f"pipeline (flags 0x{c.flags:x})")
+            if attempt == max_retries:
+                break
             need = dict(cells=c.n_cells, edges=c.n_edges, tuples=c.n_tuples, tracks=c.n_tracks)
             cap = {k: max(bufs.capacity[k], int(need[k] * 1.25) + 1024) for k in need}
             bufs = self.allocate(x.numel(), ev_off.numel() - 1, cap)

@@ -59,7 +59,7 @@ def test_retries_are_bounded(monkeypatch):
     pipe, hits, allocated = _pipe(monkeypatch, [L.PT_ERR_CAPACITY] * 10, dict(cells=5, edges=5, tuples=5, tracks=5))
     with pytest.raises(L.PtError):
         pipe.run(*hits, max_retries=2)
-    assert len(allocated) == 4                                          # the first buffers and 3 retries
+    assert len(allocated) == 3            # the first buffers and one growth per retry, none after the last
 
 
 def test_find_vertices_checks_its_tensors_before_any_call():
