@@ -105,6 +105,32 @@ def find_vertices(ev, z0, ez0, pt, nhits, keep, n_events: int, cuts: dict | None
     return res
 
 
+STAGES = ("cells", "edges", "tuples", "tracks")
+_STAGE_FLAG = dict(cells=L.FLAG_CELLS, edges=L.FLAG_EDGES, tuples=L.FLAG_TUPLES, tracks=L.FLAG_TRACKS)
+MAX_CAPACITY = 0x7FFFFFFF          # int32 indices
+
+
+def grow_capacity(cap: dict, need: dict, flags: int) -> dict:
+    """Capacities for the rerun after an overflow.  A stage that overflowed
+    keeps counting, so its count is what it needs: it gets that plus a
+    quarter and a margin.  The stages after it ran on incomplete inputs
+    (or not at all), so their counts say nothing: each grows at least by the
+    largest ratio an earlier stage grew by.  No capacity shrinks; none may
+    pass 2^31 - 1 (int32 indices), which raises PT_ERR_CAPACITY."""
+    out, ratio = {}, 1.0
+    for k in STAGES:
+        if need[k] > MAX_CAPACITY:
+            raise L.PtError(L.PT_ERR_CAPACITY, f"pipeline: {need[k]} {k} needed, above the int32 limit")
+        want = max(cap[k], int(need[k] * 1.25) + 1024)
+        if ratio > 1.0:
+            want = max(want, int(cap[k] * ratio) + 1024)
+        want = min(want, MAX_CAPACITY)
+        if flags & _STAGE_FLAG[k]:
+            ratio = max(ratio, want / max(1, cap[k]))
+        out[k] = want
+    return out
+
+
 @dataclasses.dataclass
 class Result:
     counts: L.Counts
@@ -277,9 +303,10 @@ class Pipeline:
                           ev_off.numel() - 1, cuts, max_vertices, stream)
         return v, sm
 
-    def run(self, x, y, z, r, module, ev_off, bufs: Buffers | None = None, max_retries: int = 3):
-        """Run the batch and read the counts back; grow buffers on overflow.
-        Returns (Result, Buffers)."""
+    def run(self, x, y, z, r, module, ev_off, bufs: Buffers | None = None, max_retries: int = 4):
+        """Run the batch and read the counts back; grow buffers on overflow
+        (``grow_capacity``) and rerun, at most ``max_retries`` times (one per
+        stage covers the worst cascade).  Returns (Result, Buffers)."""
         if bufs is None:
             bufs = self.allocate(x.numel(), ev_off.numel() - 1)
         for attempt in range(max_retries + 1):
@@ -292,8 +319,7 @@ class Pipeline:
             if attempt == max_retries:
                 break
             need = dict(cells=c.n_cells, edges=c.n_edges, tuples=c.n_tuples, tracks=c.n_tracks)
-            cap = {k: max(bufs.capacity[k], int(need[k] * 1.25) + 1024) for k in need}
-            bufs = self.allocate(x.numel(), ev_off.numel() - 1, cap)
+            bufs = self.allocate(x.numel(), ev_off.numel() - 1, grow_capacity(bufs.capacity, need, c.flags))
         raise L.PtError(L.PT_ERR_CAPACITY, "pipeline: capacity still exceeded after retries")
 
     def run_per_event(self, x, y, z, r, module, ev_off_host):

@@ -10,10 +10,12 @@ from synth import cuts as CU
 from synth import geometry as G
 
 
-def _pipe(monkeypatch, statuses, need):
+def _pipe(monkeypatch, statuses, need, flags=None):
     pipe = Pipeline(G.layers(), G.module_layer_table(), CU.cuts_for("pu50-ttbar-like"), CU.FIT_PARAMS,
                     device="cpu")
     allocated, seq = [], iter(statuses)
+    fl = iter(flags or [0] * len(statuses))
+    needs = iter(need) if isinstance(need, list) else None
 
     class Bufs:
         def __init__(self, cap):
@@ -26,8 +28,9 @@ def _pipe(monkeypatch, statuses, need):
 
     def counts(bufs, *hits, stream=None):
         c = L.Counts()
-        c.n_cells, c.n_edges, c.n_tuples, c.n_tracks = need["cells"], need["edges"], need["tuples"], need["tracks"]
-        c.flags = 0
+        n = next(needs) if needs else need
+        c.n_cells, c.n_edges, c.n_tuples, c.n_tracks = n["cells"], n["edges"], n["tuples"], n["tracks"]
+        c.flags = next(fl)
         return next(seq), c
 
     monkeypatch.setattr(pipe, "allocate", allocate)
@@ -60,6 +63,36 @@ def test_retries_are_bounded(monkeypatch):
     with pytest.raises(L.PtError):
         pipe.run(*hits, max_retries=2)
     assert len(allocated) == 3            # the first buffers and one growth per retry, none after the last
+
+
+def test_a_four_stage_cascade_fits_in_the_default_retries(monkeypatch):
+    # each stage overflows in turn; the stages after an overflowing one
+    # report partial counts (here 0) and still grow with it
+    base = Pipeline.default_capacity(100)
+    seq = [dict(base, cells=2 * base["cells"], edges=0, tuples=0, tracks=0),
+           dict(base, cells=10, edges=3 * base["edges"], tuples=0, tracks=0),
+           dict(base, cells=10, edges=10, tuples=5 * base["tuples"], tracks=0),
+           dict(base, cells=10, edges=10, tuples=10, tracks=7 * base["tracks"]),
+           dict(cells=1, edges=1, tuples=1, tracks=1)]
+    flags = [L.FLAG_CELLS, L.FLAG_EDGES, L.FLAG_TUPLES, L.FLAG_TRACKS, 0]
+    pipe, hits, allocated = _pipe(monkeypatch, [L.PT_ERR_CAPACITY] * 4 + [L.PT_OK], seq, flags)
+    (tag, cap), _ = pipe.run(*hits)
+    assert tag == "result" and len(allocated) == 5
+    a = allocated
+    assert a[1]["cells"] == int(2 * base["cells"] * 1.25) + 1024
+    # the downstream stages grew by the cells' ratio although their counts were 0
+    for k in ("edges", "tuples", "tracks"):
+        assert a[1][k] >= int(base[k] * a[1]["cells"] / base["cells"])
+    assert a[2]["edges"] >= int(3 * base["edges"] * 1.25) and a[4]["tracks"] >= int(7 * base["tracks"] * 1.25)
+
+
+def test_grown_capacities_stay_int32():
+    from paper_2008_13461_gb300.pipeline import MAX_CAPACITY, grow_capacity
+    cap = dict(cells=2 ** 30, edges=2 ** 30, tuples=10, tracks=10)
+    out = grow_capacity(cap, dict(cells=2 ** 31 - 100, edges=5, tuples=5, tracks=5), L.FLAG_CELLS)
+    assert out["cells"] == MAX_CAPACITY and max(out.values()) <= MAX_CAPACITY
+    with pytest.raises(L.PtError):
+        grow_capacity(cap, dict(cells=2 ** 31, edges=5, tuples=5, tracks=5), L.FLAG_CELLS)
 
 
 def test_find_vertices_checks_its_tensors_before_any_call():
