@@ -53,12 +53,29 @@ class DifferentiableFit:
     small rotations about ``centres`` (float[n_modules, 3]), differentiable in
     all of them.  Hit coordinates are float32 tensors on the pipeline's
     device; the hits' modules and events stay those of the run.
+
+    A refit writes into track arrays of its own (allocated here at the
+    run's track capacity), so the run's ``Result.tracks`` keep the fit of
+    the original hits.  The refit still shares the run's workspace, whose
+    track counters it sets to the same values (the selection of tracks
+    depends on the n-tuplets only).
     """
 
     def __init__(self, pipe, bufs, r, module, ev_off, centres: torch.Tensor | None = None):
         self.pipe, self.bufs = pipe, bufs
         self.r, self.module, self.ev_off = r, module, ev_off
         self.centres = None if centres is None else centres.to(pipe.device, torch.float32).contiguous()
+        nk = max(1, int(bufs.capacity["tracks"]))
+        d = pipe.device
+        self.params = torch.empty(nk * 5, dtype=torch.float32, device=d)
+        self.cov = torch.empty(nk * 15, dtype=torch.float32, device=d)
+        self.chi2 = torch.empty(nk, dtype=torch.float32, device=d)
+        self.ndf = torch.empty(nk, dtype=torch.int8, device=d)
+        self.tuple = torch.empty(nk, dtype=torch.int32, device=d)
+
+    def _tracks(self) -> L.Tracks:
+        return L.Tracks(self.params.data_ptr(), self.cov.data_ptr(), self.chi2.data_ptr(), self.ndf.data_ptr(),
+                        self.tuple.data_ptr())
 
     # -- fit
     def _hits(self, x, y, z):
@@ -75,13 +92,13 @@ class DifferentiableFit:
         b = self.bufs
         cfg = self.pipe._cfg(b.capacity)
         h = self._hits(x, y, z)
-        _, _, tuples, tracks = b.structs()
+        _, _, tuples, _ = b.structs()
         s = self._stream()
-        L.fit_tracks(b.ws.data_ptr(), b.ws.numel(), h, cfg, tuples, tracks, s)
+        L.fit_tracks(b.ws.data_ptr(), b.ws.numel(), h, cfg, tuples, self._tracks(), s)
         st, c = L.read_counts(b.ws.data_ptr(), b.ws.numel(), h, cfg, s)
         L.check(st, "refit")
         k = c.n_tracks
-        return b.trk_params[:k * 5].view(k, 5).clone(), b.trk_chi2[:k].clone()
+        return self.params[:k * 5].view(k, 5).clone(), self.chi2[:k].clone()
 
     def _fit_grad(self, x, y, z, gparams, gchi2):
         x, y, z = (t.detach().contiguous() for t in (x, y, z))
@@ -93,9 +110,9 @@ class DifferentiableFit:
         if gparams is None:
             k = int(gc.numel()) if gc is not None else 0
             gp = torch.zeros(k, 5, device=dev)
-        _, _, tuples, tracks = b.structs()
+        _, _, tuples, _ = b.structs()
         L.fit_tracks_grad(b.ws.data_ptr(), b.ws.numel(), self._hits(x, y, z), self.pipe._cfg(b.capacity), tuples,
-                          tracks, gp.data_ptr(), None if gc is None else gc.data_ptr(), gx.data_ptr(),
+                          self._tracks(), gp.data_ptr(), None if gc is None else gc.data_ptr(), gx.data_ptr(),
                           gy.data_ptr(), gz.data_ptr(), self._stream())
         return gx, gy, gz
 

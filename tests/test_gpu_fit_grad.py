@@ -183,3 +183,18 @@ def test_alignment_gradient_matches_the_oracle(pu50_pair):
                 fd = (total(np.zeros(3), hstep * e) - total(np.zeros(3), -hstep * e)) / (2 * hstep)
                 got = gr[m, j - 3]
             assert abs(got - fd) <= 1e-3 * abs(fd) + 1e-3 * (1.0 + np.abs(gs[m]).max()), (int(m), j, got, fd)
+
+
+def test_a_refit_leaves_the_run_tracks_unchanged():
+    from paper_2008_13461_gb300.autograd import DifferentiableFit
+    b = E.make_batch("pu50-batch32", n_events=1)
+    pipe = make_pipeline(CU.cuts_for("pu50-batch32"))
+    t = to_dev(b)
+    res, bufs = pipe.run(t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
+    before = {k: v.clone() for k, v in res.tracks.items()}
+    df = DifferentiableFit(pipe, bufs, t["r"], t["module"], t["ev_off"])
+    params, _ = df.fit(t["x"] + 1e-3, t["y"] - 2e-3, t["z"] + 5e-3)     # moved hits
+    torch.cuda.synchronize()
+    assert not torch.equal(params, before["params"])                      # the refit saw the moved hits
+    for k, v in before.items():
+        assert torch.equal(res.tracks[k], v), k                           # the run's tracks did not change
