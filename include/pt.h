@@ -417,6 +417,9 @@ const char *pt_status_string(pt_status s);
  * memsets, kernels and one 4-byte device copy on `stream`.  The first call on
  * each device looks up the address of the fixed array with
  * cudaGetSymbolAddress, so make that first call before any stream capture.
+ * The address is kept for the life of the process: after cudaDeviceReset()
+ * (or anything else that destroys the device's primary context) it is
+ * stale, so do not call this function again in that process.
  * All calls share the one array: calls whose work overlaps on the GPU (other
  * streams, other host threads) race and must be serialised by the caller. */
 pt_status pt_bin_hits_noalloc(const pt_hits *hits, const pt_geometry *geometry, int32_t n_phi_bins,

@@ -5,6 +5,8 @@
 // callers that cannot allocate device memory (see pt.h).
 #include <string.h>
 
+#include <atomic>
+
 #include "pt_common.cuh"
 #include "pt_kernels.cuh"
 
@@ -26,17 +28,18 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // Device address of g_scratch for the current device, looked up once per
 // device (the name of a __device__ array is only a host-side stand-in).
-void *g_scratch_ptr[64];
+// Host threads may race on the first lookup; each stores the same address.
+std::atomic<void *> g_scratch_ptr[64];
 
 pt_status scratch_address(void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PT_ERR_CUDA;
-    if (!g_scratch_ptr[dev]) {
-        void *ptr = nullptr;
+    void *ptr = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!ptr) {
         if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return PT_ERR_CUDA;
-        g_scratch_ptr[dev] = ptr;
+        g_scratch_ptr[dev].store(ptr, std::memory_order_release);
     }
-    *out = g_scratch_ptr[dev];
+    *out = ptr;
     return PT_OK;
 }
 

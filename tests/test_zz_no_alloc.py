@@ -73,6 +73,28 @@ def test_noalloc_binning_matches_the_workspace_path_on_consecutive_calls():
     _check(b2, pipe2, t2, ref2)     # third call: stale contents of the array must not matter
 
 
+def test_noalloc_call_allocates_no_device_memory():
+    b = E.make_batch("pu50-batch32", n_events=2)
+    pipe, t, _ = _reference_order(b, CU.cuts_for("pu50-batch32"))
+    _noalloc(pipe, t)                                   # warm-up: the library's kernels are loaded
+    from paper_2008_13461_gb300 import _lib as L
+    n = t["x"].numel()
+    nphi, nt = pipe.tuning["n_phi_bins"], pipe.tuning["n_t_bins"]
+    binned = torch.empty((n, 4), dtype=torch.float32, device="cuda:0")
+    order = torch.empty(n, dtype=torch.int32, device="cuda:0")
+    tile_off = torch.empty(2 * 10 * nphi * nt + 1, dtype=torch.int32, device="cuda:0")
+    flags = torch.empty(1, dtype=torch.int32, device="cuda:0")
+    hits = pipe._hits(t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    L.bin_hits_noalloc(hits, pipe.cfg.geometry, nphi, nt, binned.data_ptr(), order.data_ptr(),
+                       tile_off.data_ptr(), flags.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0          # no device allocation by the library
+    assert torch.cuda.memory_allocated() == alloc0        # nor through torch
+    assert int(flags.item()) == 0 and int(tile_off[-1].item()) == n
+
+
 def test_noalloc_rejects_problems_beyond_its_fixed_scratch():
     from paper_2008_13461_gb300 import _lib as L
     b = E.make_batch("barrel-50-helices")
