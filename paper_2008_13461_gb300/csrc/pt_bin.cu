@@ -1,8 +1,8 @@
 // Step a0: tile the hits of every (event, layer) in phi x t (t = z on barrel
 // layers, r on disks) -- the paper's phi-tiled hit structure of Sec. 3.2,
-// here two-dimensional.  Counting sort: per-hit tile + rank by atomics,
-// exclusive scan of the tile counts, scatter into a binned structure of
-// arrays.  Tiles only accelerate the doublet search; results do not depend
+// here two-dimensional.  Counting sort: per-hit tile + rank by
+// warp-aggregated atomics, exclusive scan of the tile counts (block prefix
+// scans), scatter into a binned structure of arrays.  Tiles only accelerate the doublet search; results do not depend
 // on them.
 #include "pt_common.cuh"
 #include "pt_kernels.cuh"
@@ -14,41 +14,54 @@ __device__ __forceinline__ bool on_grid(float v) {
     return fabsf(v) < 64.0f && s == rintf(s);
 }
 
+// Tile and rank of every hit.  The warp takes 32 consecutive hits; lanes
+// whose hits fall in the same tile reserve their ranks with one atomic
+// (warp-aggregated: __match_any_sync groups them, the lowest lane adds the
+// group's size and shares the old count).
 __global__ void __launch_bounds__(kThreads) k_bin_count(Params p) {
+    const int lane = threadIdx.x & 31;
     const int stride = gridDim.x * blockDim.x;
-    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < p.n_hits; h += stride) {
-        float x = p.x[h], y = p.y[h], z = p.z[h], r = p.r[h];
-        int m = p.module[h];
-        bool bad = m < 0 || m >= p.n_modules;
-        int L = bad ? 0 : p.module_layer[m];
-        bad = bad || L < 0 || L >= PT_N_LAYERS;
-        bad = bad || !on_grid(x) || !on_grid(y) || !on_grid(z) || !on_grid(r);
-        float tmin = 0.f, tmax = 1.f, t = 0.f;
-        if (!bad) {
-            const pt_layer ly = p.layer[L];
-            bad = r < ly.rmin || r > ly.rmax || z < ly.zmin || z > ly.zmax;
-            if (ly.kind == PT_LAYER_BARREL) {
-                t = z; tmin = ly.zmin; tmax = ly.zmax;
-            } else {
-                t = r; tmin = ly.rmin; tmax = ly.rmax;
+    for (int h0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); h0 < p.n_hits; h0 += stride) {
+        const int h = h0 + lane;
+        int bin = -1;
+        if (h < p.n_hits) {
+            float x = p.x[h], y = p.y[h], z = p.z[h], r = p.r[h];
+            int m = p.module[h];
+            bool bad = m < 0 || m >= p.n_modules;
+            int L = bad ? 0 : p.module_layer[m];
+            bad = bad || L < 0 || L >= PT_N_LAYERS;
+            bad = bad || !on_grid(x) || !on_grid(y) || !on_grid(z) || !on_grid(r);
+            float tmin = 0.f, tmax = 1.f, t = 0.f;
+            if (!bad) {
+                const pt_layer ly = p.layer[L];
+                bad = r < ly.rmin || r > ly.rmax || z < ly.zmin || z > ly.zmax;
+                if (ly.kind == PT_LAYER_BARREL) {
+                    t = z; tmin = ly.zmin; tmax = ly.zmax;
+                } else {
+                    t = r; tmin = ly.rmin; tmax = ly.rmax;
+                }
             }
+            if (bad) {
+                set_flag(p.counters, PT_FLAG_INPUT);
+            } else {
+                // event of hit h: ev_off[e] <= h < ev_off[e+1]
+                int lo = 0, hi = p.n_events - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (__ldg(p.ev_off + mid) <= h) lo = mid; else hi = mid - 1;
+                }
+                int pb = phi_tile(atan2f(y, x), p.n_phi);
+                int tb = t_tile(t, tmin, tmax, p.n_t);
+                bin = ((lo * PT_N_LAYERS + L) * p.n_phi + pb) * p.n_t + tb;
+            }
+            p.hit_bin[h] = bin;
         }
-        if (bad) {
-            set_flag(p.counters, PT_FLAG_INPUT);
-            p.hit_bin[h] = -1;
-            continue;
-        }
-        // event of hit h: ev_off[e] <= h < ev_off[e+1]
-        int lo = 0, hi = p.n_events - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (__ldg(p.ev_off + mid) <= h) lo = mid; else hi = mid - 1;
-        }
-        int pb = phi_tile(atan2f(y, x), p.n_phi);
-        int tb = t_tile(t, tmin, tmax, p.n_t);
-        int bin = ((lo * PT_N_LAYERS + L) * p.n_phi + pb) * p.n_t + tb;
-        p.hit_bin[h] = bin;
-        p.hit_rank[h] = atomicAdd(p.bin_cnt + bin, 1);
+        const unsigned peers = __match_any_sync(0xffffffffu, bin);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader && bin >= 0) base = atomicAdd(p.bin_cnt + bin, __popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (bin >= 0) p.hit_rank[h] = base + __popc(peers & ((1u << lane) - 1u));
     }
 }
 
