@@ -7,9 +7,11 @@ parameters are compared within the tolerance of the float32 path:
   kappa:                        |d| <= 1e-4 |kappa|
   phi0, tan(lambda), d0, z0:    |d| <= 1e-5 max(1, |value|)   (phi0 mod 2 pi)
 covariance diagonal within 1e-3 relative, and chi2 within
-2e-2 sqrt(max(1, chi2)): the float32 arc lengths carry ~1e-6 cm rounding
-(one ulp at 10-20 cm), which moves the s-z residuals by |tan lambda| times
-that, up to ~1e-2 sigma_z, and chi2 by twice that times sqrt(chi2).
+CHI2_TOL sqrt(max(1, chi2)).  The chi2 bound is twice the largest departure
+measured on every track of whole events of all the workloads (3.0e-3, a
+stress event): its source is the float32 rounding of the arc lengths
+(~1e-6 cm at 10-20 cm), which moves the s-z residuals by |tan lambda| times
+that and chi2 by about twice that times sqrt(chi2).
 """
 from __future__ import annotations
 
@@ -21,6 +23,7 @@ from synth import cuts as CU
 from synth import geometry as G
 
 DISK = [0] * 4 + [1] * 6
+CHI2_TOL = 6e-3
 KEYS = ("x", "y", "z", "r", "module", "ev_off")
 
 
@@ -123,7 +126,7 @@ def compare_params(P, CV, X2, ND, WP, WC, WX2, WND):
     assert np.all(rel <= 1e-3), f"cov diag max rel err {rel.max():.3g}"
     rc = np.abs(X2 - WX2) / np.sqrt(np.maximum(1.0, WX2))
     err["chi2_scaled"] = rc
-    assert np.all(rc <= 2e-2), f"chi2 max scaled err {rc.max():.3g}"
+    assert np.all(rc <= CHI2_TOL), f"chi2 max scaled err {rc.max():.3g}"
     return {k: (float(v.max()), float(np.percentile(v, 99))) for k, v in err.items()}
 
 

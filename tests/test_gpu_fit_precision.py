@@ -17,7 +17,7 @@ from synth import cuts as CU
 from synth import events as E
 from synth import geometry as G
 
-from parity import compare_params, to_dev
+from parity import CHI2_TOL, compare_params, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -78,7 +78,7 @@ def _outside(P, CV, X2, WP, WC, WX):
             ok &= np.abs(dd) <= 1e-5 * np.maximum(1.0, np.abs(WP[:, j]))
         diag = [0, 2, 5, 9, 14]
         ok &= (np.abs(CV[:, diag] - WC[:, diag]) <= 1e-3 * np.abs(WC[:, diag])).all(1)
-        ok &= np.abs(X2 - WX) <= 2e-2 * np.sqrt(np.maximum(1.0, WX))
+        ok &= np.abs(X2 - WX) <= CHI2_TOL * np.sqrt(np.maximum(1.0, WX))
     return ~ok
 
 
