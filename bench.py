@@ -166,12 +166,6 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ bytes
-# kernels the pipeline launches per step: binning 5 (count, 3 scan passes,
-# fill), doublets 2 (main, exact pass), Fishbone 4 (small, medium, large,
-# exact pass), connection 2 (main, exact pass), n-tuplets 4 (edge records,
-# search, 2 cleaning), fit 6 (count and selection, one per hit count 3, 4,
-# 5, 6..8)
-KERNELS_PER_STEP = 23
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "dram_traffic_pu200_batch8.md")
 
 
@@ -211,21 +205,24 @@ def _profile_entry(key: str):
     return val if src == kernel_source_hash() and val else None
 
 
-def measured_traffic(stage: str, cells: int):
-    """DRAM bytes of one launch of an ABI call, scaled by cells from the
+def measured_traffic(kernel: str, cells: int):
+    """DRAM bytes of one launch of a kernel, scaled by cells from the
     committed ncu summary; None when the kernels changed since it was taken."""
     per = _profile_entry("traffic_bytes_per_cell")
     if not per:
         return None
     table = dict(kv.split("=") for kv in per)
-    return float(table[stage]) * cells if stage in table else None
+    return float(table[kernel]) * cells if kernel in table else None
 
 
-def measured_fit_flops(tracks: int):
-    """float64 flops of one pt_fit_tracks call (FMA = 2, add, multiply),
-    scaled by tracks from the ncu instruction counts of the summary."""
-    per = _profile_entry("fit_fp64_flops_per_track")
-    return float(per[0]) * tracks if per else None
+def measured_issue(kernel: str):
+    """Warp instructions issued per SM cycle of a kernel (of the 4 the SM's
+    schedulers can issue) from the committed ncu summary, or None."""
+    per = _profile_entry("issue_per_sm_cycle")
+    if not per:
+        return None
+    table = dict(kv.split("=") for kv in per)
+    return float(table[kernel]) if kernel in table else None
 
 
 def measure_alu_peaks(dev, stream):
@@ -252,22 +249,72 @@ def measure_alu_peaks(dev, stream):
     return out
 
 
-def algorithmic_bytes(H, D, E, T, K, nbar):
-    """Bytes each stage must move at least (each input read once, each output
-    written once): binning 20H + 24H; doublets 16H per layer-pair slot
-    (3.4 on average) + 9D (cell) + 8H (per-hit cell range); Fishbone 8D read +
-    1D write; connection 13D + 4E + 4E (edge src, dst); n-tuplets 8E + 8D read
-    + 66T written (hits, cells, n, alive); cleaning 66T; fit 36K + 12 nbar K
-    read + 88K written."""
+# Algorithmic bytes per unit of each step (each input read once, each
+# output written once), with H hits, D cells, E edges, T n-tuplets, K
+# tracks (K_n of them with n hits):
+#   a0 binning      20 H read + 24 H written
+#   a1 doublets     16 H x 3.4 (layer pairs per hit's layer) read + 9 D (cells) + 4 D (incoming lists) written
+#   a2 Fishbone     8 D + 16 H read + 1 D written
+#   a3 connection   8 D + 4 D read + 4 E (neighbour lists) + 1 D written
+#   a4 search       4 E + 8 D read + 36 T written
+#   a5 cleaning     36 T read + 12 T (per-cell maxima) + 1 T written
+#   a6 fit          (36 + 16 n + 84 + 1) K_n
+STAGE_KERNELS = {
+    "a0_binning": ("k_bin_count", "k_scan_reduce", "k_scan_partials", "k_scan_apply", "k_bin_fill"),
+    "a1_doublets": ("k_doublets", "k_doublets_exact"),
+    "a2_fishbone": ("k_fishbone_small", "k_fishbone_medium", "k_fishbone_large", "k_fishbone_exact"),
+    "a3_connect": ("k_connect", "k_connect_exact"),
+    "a4_search": ("k_edge_records", "k_dfs"),
+    "a5_cleaning": ("k_clean_max", "k_clean_keep"),
+    "a6_fit": ("k_count_tracks", "k_select_tracks", "k_fit<3>", "k_fit<4>", "k_fit<5>", "k_fit<6..8>"),
+}
+FB_CLASS_MAX = {"k_fishbone_small": 192, "k_fishbone_medium": 320, "k_fishbone_large": 512}
+
+
+def stage_bytes(H, D, E, T, K_by_n):
     return {
-        "binning": 44 * H,
-        "doublets": 16 * 3.4 * H + 9 * D + 8 * H,
-        "fishbone": 9 * D,
-        "connect": 13 * D + 8 * E,
-        "ntuplets": 8 * E + 8 * D + 66 * T + 66 * T,
-        "fit": 36 * K + 12 * nbar * K + 88 * K,
+        "a0_binning": 44 * H,
+        "a1_doublets": 16 * 3.4 * H + 13 * D,
+        "a2_fishbone": 9 * D + 16 * H,
+        "a3_connect": 13 * D + 4 * E,
+        "a4_search": 4 * E + 8 * D + 36 * T,
+        "a5_cleaning": 49 * T,
+        "a6_fit": sum((121 + 16 * n) * k for n, k in K_by_n.items()),
     }
 
+
+def kernel_bytes(H, D, E, T, K_by_n, fb_cells):
+    """Algorithmic bytes of one launch of each kernel: its stage's bytes
+    for the units it processes.  The main kernel of a stage processes all
+    of its units (its exact pass repeats a few and gets none); the
+    Fishbone's three kernels split the cells by their outer hit's cell count
+    (fb_cells: cells of each kernel); each fit kernel has its tracks."""
+    sb = stage_bytes(H, D, E, T, K_by_n)
+    out = {"k_bin_count": 20 * H, "k_bin_fill": 24 * H, "k_doublets": sb["a1_doublets"],
+           "k_connect": sb["a3_connect"], "k_dfs": sb["a4_search"], "k_clean_max": 36 * T + 12 * T,
+           "k_clean_keep": 36 * T + 1 * T}
+    for k, c in fb_cells.items():
+        out[k] = sb["a2_fishbone"] * (c / D if D else 0.0)
+    names = {3: "k_fit<3>", 4: "k_fit<4>", 5: "k_fit<5>"}
+    for n, k in K_by_n.items():
+        name = names.get(n, "k_fit<6..8>")
+        out[name] = out.get(name, 0.0) + (121 + 16 * n) * k
+    return out
+
+
+def fit_flops_per_track(n: int) -> float:
+    """Floating-point operations of the broken-line fit of one n-hit track,
+    counted on the method as written (dense algebra): the s-z line system
+    (n unknowns, 3-point slope kinks) and the circle system (n offsets plus
+    the curvature correction, 4-term kinks), each assembled (2 flops per
+    measurement, 2 per entry of each kink's outer product), factorised by
+    Cholesky (m^3/3 + m^2/2) and solved forward and back (2 m^2 each), plus
+    the pre-fit circle and the arc lengths and offsets of the hits (~30 +
+    20 n)."""
+    total = 30.0 + 20.0 * n
+    for m, kink in ((n, 3), (n + 1, 4)):
+        total += 2 * n + 2 * kink * kink * max(0, n - 2) + m ** 3 / 3.0 + m * m / 2.0 + 4.0 * m * m
+    return total
 
 
 class Ctx:
@@ -557,12 +604,17 @@ def run_native(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    # per-kernel CUDA events around every launch of the library, on the
+    # launching stream, over the timed steps (pt_kernel_timing)
+    L.kernel_timing(True)
     for k in range(args.steps):
         flush.zero_()
         step(evs[k])
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    kt = L.kernel_timing_read()
+    L.kernel_timing(False)
     clk = clocks.stop() if clocks else None
     step_ms = [e[0].elapsed_time(e[4]) for e in evs]
     stage_ms = [statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i in range(4)]
@@ -579,27 +631,66 @@ def run_native(args, rank, world, local_rank):
         if rank == 0:
             per_event_s = measure_per_event(ctx, batch)
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel (the one with the most time in the
+    # timed steps), per launch, from the per-kernel events
     H, D, Ed, T, K = bufs.n_hits, counts.n_cells, counts.n_edges, counts.n_tuples, counts.n_tracks
-    n = res.tuples["n"].cpu().numpy()
-    nbar = float(n[res.tracks["tuple"].cpu().numpy()].mean()) if K else 0.0
-    ab = algorithmic_bytes(H, D, Ed, T, K, nbar)
-    stage_bytes = [ab["binning"] + ab["doublets"] + ab["fishbone"], ab["connect"], ab["ntuplets"], ab["fit"]]
-    stage_names = ["build_doublets", "connect_cells", "find_ntuplets", "fit_tracks"]
-    dom = max(range(4), key=lambda i: stage_ms[i])
+    n_t = res.tuples["n"].long()
+    n_of_track = n_t[res.tracks["tuple"].long()].cpu().numpy() if K else np.zeros(0, int)
+    K_by_n = {int(v): int((n_of_track == v).sum()) for v in np.unique(n_of_track)}
+    # cells per Fishbone kernel: by their outer hit's cell count
+    per_outer = torch.bincount(res.cells["outer"].long(), minlength=H)
+    fb_cells, lo = {}, 0
+    for name, hi in FB_CLASS_MAX.items():
+        fb_cells[name] = int(per_outer[(per_outer > lo) & (per_outer <= hi)].sum().item())
+        lo = hi
+    kb = kernel_bytes(H, D, Ed, T, K_by_n, fb_cells)
     peak, peak_kind = _peaks()
-    achieved = stage_bytes[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    total_kernel_ms = sum(ms for _, ms in kt.values())
+    kernels = {}
+    for name, (launches, ms) in sorted(kt.items(), key=lambda kv: -kv[1][1]):
+        per_launch = ms / launches
+        e = {"launches": launches, "ms_per_launch": per_launch, "share": ms / total_kernel_ms}
+        if name in kb and kb[name] > 0:
+            e["algorithmic_bytes"] = kb[name]
+            e["gbs"] = kb[name] / (per_launch * 1e-3) / 1e9
+            e["frac"] = e["gbs"] / peak
+        kernels[name] = e
+    dom = max(kt, key=lambda k: kt[k][1])
+    dom_ms = kt[dom][1] / kt[dom][0]
+    dom_bytes = kb.get(dom)
+    sb = stage_bytes(H, D, Ed, T, K_by_n)
+    stages = {}
+    for st_name, names in STAGE_KERNELS.items():
+        ms = sum(kt[k][1] / kt[k][0] for k in names if k in kt)
+        stages[st_name] = {"ms": ms, "algorithmic_bytes": sb[st_name],
+                           "frac": sb[st_name] / (ms * 1e-3) / 1e9 / peak if ms > 0 else None}
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": (dom_bytes / (dom_ms * 1e-3) / 1e9) if dom_bytes else None,
+                "peak": peak, "unit": "GB/s", "peak_source": peak_kind, "launch_ms": dom_ms,
+                "algorithmic_bytes": dom_bytes, "traffic": measured_traffic(dom, D),
+                "traffic_source": "profiles/dram_traffic_pu200_batch8.md (ncu, 8 events), scaled by cells",
+                "issue_per_sm_cycle": measured_issue(dom),
+                "timing": "CUDA events around each launch on the launching stream, over the timed steps"}
+    roofline["frac"] = roofline["achieved"] / peak if roofline["achieved"] else None
 
     # the fit is bound by the float64 pipe: its arithmetic roofline
     alu = measure_alu_peaks(dev, stream)
-    fit_flops = measured_fit_flops(K)
-    fit_roofline = {"bound": "alu", "kernel": "fit_tracks", "unit": "TFLOP/s", "precision": "f64",
+    fit_flops = sum(fit_flops_per_track(n) * k for n, k in K_by_n.items())
+    fit_ms = sum(kt[k][1] / kt[k][0] for k in ("k_fit<3>", "k_fit<4>", "k_fit<5>", "k_fit<6..8>") if k in kt)
+    fit_roofline = {"bound": "alu", "kernel": "k_fit<3..8>", "unit": "TFLOP/s", "precision": "f64",
                     "peak": alu["fp64_tflops"], "peak_source": alu["method"], "fp32_peak": alu["fp32_tflops"],
-                    "algorithmic_flops": fit_flops,
-                    "flops_source": "ncu float64 instruction counts, profiles/dram_traffic_pu200_batch8.md"}
-    if fit_flops is not None:
-        fit_roofline["achieved"] = fit_flops / (stage_ms[3] * 1e-3) / 1e12
+                    "algorithmic_flops": fit_flops, "ms": fit_ms,
+                    "flops_source": "the method's dense-algebra count per track (bench.fit_flops_per_track)"}
+    if fit_ms > 0:
+        fit_roofline["achieved"] = fit_flops / (fit_ms * 1e-3) / 1e12
         fit_roofline["frac"] = fit_roofline["achieved"] / alu["fp64_tflops"]
+
+    # the doublet search's candidates per accepted cell, per layer pair
+    cand = L.doublet_candidates(ws, nb, h, cfg, s)
+    acc = torch.bincount(res.cells["pair"].long(), minlength=len(cand)).cpu().numpy()
+    cuts = CU.cuts_for("pu200-batch64")
+    cand_pairs = {f"{pp['inner']}-{pp['outer']}": {"candidates": int(cand[i]), "cells": int(acc[i]),
+                                                   "per_cell": cand[i] / max(1, int(acc[i]))}
+                  for i, pp in enumerate(cuts["pairs"])}
 
     if rank != 0:
         return None
@@ -640,8 +731,11 @@ def run_native(args, rank, world, local_rank):
         "tracks_per_s": K * world / (ms_per_step * 1e-3),
         "counts_per_step": {"hits": H, "cells": D, "alive_cells": counts.n_alive_cells, "edges": Ed,
                             "ntuplets": T, "alive_ntuplets": counts.n_alive_tuples, "tracks": K,
-                            "exact_fallbacks": counts.n_exact_fallbacks},
-        "stage_ms": dict(zip(stage_names, stage_ms)),
+                            "tracks_by_hits": K_by_n, "exact_fallbacks": counts.n_exact_fallbacks,
+                            "doublet_candidates": counts.n_doublet_candidates,
+                            "doublet_candidates_per_cell": counts.n_doublet_candidates / max(1, D),
+                            "doublet_candidates_by_pair": cand_pairs},
+        "stage_ms": dict(zip(("build_doublets", "connect_cells", "find_ntuplets", "fit_tracks"), stage_ms)),
         "graph_ms_per_step": graph_ms,
         "graph_events_per_s": (n_ev / (graph_ms * 1e-3)) if isinstance(graph_ms, float) else graph_ms,
         "per_event_form": per_event_s if isinstance(per_event_s, str) else {
@@ -651,12 +745,11 @@ def run_native(args, rank, world, local_rank):
         "differentiable_form": diff_form,
         "ambiguity_resolution": getattr(ctx, "ambiguity", "skipped"),
         "vertexing": getattr(ctx, "vertexing", "skipped"),
-        "roofline": {"bound": "hbm", "kernel": stage_names[dom], "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                     "algorithmic_bytes": stage_bytes[dom], "traffic": measured_traffic(stage_names[dom], D),
-                     "traffic_source": "profiles/dram_traffic_pu200_batch8.md, scaled by cells"},
+        "roofline": roofline,
+        "kernels": kernels,
+        "stage_roofline": stages,
         "fit_roofline": fit_roofline,
-        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "gpu_launches": sum(v[0] for v in kt.values()),
         "clocks": clk,
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all,

@@ -22,8 +22,9 @@
  *   pt_resolve_ambiguities  Sec. 3.5 (post-fit ambiguity resolution);
  *   pt_track_summary, pt_find_vertices  Sec. 3.6 (pixel vertices);
  *   pt_bin_hits_noalloc the binning step without a caller workspace;
- *   pt_fma_probe       a measurement helper (arithmetic peaks), not part of
- *                      the method.
+ *   pt_fma_probe, pt_doublet_candidates, pt_kernel_timing[_read]
+ *                      measurement aids (arithmetic peaks, search work,
+ *                      per-kernel times), not part of the method.
  *
  * Conventions shared by every call
  * --------------------------------
@@ -221,6 +222,8 @@ typedef struct {
     int64_t n_cells, n_edges, n_tuples, n_tracks; /* counts produced (or needed) */
     int64_t n_alive_cells, n_alive_tuples;
     int64_t n_exact_fallbacks;                    /* predicates decided exactly */
+    int64_t n_doublet_candidates;                 /* inner hits the doublet search tested
+                                                     (all layer pairs; see pt_doublet_candidates) */
     uint32_t flags;                               /* PT_FLAG_* */
 } pt_counts;
 
@@ -386,6 +389,35 @@ pt_status pt_fma_probe(int32_t fp64, int32_t iters, int32_t n_threads, void *out
  * PT_ERR_CAPACITY or PT_ERR_INPUT when the corresponding flags are set. */
 pt_status pt_read_counts(const void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg,
                          pt_counts *out, void *stream);
+
+/* Measurement aid, not part of the method: synchronises `stream`, then
+ * writes to per_pair[PT_MAX_PAIRS] (host) how many candidate inner hits the
+ * doublet search of the last pt_build_doublets on ws tested for each layer
+ * pair (cfg->cuts.pair order; the rest 0): the hits of the tiles its search
+ * window covered, every one of which the Table 1 cuts were evaluated on.
+ * Their sum is pt_counts.n_doublet_candidates. */
+pt_status pt_doublet_candidates(const void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg,
+                                int64_t *per_pair, void *stream);
+
+/* Kernel timing (measurement aid, not part of the method).  While enabled,
+ * every kernel this library launches on a stream that is not being captured
+ * is bracketed by two CUDA events on that stream; pt_kernel_timing_read
+ * waits for them and accumulates, per kernel name, the launches and their
+ * total duration (ms).  pt_kernel_timing(1) clears the totals and starts
+ * recording, pt_kernel_timing(0) stops it.  Host-side cost: two event
+ * records per launch.  Not for use while another host thread launches
+ * kernels of this library and reads the totals at the same time. */
+typedef struct {
+    char name[48];          /* kernel name, NUL-terminated */
+    int64_t launches;
+    double total_ms;
+} pt_kernel_time;
+
+pt_status pt_kernel_timing(int32_t enable);
+
+/* Waits for the recorded launches and returns how many kernels have
+ * totals; writes up to max_entries of them to out (host). */
+int32_t pt_kernel_timing_read(pt_kernel_time *out, int32_t max_entries);
 
 /* Device pointer (inside ws) to int32[n_hits]: binned position -> input hit
  * index, valid after pt_build_doublets. */

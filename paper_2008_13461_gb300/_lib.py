@@ -109,7 +109,11 @@ PT_VTX_EVENT_TOO_LARGE, PT_VTX_TOO_MANY, PT_VTX_INTERNAL = 1, 2, 4
 class Counts(C.Structure):
     _fields_ = [("n_cells", C.c_int64), ("n_edges", C.c_int64), ("n_tuples", C.c_int64),
                 ("n_tracks", C.c_int64), ("n_alive_cells", C.c_int64), ("n_alive_tuples", C.c_int64),
-                ("n_exact_fallbacks", C.c_int64), ("flags", C.c_uint32)]
+                ("n_exact_fallbacks", C.c_int64), ("n_doublet_candidates", C.c_int64), ("flags", C.c_uint32)]
+
+
+class KernelTime(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
 
 # every symbol declared in include/pt.h
@@ -117,7 +121,8 @@ EXPORTS = ("pt_workspace_size", "pt_build_doublets", "pt_connect_cells", "pt_fin
            "pt_fit_tracks", "pt_fit_tracks_grad", "pt_align_hits", "pt_align_hits_grad",
            "pt_resolve_ambiguities", "pt_track_summary", "pt_vertex_scratch_size", "pt_find_vertices",
            "pt_fma_probe", "pt_read_counts",
-           "pt_hit_order", "pt_status_string", "pt_bin_hits_noalloc")
+           "pt_hit_order", "pt_status_string", "pt_bin_hits_noalloc", "pt_doublet_candidates",
+           "pt_kernel_timing", "pt_kernel_timing_read")
 
 _lib = None
 
@@ -172,6 +177,12 @@ def lib(build_if_missing: bool = True):
     L.pt_bin_hits_noalloc.restype = C.c_int
     L.pt_bin_hits_noalloc.argtypes = [P(Hits), P(Geometry), C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p]
+    L.pt_doublet_candidates.restype = C.c_int
+    L.pt_doublet_candidates.argtypes = common + [P(C.c_int64), C.c_void_p]
+    L.pt_kernel_timing.restype = C.c_int
+    L.pt_kernel_timing.argtypes = [C.c_int32]
+    L.pt_kernel_timing_read.restype = C.c_int32
+    L.pt_kernel_timing_read.argtypes = [P(KernelTime), C.c_int32]
     _lib = L
     return L
 
@@ -268,3 +279,25 @@ def bin_hits_noalloc(hits, geometry, n_phi_bins, n_t_bins, binned, hit_order_out
     """Allocation-free binning (see pt_bin_hits_noalloc in pt.h)."""
     check(lib().pt_bin_hits_noalloc(C.byref(hits), C.byref(geometry), n_phi_bins, n_t_bins, binned, hit_order_out,
                                     tile_off, flags, stream), "pt_bin_hits_noalloc")
+
+
+def doublet_candidates(ws, ws_bytes, hits, cfg, stream) -> list[int]:
+    """Candidate inner hits tested per layer pair by the last doublet search
+    (pt_doublet_candidates; synchronises the stream)."""
+    out = (C.c_int64 * MAX_PAIRS)()
+    check(lib().pt_doublet_candidates(ws, ws_bytes, C.byref(hits), C.byref(cfg), out, stream),
+          "pt_doublet_candidates")
+    return list(out)
+
+
+def kernel_timing(enable: bool) -> None:
+    """Start (clearing the totals) or stop per-kernel timing (pt_kernel_timing)."""
+    check(lib().pt_kernel_timing(1 if enable else 0), "pt_kernel_timing")
+
+
+def kernel_timing_read() -> dict:
+    """{kernel name: (launches, total ms)} of the launches timed so far."""
+    n = lib().pt_kernel_timing_read(None, 0)
+    buf = (KernelTime * max(1, n))()
+    n = lib().pt_kernel_timing_read(buf, n)
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(n)}

@@ -19,7 +19,7 @@ LIB = os.path.join(OUT_DIR, "libpt_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["pt_bin.cu", "pt_doublets.cu", "pt_fishbone.cu", "pt_connect.cu", "pt_ntuplets.cu", "pt_fit.cu",
            "pt_fit_grad.cu", "pt_postfit.cu", "pt_vertex.cu", "pt_probe.cu", "pt_abi.cu",
-           "pt_noalloc.cu"]
+           "pt_noalloc.cu", "pt_timing.cu"]
 
 
 def nvcc() -> str:

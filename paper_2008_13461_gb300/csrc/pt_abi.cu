@@ -224,6 +224,13 @@ int grid_for(const pt_config *cfg) {
 
 pt_status launched() { return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ERR_CUDA; }
 
+// the 64-bit candidate counter of layer pair k in a host copy of the counters
+int64_t pair_candidates(const int32_t *c, int k) {
+    uint64_t v;
+    memcpy(&v, c + C_PAIR_CAND + 2 * k, sizeof v);
+    return (int64_t)v;
+}
+
 }  // namespace
 
 extern "C" {
@@ -458,9 +465,25 @@ pt_status pt_read_counts(const void *ws, size_t ws_bytes, const pt_hits *hits, c
     out->n_alive_cells = (uint32_t)c[C_ALIVE_CELLS];
     out->n_alive_tuples = (uint32_t)c[C_ALIVE_TUPLES];
     out->n_exact_fallbacks = (uint32_t)c[C_FALLBACK];
+    int64_t cand = 0;
+    for (int k = 0; k < PT_MAX_PAIRS; k++) cand += pair_candidates(c, k);
+    out->n_doublet_candidates = cand;
     out->flags = (uint32_t)c[C_FLAGS];
     if (out->flags & PT_FLAG_INPUT) return PT_ERR_INPUT;
     if (out->flags & (PT_FLAG_CELLS | PT_FLAG_EDGES | PT_FLAG_TUPLES | PT_FLAG_TRACKS)) return PT_ERR_CAPACITY;
+    return PT_OK;
+}
+
+pt_status pt_doublet_candidates(const void *ws, size_t ws_bytes, const pt_hits *hits, const pt_config *cfg,
+                                int64_t *per_pair, void *stream) {
+    WsLayout L;
+    if (!ws || !per_pair || !layout(hits, cfg, L) || ws_bytes < L.total) return PT_ERR_INVALID_ARG;
+    int32_t c[kCounters];
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(c, (const char *)ws + L.counters, sizeof c, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PT_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PT_ERR_CUDA;
+    for (int k = 0; k < PT_MAX_PAIRS; k++) per_pair[k] = pair_candidates(c, k);
     return PT_OK;
 }
 

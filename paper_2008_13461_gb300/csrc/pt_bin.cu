@@ -147,9 +147,18 @@ __global__ void __launch_bounds__(kThreads) k_scan_apply(int32_t *a, int64_t n, 
 
 void launch_scan(int32_t *a, int64_t n, int32_t *part, cudaStream_t s) {
     const int nb = (int)((n + kScanItems - 1) / kScanItems);
-    if (nb > 0) k_scan_reduce<<<nb, kThreads, 0, s>>>(a, n, part);
-    k_scan_partials<<<1, kThreads, 0, s>>>(part, nb, a + n);
-    if (nb > 0) k_scan_apply<<<nb, kThreads, 0, s>>>(a, n, part);
+    if (nb > 0) {
+        KernelTimer t("k_scan_reduce", s);
+        k_scan_reduce<<<nb, kThreads, 0, s>>>(a, n, part);
+    }
+    {
+        KernelTimer t("k_scan_partials", s);
+        k_scan_partials<<<1, kThreads, 0, s>>>(part, nb, a + n);
+    }
+    if (nb > 0) {
+        KernelTimer t("k_scan_apply", s);
+        k_scan_apply<<<nb, kThreads, 0, s>>>(a, n, part);
+    }
 }
 
 __global__ void __launch_bounds__(kThreads) k_bin_fill(Params p) {
@@ -167,8 +176,12 @@ __global__ void __launch_bounds__(kThreads) k_bin_fill(Params p) {
 }
 
 void launch_binning(const Params &p, int grid, cudaStream_t s) {
-    k_bin_count<<<grid, kThreads, 0, s>>>(p);
+    {
+        KernelTimer t("k_bin_count", s);
+        k_bin_count<<<grid, kThreads, 0, s>>>(p);
+    }
     launch_scan(p.bin_cnt, p.n_bins, p.scan_part, s);
+    KernelTimer t("k_bin_fill", s);
     k_bin_fill<<<grid, kThreads, 0, s>>>(p);
 }
 

@@ -12,7 +12,7 @@ namespace ptk {
 
 constexpr int kThreads = 256;            // threads per block of every kernel
 constexpr int kMaxPairsPerLayer = 8;
-constexpr int kCounters = 32;
+constexpr int kCounters = 32 + 2 * PT_MAX_PAIRS;
 
 // workspace counters (int32 slots at the start of ws)
 enum Counter {
@@ -27,7 +27,8 @@ enum Counter {
     C_TRK_CNT = 16,       // tracks with 3, 4, 5, 6..8 hits (4 slots)
     C_TRK_CUR = 20,       // next track index of each of those classes (4 slots)
     C_FB_HUGE = 24,       // Fishbone: outer hits listed for the largest warps
-    C_FB_HUGE_NEXT = 25   // Fishbone: next of those to take
+    C_FB_HUGE_NEXT = 25,  // Fishbone: next of those to take
+    C_PAIR_CAND = 32      // doublet candidates per layer pair (64-bit, PT_MAX_PAIRS of them)
 };
 
 // class of a track by its hit count: 3, 4, 5, 6..8 -> 0..3

@@ -285,7 +285,11 @@ __global__ void __launch_bounds__(128) k_connect_exact(Params p) {
 }
 
 void launch_connect(const Params &p, int grid, cudaStream_t s) {
-    k_connect<<<grid * (kThreads / (32 * kCaWarps)), 32 * kCaWarps, 0, s>>>(p);
+    {
+        KernelTimer t("k_connect", s);
+        k_connect<<<grid * (kThreads / (32 * kCaWarps)), 32 * kCaWarps, 0, s>>>(p);
+    }
+    KernelTimer t("k_connect_exact", s);
     k_connect_exact<<<grid / 8 + 1, 128, 0, s>>>(p);
 }
 

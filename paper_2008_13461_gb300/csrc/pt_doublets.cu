@@ -50,10 +50,12 @@ __device__ __forceinline__ void t_window(const Params &p, const pt_pair_cuts &pc
 // group's shared buffer (up to cap entries) and count; kWrite = true: write
 // cells directly at global index base + slot.  kExact = false: the
 // predicates are float32 filters only, and *undecided is set on the lanes
-// that met a candidate they cannot decide.
+// that met a candidate they cannot decide.  s_cand (or null): per-pair
+// counts of the candidate inner hits tested, summed in shared memory.
 template <int G, bool kWrite, bool kExact>
 __device__ int sweep_outer(const Params &p, int o, int lane, unsigned gmask, int gshift, int32_t *s_inner,
-                           uint8_t *s_pair, int cap, int64_t base, bool *undecided) {
+                           uint8_t *s_pair, int cap, int64_t base, bool *undecided,
+                           unsigned long long *s_cand = nullptr) {
     const float4 ho = __ldg(p.bh + o);
     const float xo = ho.x, yo = ho.y, zo = ho.z, ro = ho.w;
     const int Lo = p.blayer[o], ev = p.bev[o];
@@ -88,10 +90,12 @@ __device__ int sweep_outer(const Params &p, int o, int lane, unsigned gmask, int
             f1 = p.n_phi - 1;
         }
         const int row0 = (ev * PT_N_LAYERS + pc.inner) * p.n_phi;
+        unsigned cand = 0;
         for (int f = f0; f <= f1; f++) {
             const int fb = ((f % p.n_phi) + p.n_phi) % p.n_phi;
             const int tile = (row0 + fb) * p.n_t;
             const int beg = p.bin_cnt[tile + tb0], end = p.bin_cnt[tile + tb1 + 1];
+            cand += (unsigned)(end - beg);
             for (int i0 = beg; i0 < end; i0 += G) {
                 const int i = i0 + lane;
                 int v = 0;     // 1 accepted, 0 rejected, 2|3 undecided (kExact = false)
@@ -132,6 +136,7 @@ __device__ int sweep_outer(const Params &p, int o, int lane, unsigned gmask, int
                 count += __popc(m);
             }
         }
+        if (s_cand && lane == 0 && cand) atomicAdd(s_cand + pi, (unsigned long long)cand);
     }
     return count;
 }
@@ -140,9 +145,10 @@ __device__ int sweep_outer(const Params &p, int o, int lane, unsigned gmask, int
 // false without writing anything when a candidate is undecided.
 template <int G, bool kExact>
 __device__ __forceinline__ bool doublets_hit(const Params &p, int o, int lane, unsigned gmask, int gshift,
-                                             int32_t *s_inner, uint8_t *s_pair, int cap) {
+                                             int32_t *s_inner, uint8_t *s_pair, int cap,
+                                             unsigned long long *s_cand = nullptr) {
     bool und = false;
-    const int n = sweep_outer<G, false, kExact>(p, o, lane, gmask, gshift, s_inner, s_pair, cap, 0, &und);
+    const int n = sweep_outer<G, false, kExact>(p, o, lane, gmask, gshift, s_inner, s_pair, cap, 0, &und, s_cand);
     if (!kExact && __ballot_sync(gmask, und)) return false;
     int64_t base = 0;
     if (lane == 0 && n > 0) base = atomicAdd(p.counters + C_CELLS, n);
@@ -173,23 +179,31 @@ __device__ __forceinline__ bool doublets_hit(const Params &p, int o, int lane, u
 
 // Main pass: float32 filters only (no big-integer code, so far fewer
 // registers); an outer hit with an undecided candidate (about one in 10^3)
-// is listed for the exact pass.
+// is listed for the exact pass.  It also counts the candidates tested per
+// layer pair (the exact pass repeats a few of them and does not count).
 template <int G>
 __global__ void __launch_bounds__(kThreads, 5) k_doublets(Params p) {
     constexpr int kGroups = kThreads / G;
     constexpr int kBuf = 32 * G;   // 40 KB of shared memory per block for every G
     __shared__ int32_t s_inner[kGroups][kBuf];
     __shared__ uint8_t s_pair[kGroups][kBuf];
+    __shared__ unsigned long long s_cand[PT_MAX_PAIRS];
+    if (threadIdx.x < PT_MAX_PAIRS) s_cand[threadIdx.x] = 0;
+    __syncthreads();
     const int lane = threadIdx.x % G, grp = threadIdx.x / G;
     const int gshift = (threadIdx.x & 31) & ~(G - 1);
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << gshift);
     const int n_binned = p.bin_cnt[p.n_bins];
     for (int o = blockIdx.x * kGroups + grp; o < n_binned; o += gridDim.x * kGroups) {
-        if (!doublets_hit<G, false>(p, o, lane, gmask, gshift, s_inner[grp], s_pair[grp], kBuf) && lane == 0) {
+        if (!doublets_hit<G, false>(p, o, lane, gmask, gshift, s_inner[grp], s_pair[grp], kBuf, s_cand) &&
+            lane == 0) {
             // listed in hit_bin, free once the hits are binned (one slot per hit)
             p.hit_bin[atomicAdd(p.counters + C_DB_PENDING, 1)] = o;
         }
     }
+    __syncthreads();
+    if (threadIdx.x < p.n_pairs && s_cand[threadIdx.x])
+        atomicAdd(reinterpret_cast<unsigned long long *>(p.counters + C_PAIR_CAND) + threadIdx.x, s_cand[threadIdx.x]);
 }
 
 // Exact pass over the listed outer hits.
@@ -206,12 +220,16 @@ __global__ void __launch_bounds__(kThreads) k_doublets_exact(Params p) {
 }
 
 void launch_doublets(const Params &p, int lanes, int grid, cudaStream_t s) {
-    switch (lanes) {
-    case 4: k_doublets<4><<<grid, kThreads, 0, s>>>(p); break;
-    case 8: k_doublets<8><<<grid, kThreads, 0, s>>>(p); break;
-    case 16: k_doublets<16><<<grid, kThreads, 0, s>>>(p); break;
-    default: k_doublets<32><<<grid, kThreads, 0, s>>>(p); break;
+    {
+        KernelTimer t("k_doublets", s);
+        switch (lanes) {
+        case 4: k_doublets<4><<<grid, kThreads, 0, s>>>(p); break;
+        case 8: k_doublets<8><<<grid, kThreads, 0, s>>>(p); break;
+        case 16: k_doublets<16><<<grid, kThreads, 0, s>>>(p); break;
+        default: k_doublets<32><<<grid, kThreads, 0, s>>>(p); break;
+        }
     }
+    KernelTimer t("k_doublets_exact", s);
     k_doublets_exact<<<grid / 4 + 1, kThreads, 0, s>>>(p);
 }
 

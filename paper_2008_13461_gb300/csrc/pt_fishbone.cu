@@ -451,9 +451,19 @@ __global__ void __launch_bounds__(32 * W) k_fishbone_exact(Params p, float unit_
 }
 
 void launch_fishbone(const Params &p, float unit_thr, float du, int grid, cudaStream_t s) {
-    k_fishbone_small<8, kFbSmallMax, 256, 4><<<grid, 256, 0, s>>>(p, unit_thr, du);
-    k_fishbone_large<4, kFbMidMax, 512, false, false><<<grid, 128, 0, s>>>(p, unit_thr, du);
-    k_fishbone_large<2, 512, 1024, true, true><<<grid / 4 + 1, 64, 0, s>>>(p, unit_thr, du);
+    {
+        KernelTimer t("k_fishbone_small", s);
+        k_fishbone_small<8, kFbSmallMax, 256, 4><<<grid, 256, 0, s>>>(p, unit_thr, du);
+    }
+    {
+        KernelTimer t("k_fishbone_medium", s);
+        k_fishbone_large<4, kFbMidMax, 512, false, false><<<grid, 128, 0, s>>>(p, unit_thr, du);
+    }
+    {
+        KernelTimer t("k_fishbone_large", s);
+        k_fishbone_large<2, 512, 1024, true, true><<<grid / 4 + 1, 64, 0, s>>>(p, unit_thr, du);
+    }
+    KernelTimer t("k_fishbone_exact", s);
     k_fishbone_exact<2, 512, 1024><<<grid / 8 + 1, 64, 0, s>>>(p, unit_thr, du);
 }
 

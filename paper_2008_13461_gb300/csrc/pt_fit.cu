@@ -443,9 +443,19 @@ __global__ void __launch_bounds__(kThreads) k_fit(Params p) {
 
 template <typename R>
 void launch_fit_r(const Params &p, int grid, cudaStream_t s) {
-    k_fit<3, R><<<grid, kThreads, 0, s>>>(p);
-    k_fit<4, R><<<grid, kThreads, 0, s>>>(p);
-    k_fit<5, R><<<grid, kThreads, 0, s>>>(p);
+    {
+        KernelTimer t("k_fit<3>", s);
+        k_fit<3, R><<<grid, kThreads, 0, s>>>(p);
+    }
+    {
+        KernelTimer t("k_fit<4>", s);
+        k_fit<4, R><<<grid, kThreads, 0, s>>>(p);
+    }
+    {
+        KernelTimer t("k_fit<5>", s);
+        k_fit<5, R><<<grid, kThreads, 0, s>>>(p);
+    }
+    KernelTimer t("k_fit<6..8>", s);
     k_fit<6, R><<<grid, kThreads, 0, s>>>(p);
 }
 

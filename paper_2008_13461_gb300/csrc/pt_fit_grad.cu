@@ -616,20 +616,32 @@ __global__ void __launch_bounds__(kThreads) k_align_grad(int n, const float *x, 
 
 void launch_fit_grad(const Params &p, const float *gpar, const float *gchi, float *gx, float *gy, float *gz, int grid,
                      cudaStream_t s) {
-    k_fit_grad<3><<<grid, 128, 0, s>>>(p, gpar, gchi, gx, gy, gz);
-    k_fit_grad<4><<<grid, 128, 0, s>>>(p, gpar, gchi, gx, gy, gz);
-    k_fit_grad<5><<<grid, 128, 0, s>>>(p, gpar, gchi, gx, gy, gz);
+    {
+        KernelTimer t("k_fit_grad<3>", s);
+        k_fit_grad<3><<<grid, 128, 0, s>>>(p, gpar, gchi, gx, gy, gz);
+    }
+    {
+        KernelTimer t("k_fit_grad<4>", s);
+        k_fit_grad<4><<<grid, 128, 0, s>>>(p, gpar, gchi, gx, gy, gz);
+    }
+    {
+        KernelTimer t("k_fit_grad<5>", s);
+        k_fit_grad<5><<<grid, 128, 0, s>>>(p, gpar, gchi, gx, gy, gz);
+    }
+    KernelTimer t("k_fit_grad<6..8>", s);
     k_fit_grad<6><<<grid, 128, 0, s>>>(p, gpar, gchi, gx, gy, gz);
 }
 
 void launch_align(int n, const float *x, const float *y, const float *z, const int32_t *module, const float *centre,
                   const float *shift, const float *rot, float *xo, float *yo, float *zo, int grid, cudaStream_t s) {
+    KernelTimer t("k_align", s);
     k_align<<<grid, kThreads, 0, s>>>(n, x, y, z, module, centre, shift, rot, xo, yo, zo);
 }
 
 void launch_align_grad(int n, const float *x, const float *y, const float *z, const int32_t *module,
                        const float *centre, const float *rot, const float *gxa, const float *gya, const float *gza,
                        float *gx, float *gy, float *gz, float *gshift, float *grot, int grid, cudaStream_t s) {
+    KernelTimer t("k_align_grad", s);
     k_align_grad<<<grid, kThreads, 0, s>>>(n, x, y, z, module, centre, rot, gxa, gya, gza, gx, gy, gz, gshift, grot);
 }
 

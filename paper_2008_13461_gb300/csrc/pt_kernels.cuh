@@ -5,6 +5,22 @@
 
 namespace ptk {
 
+// Brackets the kernel launches of its scope with two CUDA events on the
+// stream while kernel timing is enabled (pt_kernel_timing); does nothing
+// otherwise or while the stream is being captured.
+class KernelTimer {
+  public:
+    KernelTimer(const char *name, cudaStream_t s);
+    ~KernelTimer();
+    KernelTimer(const KernelTimer &) = delete;
+    KernelTimer &operator=(const KernelTimer &) = delete;
+
+  private:
+    const char *name_;
+    cudaStream_t s_;
+    cudaEvent_t a_;
+};
+
 void launch_scan(int32_t *a, int64_t n, int32_t *part, cudaStream_t s);
 void launch_binning(const Params &p, int grid, cudaStream_t s);
 void launch_doublets(const Params &p, int lanes, int grid, cudaStream_t s);

@@ -220,14 +220,28 @@ __global__ void __launch_bounds__(kThreads) k_select_tracks(Params p) {
 
 void launch_select(const Params &p, int grid, cudaStream_t s) {
     (void)grid;
-    k_count_tracks<<<kSelBlocks, kThreads, 0, s>>>(p);
+    {
+        KernelTimer t("k_count_tracks", s);
+        k_count_tracks<<<kSelBlocks, kThreads, 0, s>>>(p);
+    }
+    KernelTimer t("k_select_tracks", s);
     k_select_tracks<<<kSelBlocks, kThreads, 0, s>>>(p);
 }
 
 void launch_ntuplets(const Params &p, int grid, cudaStream_t s) {
-    k_edge_records<<<grid, kThreads, 0, s>>>(p);
-    k_dfs<<<grid, kThreads, 0, s>>>(p);
-    k_clean_max<<<grid, kThreads, 0, s>>>(p);
+    {
+        KernelTimer t("k_edge_records", s);
+        k_edge_records<<<grid, kThreads, 0, s>>>(p);
+    }
+    {
+        KernelTimer t("k_dfs", s);
+        k_dfs<<<grid, kThreads, 0, s>>>(p);
+    }
+    {
+        KernelTimer t("k_clean_max", s);
+        k_clean_max<<<grid, kThreads, 0, s>>>(p);
+    }
+    KernelTimer t("k_clean_keep", s);
     k_clean_keep<<<grid, kThreads, 0, s>>>(p);
 }
 

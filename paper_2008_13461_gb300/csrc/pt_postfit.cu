@@ -80,8 +80,15 @@ void launch_ambiguities(const int32_t *hits, const int32_t *cells, const uint8_t
                         int32_t n_hits, uint32_t *scratch, uint8_t *keep, int grid, cudaStream_t s) {
     AmbArgs a{hits, cells, track_tuple, n, chi2, tip, tip_stride, n_tracks, n_cells, n_hits,
               scratch, scratch + n_cells, keep};
-    k_amb_cells<<<grid, kThreads, 0, s>>>(a);
-    k_amb_hits<<<grid, kThreads, 0, s>>>(a);
+    {
+        KernelTimer t("k_amb_cells", s);
+        k_amb_cells<<<grid, kThreads, 0, s>>>(a);
+    }
+    {
+        KernelTimer t("k_amb_hits", s);
+        k_amb_hits<<<grid, kThreads, 0, s>>>(a);
+    }
+    KernelTimer t("k_amb_final", s);
     k_amb_final<<<grid, kThreads, 0, s>>>(a);
 }
 

@@ -478,9 +478,16 @@ pt_status launch_vertices(const pt_vertex_tracks &in, int32_t n_tracks, int32_t 
     if (cudaMemsetAsync(w, 0, sizeof(int32_t) * 2 * ((size_t)n_events + 1), s) != cudaSuccess ||
         cudaMemsetAsync(out.status, 0, sizeof(int32_t), s) != cudaSuccess)
         return PT_ERR_CUDA;
-    k_vtx_count<<<grid, kThreads, 0, s>>>(a);
+    {
+        KernelTimer t("k_vtx_count", s);
+        k_vtx_count<<<grid, kThreads, 0, s>>>(a);
+    }
     launch_scan(a.ev_off, n_events, part, s);
-    k_vtx_fill<<<grid, kThreads, 0, s>>>(a);
+    {
+        KernelTimer t("k_vtx_fill", s);
+        k_vtx_fill<<<grid, kThreads, 0, s>>>(a);
+    }
+    KernelTimer t("k_vtx_event", s);
     k_vtx_event<<<n_events, kVtxThreads, kVtxDynSmem, s>>>(a);
     return PT_OK;
 }
@@ -490,6 +497,7 @@ void launch_track_summary(int32_t n_tracks, const int32_t *hits, const uint8_t *
                           int32_t *ev, float *z0, float *ez0, float *pt, uint8_t *nhits, int grid, cudaStream_t s) {
     // pT [GeV] = 0.299792458 B[T] R[m], R = 1 / (100 |kappa|) with kappa in 1/cm
     const float pt_of_kappa = 0.299792458e-2f * bz;
+    KernelTimer t("k_track_summary", s);
     k_track_summary<<<grid, kThreads, 0, s>>>(n_tracks, hits, tn, params, cov, tuple, ev_off, n_events, pt_of_kappa,
                                              ev, z0, ez0, pt, nhits);
 }

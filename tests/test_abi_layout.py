@@ -19,7 +19,7 @@ STRUCTS = {
     "pt_cuts": L.Cuts, "pt_fit_params": L.FitParams, "pt_tuning": L.Tuning, "pt_capacity": L.Capacity,
     "pt_config": L.Config, "pt_hits": L.Hits, "pt_cells": L.Cells, "pt_edges": L.Edges, "pt_tuples": L.Tuples,
     "pt_tracks": L.Tracks, "pt_counts": L.Counts, "pt_vertex_tracks": L.VertexTracks,
-    "pt_vertex_cuts": L.VertexCuts, "pt_vertices": L.Vertices,
+    "pt_vertex_cuts": L.VertexCuts, "pt_vertices": L.Vertices, "pt_kernel_time": L.KernelTime,
 }
 
 CONSTANTS = {

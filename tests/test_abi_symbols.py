@@ -86,3 +86,12 @@ def test_a_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(build, "nvcc", no_compiler)
     with pytest.raises(RuntimeError, match="nvcc"):
         _lib.lib()
+
+
+def test_kernel_timing_controls_without_gpu():
+    from paper_2008_13461_gb300 import _lib as L
+    lib = L.lib()
+    assert lib.pt_kernel_timing(2) == L.PT_ERR_INVALID_ARG
+    L.kernel_timing(True)                 # nothing launched: no totals, no device call
+    assert L.kernel_timing_read() == {}
+    L.kernel_timing(False)

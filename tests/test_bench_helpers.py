@@ -6,24 +6,45 @@ import bench
 def test_profile_entries_require_the_current_kernel_code(tmp_path, monkeypatch):
     h = bench.kernel_source_hash()
     good = tmp_path / "good.md"
-    good.write_text(f"kernel_sources: {h}\ntraffic_bytes_per_cell: build_doublets=20.0 fit_tracks=2.0\n"
-                    f"fit_fp64_flops_per_track: 200.0\n")
+    good.write_text(f"kernel_sources: {h}\ntraffic_bytes_per_cell: k_doublets=20.0 k_fit<3>=2.0\n"
+                    f"issue_per_sm_cycle: k_doublets=2.5\n")
     monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(good))
-    assert bench.measured_traffic("build_doublets", 1000) == 20000.0
-    assert bench.measured_traffic("connect_cells", 1000) is None
-    assert bench.measured_fit_flops(10) == 2000.0
+    assert bench.measured_traffic("k_doublets", 1000) == 20000.0
+    assert bench.measured_traffic("k_connect", 1000) is None
+    assert bench.measured_issue("k_doublets") == 2.5
     stale = tmp_path / "stale.md"
-    stale.write_text("kernel_sources: 0000000000000000\ntraffic_bytes_per_cell: build_doublets=20.0\n")
+    stale.write_text("kernel_sources: 0000000000000000\ntraffic_bytes_per_cell: k_doublets=20.0\n")
     monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(stale))
-    assert bench.measured_traffic("build_doublets", 1000) is None
+    assert bench.measured_traffic("k_doublets", 1000) is None
 
 
-def test_algorithmic_bytes_per_stage():
-    ab = bench.algorithmic_bytes(H=100, D=1000, E=50, T=20, K=10, nbar=3.5)
-    assert ab["binning"] == 44 * 100
-    assert ab["fishbone"] == 9 * 1000
-    assert ab["connect"] == 13 * 1000 + 8 * 50
-    assert ab["fit"] == 36 * 10 + 12 * 3.5 * 10 + 88 * 10
+def test_byte_model_per_stage_and_kernel():
+    H, D, E, T = 100, 1000, 50, 20
+    K_by_n = {3: 6, 4: 4}
+    sb = bench.stage_bytes(H, D, E, T, K_by_n)
+    assert sb["a0_binning"] == 44 * H
+    assert sb["a1_doublets"] == 16 * 3.4 * H + 13 * D
+    assert sb["a2_fishbone"] == 9 * D + 16 * H
+    assert sb["a3_connect"] == 13 * D + 4 * E
+    assert sb["a4_search"] == 4 * E + 8 * D + 36 * T
+    assert sb["a5_cleaning"] == 49 * T
+    assert sb["a6_fit"] == (121 + 48) * 6 + (121 + 64) * 4
+    fb = {"k_fishbone_small": 700, "k_fishbone_medium": 200, "k_fishbone_large": 100}
+    kb = bench.kernel_bytes(H, D, E, T, K_by_n, fb)
+    # the Fishbone's kernels split its stage by cells; the fit kernels by tracks
+    assert abs(sum(kb[k] for k in fb) - sb["a2_fishbone"]) < 1e-6
+    assert kb["k_fit<3>"] + kb["k_fit<4>"] == sb["a6_fit"]
+    assert kb["k_bin_count"] + kb["k_bin_fill"] == sb["a0_binning"]
+    assert kb["k_clean_max"] + kb["k_clean_keep"] == 36 * T + sb["a5_cleaning"]
+
+
+def test_fit_flop_count():
+    # n = 3: line (3 unknowns, one 3-point kink) and circle (4 unknowns,
+    # one 4-term kink), plus the pre-fit
+    line = 2 * 3 + 2 * 9 * 1 + 27 / 3 + 9 / 2 + 4 * 9
+    circle = 2 * 3 + 2 * 16 * 1 + 64 / 3 + 16 / 2 + 4 * 16
+    assert abs(bench.fit_flops_per_track(3) - (30 + 60 + line + circle)) < 1e-9
+    assert bench.fit_flops_per_track(5) > bench.fit_flops_per_track(4) > bench.fit_flops_per_track(3)
 
 
 class _FakeBufs:

@@ -299,3 +299,36 @@ def test_pu200_sampled_fits(pu200):
         WP.append(p); WC.append(cv); WX.append(c2); WN.append(nd)
     err = compare_params(P[ks], CV[ks], X2[ks], ND[ks], np.array(WP), np.array(WC), np.array(WX), np.array(WN))
     print("PU200 fit error (max, p99):", err)
+
+
+def test_kernel_timing_and_candidate_counts(pu50):
+    """The per-kernel timing brackets every launch of the four calls, and
+    the doublet search's candidate counts cover every cell it accepted."""
+    from paper_2008_13461_gb300 import _lib as L
+    cuts = CU.cuts_for("pu50-ttbar-like")
+    pipe = make_pipeline(cuts)
+    t = to_dev(pu50)
+    args = (t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
+    res, bufs = pipe.run(*args)
+    torch.cuda.synchronize()
+    L.kernel_timing(True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(3):
+        pipe.launch(bufs, *args)
+    ev[1].record()
+    torch.cuda.synchronize()
+    kt = L.kernel_timing_read()
+    L.kernel_timing(False)
+    for name in ("k_bin_count", "k_doublets", "k_fishbone_small", "k_connect", "k_dfs", "k_fit<3>"):
+        assert kt[name][0] == 3, name
+    assert sum(v[0] for v in kt.values()) == 3 * 23
+    assert sum(v[1] for v in kt.values()) <= ev[0].elapsed_time(ev[1]) * 1.01
+    st, c = pipe.counts(bufs, *args)
+    assert st == L.PT_OK
+    h = pipe._hits(*args)
+    cand = L.doublet_candidates(bufs.ws.data_ptr(), bufs.ws.numel(), h, pipe._cfg(bufs.capacity),
+                                torch.cuda.current_stream().cuda_stream)
+    assert sum(cand) == c.n_doublet_candidates
+    acc = np.bincount(res.cells["pair"].cpu().numpy(), minlength=len(cand))
+    assert np.all(np.array(cand) >= acc) and c.n_doublet_candidates > c.n_cells
