@@ -448,6 +448,79 @@ def measure_differentiable(c, args):
             "note": "gradient of a loss of all track parameters and chi2 with respect to every hit"}
 
 
+MISALIGNMENT_SEED = 2008134610 + 4000 + 999
+
+
+def measure_misaligned(args, dev, stream):
+    """The differentiable form on the misaligned pileup-50 workload: 32
+    events, every module shifted ~ N(0, 50 um) and rotated ~ N(0, 0.1 mrad)
+    per axis (seeded); per step, the alignment of every hit, the refit of
+    every track (its n-tuplets found on the nominal hits), the adjoint of
+    the fit for a loss of all parameters and chi2, and the adjoint of the
+    alignment down to every module's shift and rotation.  Median ms of each
+    phase over the steps (CUDA events, after warm-up)."""
+    import numpy as np
+    import torch
+    from synth import cuts as CU
+    from synth import events as E
+    from synth import geometry as G
+    from paper_2008_13461_gb300 import _lib as L
+    from paper_2008_13461_gb300.autograd import DifferentiableFit
+    from paper_2008_13461_gb300.pipeline import Pipeline
+    b = E.make_batch("pu50-batch32", workers=max(1, min(16, os.cpu_count() or 4)))
+    pipe = Pipeline(G.layers(), G.module_layer_table(), CU.cuts_for("pu50-batch32"), CU.FIT_PARAMS, device=dev)
+    t = {k: torch.as_tensor(b[k]).to(dev) for k in ("x", "y", "z", "r", "module", "ev_off")}
+    res, bufs = pipe.run(t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
+    K, n = res.counts.n_tracks, t["x"].numel()
+    nm = G.N_MODULES
+    rng = np.random.default_rng(MISALIGNMENT_SEED)
+    shift = torch.as_tensor(rng.normal(0.0, 50e-4, size=(nm, 3)), dtype=torch.float32, device=dev)
+    rot = torch.as_tensor(rng.normal(0.0, 1e-4, size=(nm, 3)), dtype=torch.float32, device=dev)
+    centres = torch.as_tensor(G.module_centres(), dtype=torch.float32, device=dev)
+    df = DifferentiableFit(pipe, bufs, t["r"], t["module"], t["ev_off"], centres=centres)
+    g = torch.Generator(device=dev).manual_seed(4)
+    gp = torch.randn(max(K, 1), 5, device=dev, generator=g) * 1e-3
+    gc = torch.randn(max(K, 1), device=dev, generator=g) * 1e-2
+    xa, ya, za, gx, gy, gz, hx, hy, hz = (torch.empty(n, device=dev) for _ in range(9))
+    gshift, grot = torch.empty(nm, 3, device=dev), torch.empty(nm, 3, device=dev)
+    s = stream.cuda_stream
+    cfg = pipe._cfg(bufs.capacity)
+    ws, nb = bufs.ws.data_ptr(), bufs.ws.numel()
+    _, _, tuples, _ = bufs.structs()
+    tracks = df._tracks()
+    ptr = lambda a: a.data_ptr()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    times = [[] for _ in range(4)]
+    for k in range(args.warmup + args.steps):
+        ev[0].record(stream)
+        L.align_hits(n, ptr(t["x"]), ptr(t["y"]), ptr(t["z"]), ptr(t["module"]), nm, ptr(centres), ptr(shift),
+                     ptr(rot), ptr(xa), ptr(ya), ptr(za), s)
+        ev[1].record(stream)
+        h = pipe._hits(xa, ya, za, t["r"], t["module"], t["ev_off"])
+        L.fit_tracks(ws, nb, h, cfg, tuples, tracks, s)
+        ev[2].record(stream)
+        for a in (gx, gy, gz, hx, hy, hz, gshift, grot):
+            a.zero_()
+        L.fit_tracks_grad(ws, nb, h, cfg, tuples, tracks, ptr(gp), ptr(gc), ptr(gx), ptr(gy), ptr(gz), s)
+        ev[3].record(stream)
+        L.align_hits_grad(n, ptr(t["x"]), ptr(t["y"]), ptr(t["z"]), ptr(t["module"]), nm, ptr(centres), ptr(rot),
+                          ptr(gx), ptr(gy), ptr(gz), ptr(hx), ptr(hy), ptr(hz), ptr(gshift), ptr(grot), s)
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            for i in range(4):
+                times[i].append(ev[i].elapsed_time(ev[i + 1]))
+    ms = [statistics.median(v) for v in times]
+    total = sum(ms)
+    return {"workload": "pu50-batch32: 32 synthetic pileup-50 events, every module misaligned "
+                        "(shifts ~ N(0, 50 um), rotations ~ N(0, 0.1 mrad) per axis)",
+            "events": len(b["ev_off"]) - 1, "hits": n, "tracks": K, "modules": nm,
+            "align_ms": ms[0], "refit_ms": ms[1], "adjoint_ms": ms[2], "align_adjoint_ms": ms[3],
+            "ms_per_step": total, "events_per_s": (len(b["ev_off"]) - 1) / (total * 1e-3),
+            "tracks_per_s": K / (total * 1e-3),
+            "note": "the adjoint phase includes zeroing the gradient arrays; n-tuplets from the nominal hits"}
+
+
 def grow_capacity(cap: dict, need: dict) -> dict:
     """Capacities after an overflow: the sizes needed plus a quarter and a
     margin, never smaller than before."""
@@ -623,10 +696,11 @@ def run_native(args, rank, world, local_rank):
     ctx = Ctx(dev=dev, stream=stream, s=s, ws=ws, nb=nb, h=h, cfg=cfg, cells=cells, edges=edges, tuples=tuples,
               tracks=tracks, flush=flush, counts=counts, pipe=pipe, bufs=bufs, t=t)
 
-    graph_ms = e2e = per_event_s = diff_form = "skipped"
+    graph_ms = e2e = per_event_s = diff_form = diff_misaligned = "skipped"
     if not args.no_extras:
         graph_ms = measure_graph(ctx, args)
         diff_form = measure_differentiable(ctx, args)
+        diff_misaligned = measure_misaligned(args, dev, stream)
         e2e = measure_e2e(ctx, args, batch, world)
         if rank == 0:
             per_event_s = measure_per_event(ctx, batch)
@@ -743,6 +817,7 @@ def run_native(args, rank, world, local_rank):
             "note": "same kernels one event at a time, host read of counts after every stage"},
         "e2e": e2e,
         "differentiable_form": diff_form,
+        "differentiable_form_misaligned_pu50_batch32": diff_misaligned,
         "ambiguity_resolution": getattr(ctx, "ambiguity", "skipped"),
         "vertexing": getattr(ctx, "vertexing", "skipped"),
         "roofline": roofline,

@@ -190,6 +190,44 @@ def fit_grad_fd(hx, hy, hz, is_disk, fitpar: dict, gparams, gchi2: float = 0.0, 
     return G
 
 
+def align_hits(x, y, z, module, centres, shift, rot):
+    """Per-module alignment of hits (the corrections whose gradient a
+    track-based alignment of the pixel detector needs, differentiated with
+    the fit of Sec. 3.4): a hit on module m moves to
+        x' = c_m + (I + [w_m]x) (x - c_m) + d_m = x + w_m x (x - c_m) + d_m,
+    the module rotated by the small angle vector w_m (to first order) about
+    its centre c_m and shifted by d_m.  float64 arrays (x', y', z')."""
+    P = np.stack([np.asarray(a, dtype=np.float64) for a in (x, y, z)], 1)
+    m = np.asarray(module)
+    c = np.asarray(centres, dtype=np.float64)[m]
+    out = P + np.cross(np.asarray(rot, dtype=np.float64)[m], P - c) + np.asarray(shift, dtype=np.float64)[m]
+    return out[:, 0], out[:, 1], out[:, 2]
+
+
+def fit_grad_central(hx, hy, hz, is_disk, fitpar: dict, gparams, gchi2: float = 0.0, h: float = 1e-4,
+                     ms_scale: float = 1.0) -> np.ndarray:
+    """Gradient of  gparams . params + gchi2 * chi2  of the broken-line fit
+    with respect to the hit coordinates, float[3, n]: plain central
+    differences (f(x + h) - f(x - h)) / 2h of the float64 fit with step h cm
+    (phi0 differences taken modulo 2 pi)."""
+    base = [np.array(a, dtype=np.float64) for a in (hx, hy, hz)]
+    gp = np.asarray(gparams, dtype=np.float64)
+    n = len(base[0])
+    G = np.zeros((3, n))
+    for a in range(3):
+        for i in range(n):
+            up = [b.copy() for b in base]
+            dn = [b.copy() for b in base]
+            up[a][i] += h
+            dn[a][i] -= h
+            pu, _, cu, _, _ = fit(up[0], up[1], up[2], is_disk, fitpar, ms_scale)
+            pd, _, cd, _, _ = fit(dn[0], dn[1], dn[2], is_disk, fitpar, ms_scale)
+            d = pu - pd
+            d[1] = (d[1] + np.pi) % (2 * np.pi) - np.pi
+            G[a, i] = (float(np.dot(gp, d)) + gchi2 * (cu - cd)) / (2 * h)
+    return G
+
+
 def run(batch: dict, cuts: dict, fitpar: dict, module_layer: np.ndarray,
         layer_is_disk, stage: int = 4, ms_scale: float = 1.0) -> dict:
     """Run the oracle chain up to `stage` (1 doublets+Fishbone, 2 connect,

@@ -162,6 +162,26 @@ def test_vertices_of_the_pipeline_tracks():
             assert abs(float(v["z"][e, k]) - np.sum(w * z0[m]) / np.sum(w)) <= 1e-5
 
 
+def test_vertices_of_the_pipeline_tracks_match_the_oracle():
+    """End to end on four pileup-50 events: the four calls, the ambiguity
+    resolution, the track summaries and the vertex finder on the GPU; the
+    oracle's vertex finder on the same summaries and keep flags gives the
+    same vertices (counts, tracks, ndf and the track map exactly; z, ez,
+    chi2 and sum pT^2 to float32 rounding)."""
+    b = E.make_batch("pu50-batch32", n_events=4)
+    pipe = make_pipeline(CU.cuts_for("pu50-batch32"))
+    t = to_dev(b)
+    res, bufs = pipe.run(t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
+    v, sm = pipe.find_vertices(bufs, res.counts, t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
+    torch.cuda.synchronize()
+    g = {k: x.cpu().numpy() for k, x in v.items() if k != "scratch"}
+    d = {k: sm[k].cpu().numpy() for k in KEYS}
+    assert d["keep"].sum() < len(d["keep"])                  # the ambiguity resolution dropped tracks
+    want, vidx = postfit.find_vertices(d["ev"], d["z0"], d["ez0"], d["pt"], d["nhits"], d["keep"], 4, CUTS)
+    assert all(len(w) > 10 for w in want)
+    _compare(g, want, vidx, 4)
+
+
 def test_vertices_do_not_depend_on_the_order_of_the_tracks():
     d = vertex_tracks(10, 4, pileup=40.0)
     assert len(np.unique(d["z0"])) == len(d["z0"])          # distinct z0: no tie left to the index

@@ -579,3 +579,57 @@ def test_fit_reports_the_condition_of_its_normal_matrices():
     P = _helix_points(1 / 200.0, 0.3, 0.5, 0.001, 1.0, [3.0, 6.9, 11.0, 15.5])
     ex = oracle.fit(P[:, 0], P[:, 1], P[:, 2], [0, 0, 0, 0], CU.FIT_PARAMS)[4]
     assert len(ex) == 10 and ex[8] >= 1.0 and ex[9] >= 1.0 and np.isfinite(ex[8:]).all()
+
+
+# ------------------------------------------------------------- alignment
+def test_alignment_moves_each_module_rigidly_to_first_order():
+    """The oracle's per-module alignment: no correction leaves the hits in
+    place; a shift moves exactly the hits of its module by it; a small
+    rotation turns a module's hits about its centre, equal to the exact
+    rotation matrix up to second order in the angle."""
+    rng = np.random.default_rng(11)
+    n, nm = 400, 5
+    centres = rng.normal(size=(nm, 3)) * 5.0
+    module = rng.integers(0, nm, size=n)
+    P = centres[module] + rng.normal(size=(n, 3)) * 2.0
+    zero = np.zeros((nm, 3))
+    got = np.stack(oracle.align_hits(P[:, 0], P[:, 1], P[:, 2], module, centres, zero, zero), 1)
+    assert np.array_equal(got, P)
+    shift = zero.copy()
+    shift[2] = (1e-3, -2e-3, 5e-4)
+    got = np.stack(oracle.align_hits(P[:, 0], P[:, 1], P[:, 2], module, centres, shift, zero), 1)
+    on = module == 2
+    assert np.allclose(got[on] - P[on], shift[2], atol=1e-15) and np.array_equal(got[~on], P[~on])
+    axis = np.array([0.3, -0.5, 0.8])
+    axis /= np.linalg.norm(axis)
+    theta = 1e-4
+    rot = zero.copy()
+    rot[3] = theta * axis
+    got = np.stack(oracle.align_hits(P[:, 0], P[:, 1], P[:, 2], module, centres, zero, rot), 1)
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    R = np.eye(3) + math.sin(theta) * K + (1 - math.cos(theta)) * K @ K          # Rodrigues
+    on = module == 3
+    exact = centres[3] + (P[on] - centres[3]) @ R.T
+    r = np.linalg.norm(P[on] - centres[3], axis=1)
+    assert np.all(np.linalg.norm(got[on] - exact, axis=1) <= theta ** 2 * r + 1e-14)
+    assert np.array_equal(got[~on], P[~on])
+
+
+def test_plain_central_differences_agree_with_the_extrapolated_gradient():
+    """The plain central differences at the 1e-4 cm step agree with the
+    Richardson-extrapolated gradient to the step's O(h^2) error (here
+    ~3e-5 of the largest component: the fit bends on the scale of the hit
+    resolution, tens of um), and halving the step divides the departure
+    by about four."""
+    b = E.make_batch("barrel-50-helices")
+    lay = G.module_layer_table()[b["module"]]
+    idx = np.nonzero(b["track"] == 3)[0]
+    idx = idx[np.argsort(b["r"][idx])]
+    gp = np.array([1e-3, 1e-3, 1e-3, 1e-2, 1e-2])
+    args = (b["x"][idx], b["y"][idx], b["z"][idx], (lay[idx] >= 4).astype(int), CU.FIT_PARAMS, gp, 0.3)
+    a = oracle.fit_grad_central(*args, h=1e-4)
+    ref = oracle.fit_grad_fd(*args)
+    e1 = np.abs(a - ref).max()
+    assert e1 <= 1e-4 * np.abs(ref).max()
+    e2 = np.abs(oracle.fit_grad_central(*args, h=5e-5) - ref).max()
+    assert 3.0 < e1 / e2 < 5.0
