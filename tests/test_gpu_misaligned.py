@@ -6,7 +6,15 @@ n-tuplets found on the nominal hits are then refitted after every one of the
 and rotations ~ N(0, 0.1 mrad) per axis about the module centre.  Checked
 against the oracle (float64):
 
-  * the aligned hits (pt_align_hits) and the refit of every track on them;
+  * the aligned hits (pt_align_hits) and the refit of every track on them.
+    Aligned hits are off the 2^-14 cm grid, so the float32 differences of
+    hit coordinates the fit starts from are no longer exact: each carries
+    up to u |d| (u = 2^-24, |d| < 16 cm) of rounding, which moves the
+    sagitta of an L ~ 10 cm track by ~2e-6 cm and its curvature by up to
+    8 s / L^2 ~ 1e-7 /cm.  The curvature is therefore compared within
+    1e-4 |kappa| + 1e-7 /cm (the relative bound alone cannot hold for the
+    few tracks the misalignment makes nearly straight); every other
+    tolerance is the on-grid one;
   * the adjoint's gradient with respect to the aligned hits, against plain
     central differences of the oracle fit with the 1e-4 cm step and against
     the oracle's extrapolated gradient;
@@ -34,6 +42,7 @@ H_SHIFT = 1e-4           # cm
 H_ROT = 3e-5             # rad: hits ~3 cm from the centre move by ~1e-4 cm
 MISALIGNMENT_SEED = 2008134610 + 4000 + 999
 SCALE = np.array([1e3, 1e3, 1e3, 1e2, 1e2])   # a unit of each parameter ~ its resolution
+KAPPA_OFF_GRID = 1e-7    # /cm: float32 rounding of off-grid hit differences (module docstring)
 
 
 @pytest.fixture(scope="module")
@@ -105,8 +114,11 @@ def test_alignment_and_refit_of_every_track_match_the_oracle(batch32):
     CV = d["df"].cov[:K * 15].view(K, 15).double().cpu().numpy()
     ND = d["df"].ndf[:K].cpu().numpy()
     W = [oracle.fit(xa[h], ya[h], za[h], d["disk"][h], CU.FIT_PARAMS) for h in d["hits"]]
-    err = compare_params(P, CV, X2, ND, np.array([w[0] for w in W]), np.array([w[1] for w in W]),
-                         np.array([w[2] for w in W]), np.array([w[3] for w in W]))
+    WP = np.array([w[0] for w in W])
+    err = compare_params(P, CV, X2, ND, WP, np.array([w[1] for w in W]), np.array([w[2] for w in W]),
+                         np.array([w[3] for w in W]), kappa_abs=KAPPA_OFF_GRID)
+    print(f"largest absolute curvature departure {np.abs(P[:, 0] - WP[:, 0]).max():.2e} /cm "
+          f"(bound 1e-4 |kappa| + {KAPPA_OFF_GRID:g})")
     print(f"refit of {K} tracks on misaligned hits vs oracle (max, p99):", err)
     assert K > 50000
 
