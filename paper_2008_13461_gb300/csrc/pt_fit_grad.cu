@@ -83,14 +83,21 @@ __device__ __forceinline__ void solve_d(const double *L, double *b) {
     }
 }
 
-// asin(q)/q and its derivative (q clamped to [-1, 1] by the caller)
-__device__ __forceinline__ double asinc_d(double q) {
-    return fabs(q) < 1e-4 ? 1.0 + q * q * (1.0 / 6.0) : asin(q) * rcp_d(q);
+// asin(q)/q, keeping asin(q) in `as` for the derivative (q clamped to
+// [-1, 1] by the caller; below 1e-4 the series, and `as` is not needed)
+__device__ __forceinline__ double asinc_d(double q, double &as) {
+    if (fabs(q) < 1e-4) {
+        as = q;
+        return 1.0 + q * q * (1.0 / 6.0);
+    }
+    as = asin(q);
+    return as * rcp_d(q);
 }
-__device__ __forceinline__ double dasinc_d(double q) {
+// d/dq of asin(q)/q, given as = asin(q)
+__device__ __forceinline__ double dasinc_d(double q, double as) {
     if (fabs(q) < 1e-4) return q * (1.0 / 3.0);
     if (fabs(q) >= 1.0) return 0.0;
-    return (q * rsqrt_d(1.0 - q * q) - asin(q)) * rcp_d(q * q);
+    return (q * rsqrt_d(1.0 - q * q) - as) * rcp_d(q * q);
 }
 
 template <int N>
@@ -127,20 +134,27 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
     double sn, cs;
     sincos(psi0, &sn, &cs);
     // arc lengths and offsets from the pre-fit circle
-    double s[N], m[N], dxs[N], dys[N], dist[N], qs[N], Xs[N], Ys[N], Us[N], Sq[N], i1Sq[N];
+    double s[N], m[N], dxs[N], dys[N], dist[N], qs[N], Xs[N], Ys[N], Us[N], Sq[N], i1Sq[N], asc[N], asq[N];
 #pragma unroll
     for (int i = 0; i < N; i++) {
         dxs[i] = x[i] - x[0];
         dys[i] = y[i] - y[0];
         dist[i] = sqrt_d(dxs[i] * dxs[i] + dys[i] * dys[i]);
         qs[i] = fmin(fmax(0.5 * k0 * dist[i], -1.0), 1.0);
-        s[i] = dist[i] * asinc_d(qs[i]);
-        Xs[i] = dxs[i] * cs + dys[i] * sn;
-        Ys[i] = dys[i] * cs - dxs[i] * sn;
-        Us[i] = k0 * (Xs[i] * Xs[i] + Ys[i] * Ys[i]) - 2.0 * Ys[i];
-        Sq[i] = sqrt_d(fmax(1.0 + k0 * Us[i], 0.0));
-        i1Sq[i] = rcp_d(1.0 + Sq[i]);
-        m[i] = -Us[i] * i1Sq[i];
+        asc[i] = asinc_d(qs[i], asq[i]);
+        s[i] = dist[i] * asc[i];
+        // the pre-fit circle passes through hits 0, n/2 and n-1: their
+        // offsets are zero for any position of the hits
+        if (i == 0 || i == ib || i == ic) {
+            m[i] = 0.0;
+        } else {
+            Xs[i] = dxs[i] * cs + dys[i] * sn;
+            Ys[i] = dys[i] * cs - dxs[i] * sn;
+            Us[i] = k0 * (Xs[i] * Xs[i] + Ys[i] * Ys[i]) - 2.0 * Ys[i];
+            Sq[i] = sqrt_d(fmax(1.0 + k0 * Us[i], 0.0));
+            i1Sq[i] = rcp_d(1.0 + Sq[i]);
+            m[i] = -Us[i] * i1Sq[i];
+        }
     }
     double ds[N], ids[N];
     ds[0] = 0.0;
@@ -159,13 +173,14 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
     const double pmom = pt0 * rsec, ipmom = rcp_d(pmom);
     const double atl = fmax(fabs(tanl0), 1e-3), iatl = rcp_d(atl);
     // 2) scattering weights of the kinks at hits 1 .. n-2
-    double vb[N], vg[N], th[N], xx0[N];
+    double vb[N], vg[N], th[N], xx0[N], lx0[N];
 #pragma unroll
-    for (int i = 0; i < N; i++) vb[i] = vg[i] = th[i] = xx0[i] = 0.0;
+    for (int i = 0; i < N; i++) vb[i] = vg[i] = th[i] = xx0[i] = lx0[i] = 0.0;
 #pragma unroll
     for (int i = 1; i < N - 1; i++) {
         xx0[i] = disk[i] ? p.fit.x0_disk * rsec * iatl : p.fit.x0_barrel * rsec;
-        th[i] = 0.0136 * ipmom * sqrt_d(xx0[i]) * (1.0 + 0.038 * log(xx0[i]));
+        lx0[i] = log(xx0[i]);
+        th[i] = 0.0136 * ipmom * sqrt_d(xx0[i]) * (1.0 + 0.038 * lx0[i]);
         vb[i] = rcp_d(fmax(th[i] * th[i] * sec2, 1e-20));
         vg[i] = rcp_d(fmax(th[i] * th[i] * sec2 * sec2, 1e-20));
     }
@@ -209,7 +224,11 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
     };
     if constexpr (N != 3) chol_d<N>(A);
     solve_line(v);
-    // 4) circle fit: B x = b, x = (u_0 .. u_{n-1}, dk)
+    // 4) circle fit: B x = b, x = (u_0 .. u_{n-1}, dk).  Three hits: the
+    // pre-fit circle passes through all of them, so the offsets m are zero
+    // for any position of the hits, the fit returns u = 0, dk = 0 (its kink
+    // and chi2 vanish) and the track is that circle: nothing of the circle
+    // fit depends on the hits, and its backward pass is skipped below.
     const double wu = rcp_d((double)p.fit.sigma_rphi * p.fit.sigma_rphi);
     double B[M * (M + 1) / 2], xs[M];
 #pragma unroll
@@ -243,15 +262,20 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
             solve_d<M>(B, yv);
         }
     };
-    if constexpr (N != 3) chol_d<M>(B);
-    solve_circle(xs);
+    if constexpr (N != 3) {
+        chol_d<M>(B);
+        solve_circle(xs);
+    } else {
+#pragma unroll
+        for (int i = 0; i < M; i++) xs[i] = 0.0;
+    }
     const double dk = xs[N];
     // 5) perigee
     const double kf = k0 + dk;
     const double px = x[0] - xs[0] * sn, py = y[0] + xs[0] * cs;
     const double psi = psi0 + (xs[1] - xs[0]) * ids[1] - dk * 0.5 * ds[1];
-    double sp, cp;
-    sincos(psi, &sp, &cp);
+    double sp = sn, cp = cs;
+    if constexpr (N != 3) sincos(psi, &sp, &cp);
     const double Xo = -(px * cp + py * sp), Yo = px * sp - py * cp;
     const double U = kf * (Xo * Xo + Yo * Yo) - 2.0 * Yo;
     const double q1 = 1.0 + kf * U;
@@ -335,7 +359,7 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
     xsb[N] += kfb;
 
     // 4) circle: parameters through the solve, chi2 by the envelope theorem
-    {
+    if constexpr (N != 3) {
         double bb[M];
 #pragma unroll
         for (int i = 0; i < M; i++) bb[i] = xsb[i];
@@ -422,7 +446,7 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
         pmomb += -thb * th[i] * ipmom;
         const double sx = sqrt_d(xx0[i]);
         const double xx0b =
-            thb * 0.0136 * ipmom * ((1.0 + 0.038 * log(xx0[i])) * 0.5 * rcp_d(sx) + sx * 0.038 * rcp_d(xx0[i]));
+            thb * 0.0136 * ipmom * ((1.0 + 0.038 * lx0[i]) * 0.5 * rcp_d(sx) + sx * 0.038 * rcp_d(xx0[i]));
         // xx0 = x0 sqrt(sec2) [/ atl]
         sec2b += 0.5 * xx0b * xx0[i] * rcp_d(sec2);
         if (disk[i]) atlb += -xx0b * xx0[i] * iatl;
@@ -451,27 +475,29 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
 #pragma unroll
     for (int i = 1; i < N; i++) {
         double dxb = 0.0, dyb = 0.0;
-        // m = -U / (1 + Sq), Sq = sqrt(max(1 + k0 U, 0))
-        double Ubi = -mb[i] * i1Sq[i];
-        if (1.0 + k0 * Us[i] > 0.0 && Sq[i] > 0.0) {
-            const double Sqb = mb[i] * Us[i] * i1Sq[i] * i1Sq[i];
-            const double qb = 0.5 * Sqb * rcp_d(Sq[i]);
-            k0b += qb * Us[i];
-            Ubi += qb * k0;
+        if (i != ib && i != ic) {         // (offsets identically zero on the pre-fit circle)
+            // m = -U / (1 + Sq), Sq = sqrt(max(1 + k0 U, 0))
+            double Ubi = -mb[i] * i1Sq[i];
+            if (1.0 + k0 * Us[i] > 0.0 && Sq[i] > 0.0) {
+                const double Sqb = mb[i] * Us[i] * i1Sq[i] * i1Sq[i];
+                const double qb = 0.5 * Sqb * rcp_d(Sq[i]);
+                k0b += qb * Us[i];
+                Ubi += qb * k0;
+            }
+            // U = k0 (X^2 + Y^2) - 2 Y
+            k0b += Ubi * (Xs[i] * Xs[i] + Ys[i] * Ys[i]);
+            const double Xb = Ubi * 2.0 * k0 * Xs[i], Yb = Ubi * (2.0 * k0 * Ys[i] - 2.0);
+            // X = dx cs + dy sn, Y = dy cs - dx sn
+            dxb += Xb * cs - Yb * sn;
+            dyb += Xb * sn + Yb * cs;
+            csb += Xb * dxs[i] + Yb * dys[i];
+            snb += Xb * dys[i] - Yb * dxs[i];
         }
-        // U = k0 (X^2 + Y^2) - 2 Y
-        k0b += Ubi * (Xs[i] * Xs[i] + Ys[i] * Ys[i]);
-        const double Xb = Ubi * 2.0 * k0 * Xs[i], Yb = Ubi * (2.0 * k0 * Ys[i] - 2.0);
-        // X = dx cs + dy sn, Y = dy cs - dx sn
-        dxb += Xb * cs - Yb * sn;
-        dyb += Xb * sn + Yb * cs;
-        csb += Xb * dxs[i] + Yb * dys[i];
-        snb += Xb * dys[i] - Yb * dxs[i];
         // s = dist asinc(q), q = 0.5 k0 dist (clamped)
         if (dist[i] > 0.0) {
             const bool qin = fabs(0.5 * k0 * dist[i]) < 1.0;
-            const double da = qin ? dasinc_d(qs[i]) : 0.0;
-            const double distb = sb[i] * (asinc_d(qs[i]) + dist[i] * da * 0.5 * k0);
+            const double da = qin ? dasinc_d(qs[i], asq[i]) : 0.0;
+            const double distb = sb[i] * (asc[i] + dist[i] * da * 0.5 * k0);
             k0b += sb[i] * dist[i] * da * 0.5 * dist[i];
             const double idist = rcp_d(dist[i]);
             dxb += distb * dxs[i] * idist;
