@@ -431,15 +431,20 @@ def measure_differentiable(c, args):
     t = c.t
     hits = (t["x"], t["y"], t["z"], t["r"], t["module"], t["ev_off"])
     for k in range(args.warmup + args.steps):
+        if k == args.warmup:
+            L.kernel_timing(True)
         ev[0].record(c.stream)
         v, sm = c.pipe.find_vertices(c.bufs, c.counts, *hits, stream=c.stream)
         ev[1].record(c.stream)
         torch.cuda.synchronize()
         if k >= args.warmup:
             tv.append(ev[0].elapsed_time(ev[1]))
+    kt = L.kernel_timing_read()
+    L.kernel_timing(False)
     nv = v["n"].cpu()
     elig = int((v["track_vertex"] >= 0).sum().item())
     c.vertexing = {"ms": statistics.median(tv), "vertices_per_event": float(nv.float().mean().item()),
+                   "kernels_ms_per_launch": {k: round(ms / n, 4) for k, (n, ms) in kt.items()},
                    "tracks_in_vertices": elig, "status": int(v["status"].item()),
                    "note": "ambiguity resolution + track summary + vertex finding on the fitted tracks, "
                            "default vertex cuts"}

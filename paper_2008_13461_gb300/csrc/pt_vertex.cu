@@ -28,8 +28,10 @@
 // memory (bitonic), so that every track's compatible tracks lie in a window
 // around it; densities and links come from window scans (one thread per
 // track), roots from pointer jumping, candidates from a second sort of
-// (root, position) keys, and each candidate's fit and 2-means split from one
-// warp (shuffle reductions).
+// (root, position) keys.  The candidates' fits and 2-means splits, the
+// float64 part, then run one warp per candidate over the candidates of all
+// events at once (shuffle reductions), so that every SM takes part; a last
+// block per event orders its vertices and labels their tracks.
 #include "pt_common.cuh"
 #include "pt_kernels.cuh"
 
@@ -52,8 +54,16 @@ struct VtxArgs {
     int32_t n_tracks, n_events, max_vertices;
     pt_vertex_tracks in;
     pt_vertex_cuts cuts;
-    // scratch
+    // scratch; arrays "by sorted position" hold each event's tracks at its ev_off
     int32_t *ev_off, *ev_cur, *order, *rho, *root;
+    double2 *wz;                     // (1 / ez0^2, z0) in float64 by sorted position
+    int32_t *key;                    // (root, position) keys, grouped by root; the members of the candidates
+    int32_t *sid;                    // track index by sorted position
+    int32_t *nc, *nv;                // per event: candidates, provisional vertices
+    int32_t *cq, *cn, *cv0, *cv1;    // per event and candidate (kVtxCap each): first key, members, its vertices
+    double *vz, *vsp;                // per event and provisional vertex (kVtxCap each): z, sum of pT^2
+    float *vez, *vc2;                //   its error and chi2
+    int32_t *vnt, *vkey;             //   its tracks and (2 * first key + part)
     pt_vertices out;
 };
 
@@ -117,38 +127,39 @@ struct WSums {
 };
 
 // Weighted sums over the members mk[0, n) of a candidate (one warp); sel < 0:
-// every member, else those whose side bit equals sel.
-__device__ __forceinline__ WSums member_sums(const VtxArgs &a, const int32_t *mk, int n, int sel, const float *sz,
-                                             const int32_t *sid) {
+// every member, else those whose side bit equals sel.  wz: each track's
+// weight 1/ez0^2 and z0 in float64 by sorted position, computed once per
+// track (the float64 pipe is the slow one on this GPU, and a division, or a
+// conversion to float64, costs many of its cycles).
+__device__ __forceinline__ WSums member_sums(const int32_t *mk, int n, int sel, const double2 *wz) {
     double sw = 0.0, swz = 0.0;
     int c = 0;
     for (int k = threadIdx.x & 31; k < n; k += 32) {
         const int32_t kk = mk[k];
         if (sel >= 0 && ((kk >> kSideBit) & 1) != sel) continue;
-        const int p = kk & kPosMask;
-        const double e = a.in.ez0[sid[p]], w = 1.0 / (e * e);
-        sw += w;
-        swz += w * (double)sz[p];
+        const double2 v = wz[kk & kPosMask];
+        sw += v.x;
+        swz += v.x * v.y;
         c++;
     }
     return WSums{warp_sum(sw), warp_sum(swz), warp_sum(c)};
 }
 
-__device__ __forceinline__ double member_chi2(const VtxArgs &a, const int32_t *mk, int n, int sel, double z,
-                                              const float *sz, const int32_t *sid) {
+__device__ __forceinline__ double member_chi2(const int32_t *mk, int n, int sel, double z, const double2 *wz) {
     double c = 0.0;
     for (int k = threadIdx.x & 31; k < n; k += 32) {
         const int32_t kk = mk[k];
         if (sel >= 0 && ((kk >> kSideBit) & 1) != sel) continue;
-        const int p = kk & kPosMask;
-        const double e = a.in.ez0[sid[p]], w = 1.0 / (e * e), d = (double)sz[p] - z;
-        c += w * d * d;
+        const double2 v = wz[kk & kPosMask];
+        const double d = v.y - z;
+        c += v.x * d * d;
     }
     return warp_sum(c);
 }
 
 __device__ __forceinline__ double member_sumpt2(const VtxArgs &a, const int32_t *mk, int n, int sel,
                                                 const int32_t *sid) {
+    // (sid: the event's track index by sorted position)
     double s = 0.0;
     for (int k = threadIdx.x & 31; k < n; k += 32) {
         const int32_t kk = mk[k];
@@ -172,30 +183,25 @@ __device__ __forceinline__ void bitonic(int P, Gt gt, Swap swap) {
         }
 }
 
-__global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_event(VtxArgs a) {
+// Per event: sort, densities, links, roots, candidates (one block).
+__global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_group(VtxArgs a) {
     extern __shared__ __align__(16) unsigned char vsm[];
     float *sz = reinterpret_cast<float *>(vsm);                   // z0 by sorted position
     int32_t *sid = reinterpret_cast<int32_t *>(sz + kVtxMax);     // track index by sorted position
     int32_t *key = sid + kVtxMax;                                 // root << kPosBits | position
-    __shared__ int s_nc, s_nv;
-    __shared__ int s_cq[kVtxCap], s_cn[kVtxCap], s_cv0[kVtxCap], s_cv1[kVtxCap];
-    __shared__ double s_z[kVtxCap], s_sp[kVtxCap];
-    __shared__ float s_ez[kVtxCap], s_c2[kVtxCap];
-    __shared__ int s_nt[kVtxCap], s_vkey[kVtxCap], s_rank[kVtxCap];
+    __shared__ int s_nc;
 
-    const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int e = blockIdx.x, tid = threadIdx.x;
     const int base = a.ev_off[e], cnt = a.ev_off[e + 1] - base;
+    if (tid == 0) {
+        a.nc[e] = 0;
+        a.nv[e] = 0;
+    }
     if (cnt > kVtxMax) {                                          // uniform over the block
-        if (tid == 0) {
-            set_status(a, PT_VTX_EVENT_TOO_LARGE);
-            a.out.n[e] = 0;
-        }
+        if (tid == 0) set_status(a, PT_VTX_EVENT_TOO_LARGE);
         return;
     }
-    if (tid == 0) {
-        s_nc = 0;
-        s_nv = 0;
-    }
+    if (tid == 0) s_nc = 0;
     int P = 1;
     while (P < cnt) P <<= 1;
     for (int p = tid; p < P; p += blockDim.x) {
@@ -222,9 +228,17 @@ __global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_event(VtxArgs a) {
 
     const float dzc = a.cuts.dz_cut, c2m = a.cuts.chi2_max;
     int32_t *rho = a.rho + base, *root = a.root + base;
-    // the z0 errors by sorted position, in the key array until the keys are built
+    // the z0 errors by sorted position, in the key array until the keys are
+    // built, and the weights 1/ez0^2 of the vertex fits
     float *sez = reinterpret_cast<float *>(key);
-    for (int p = tid; p < cnt; p += blockDim.x) sez[p] = a.in.ez0[sid[p]];
+    double2 *wz = a.wz + base;
+    for (int p = tid; p < cnt; p += blockDim.x) {
+        const float ez = a.in.ez0[sid[p]];
+        sez[p] = ez;
+        const double e = ez;
+        wz[p] = make_double2(1.0 / (e * e), (double)sz[p]);
+        a.sid[base + p] = sid[p];
+    }
     __syncthreads();
     // densities: the compatible tracks lie in the window |z0 - z0_p| < dz_cut
     // (rounded differences are monotonic along the sorted order)
@@ -282,10 +296,7 @@ __global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_event(VtxArgs a) {
         done = !__syncthreads_or(ch);
     }
     if (!done) {                                                  // uniform over the block
-        if (tid == 0) {
-            set_status(a, PT_VTX_INTERNAL);
-            a.out.n[e] = 0;
-        }
+        if (tid == 0) set_status(a, PT_VTX_INTERNAL);
         return;
     }
     // group the tracks by root: sort the (root, position) keys
@@ -307,35 +318,48 @@ __global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_event(VtxArgs a) {
         if (rho[r] > 1 && n >= a.cuts.min_tracks) {
             const int c = atomicAdd(&s_nc, 1);
             if (c < kVtxCap) {
-                s_cq[c] = q;
-                s_cn[c] = n;
+                a.cq[e * kVtxCap + c] = q;
+                a.cn[e * kVtxCap + c] = n;
             } else {
                 set_status(a, PT_VTX_TOO_MANY);
             }
         }
     }
+    for (int q = tid; q < cnt; q += blockDim.x) a.key[base + q] = key[q];
     __syncthreads();
-    const int nc = min(s_nc, kVtxCap);
-    // one warp per candidate: fit, 2-means split, provisional vertices
-    for (int c = wid; c < nc; c += nw) {
-        const int q = s_cq[c], n = s_cn[c];
+    if (tid == 0) a.nc[e] = min(s_nc, kVtxCap);
+}
+
+// The candidates of all events, one warp each: fit, 2-means split,
+// provisional vertices (grid: candidates / warps per block x events).
+constexpr int kFitWarps = 8;
+
+__global__ void __launch_bounds__(32 * kFitWarps) k_vtx_fit(VtxArgs a) {
+    const int e = blockIdx.y, c = blockIdx.x * kFitWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (c >= a.nc[e]) return;                                     // uniform over the warp
+    const int base = a.ev_off[e];
+    int32_t *key = a.key + base;
+    const int32_t *sid = a.sid + base;
+    const double2 *wz = a.wz + base;
+    {
+        const int q = a.cq[e * kVtxCap + c], n = a.cn[e * kVtxCap + c];
         int32_t *mk = key + q;
-        const WSums all = member_sums(a, mk, n, -1, sz, sid);
+        const WSums all = member_sums(mk, n, -1, wz);
         const double z = all.swz / all.sw;
-        const double chi2 = member_chi2(a, mk, n, -1, z, sz, sid);
+        const double chi2 = member_chi2(mk, n, -1, z, wz);
         bool split = false;
         if (n > 1 && chi2 / (double)(n - 1) > (double)a.cuts.split_chi2) {
             int hi = 0;
             for (int k = lane; k < n; k += 32) {
                 const int32_t kk = mk[k];
-                const int s = (double)sz[kk & kPosMask] >= z;
+                const int s = wz[kk & kPosMask].y >= z;
                 mk[k] = (kk & ~(1 << kSideBit)) | (s << kSideBit);
                 hi += s;
             }
             hi = warp_sum(hi);
             __syncwarp();
             if (hi > 0 && hi < n) {
-                WSums s0 = member_sums(a, mk, n, 0, sz, sid), s1 = member_sums(a, mk, n, 1, sz, sid);
+                WSums s0 = member_sums(mk, n, 0, wz), s1 = member_sums(mk, n, 1, wz);
                 double c0 = s0.swz / s0.sw, c1 = s1.swz / s1.sw;
                 int up = 0;
                 bool have = false;
@@ -344,7 +368,7 @@ __global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_event(VtxArgs a) {
                     up = 0;
                     for (int k = lane; k < n; k += 32) {
                         const int32_t kk = mk[k];
-                        const double zz = sz[kk & kPosMask];
+                        const double zz = wz[kk & kPosMask].y;
                         const int u = fabs(zz - c1) < fabs(zz - c0);      // ties: the lower centre
                         diff |= u != ((kk >> kSideBit) & 1);
                         mk[k] = (kk & ~(1 << kSideBit)) | (u << kSideBit);
@@ -356,8 +380,8 @@ __global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_event(VtxArgs a) {
                     if (have && !diff) break;
                     have = true;
                     if (up == 0 || up == n) break;
-                    s0 = member_sums(a, mk, n, 0, sz, sid);
-                    s1 = member_sums(a, mk, n, 1, sz, sid);
+                    s0 = member_sums(mk, n, 0, wz);
+                    s1 = member_sums(mk, n, 1, wz);
                     c0 = s0.swz / s0.sw;
                     c1 = s1.swz / s1.sw;
                 }
@@ -366,32 +390,49 @@ __global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_event(VtxArgs a) {
         }
         for (int part = 0; part < (split ? 2 : 1); part++) {
             const int sel = split ? part : -1;
-            const WSums s = member_sums(a, mk, n, sel, sz, sid);
+            const WSums s = member_sums(mk, n, sel, wz);
             const double zv = s.swz / s.sw;
-            const double c2v = member_chi2(a, mk, n, sel, zv, sz, sid);
+            const double c2v = member_chi2(mk, n, sel, zv, wz);
             const double sp = member_sumpt2(a, mk, n, sel, sid);
             int v = 0;
             if (lane == 0) {
-                v = atomicAdd(&s_nv, 1);
+                v = atomicAdd(a.nv + e, 1);
                 if (v < kVtxCap) {
-                    s_z[v] = zv;
-                    s_ez[v] = (float)(1.0 / sqrt(s.sw));
-                    s_c2[v] = (float)c2v;
-                    s_nt[v] = s.n;
-                    s_sp[v] = sp;
-                    s_vkey[v] = 2 * q + part;
+                    const int o = e * kVtxCap + v;
+                    a.vz[o] = zv;
+                    a.vez[o] = (float)(1.0 / sqrt(s.sw));
+                    a.vc2[o] = (float)c2v;
+                    a.vnt[o] = s.n;
+                    a.vsp[o] = sp;
+                    a.vkey[o] = 2 * q + part;
                 } else {
                     set_status(a, PT_VTX_TOO_MANY);
                 }
-                if (part == 0) s_cv0[c] = v;
-                else s_cv1[c] = v;
-                if (!split) s_cv1[c] = -1;
+                if (part == 0) a.cv0[e * kVtxCap + c] = v;
+                else a.cv1[e * kVtxCap + c] = v;
+                if (!split) a.cv1[e * kVtxCap + c] = -1;
             }
         }
     }
+}
+
+// Per event: the vertices by sum of pT^2 (then z, then the key), their
+// outputs and the vertex of every member track (one block).
+constexpr int kOrderThreads = 256;
+
+__global__ void __launch_bounds__(kOrderThreads) k_vtx_order(VtxArgs a) {
+    __shared__ double s_z[kVtxCap], s_sp[kVtxCap];
+    __shared__ int s_vkey[kVtxCap], s_rank[kVtxCap];
+    const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int base = a.ev_off[e];
+    const int nv = min(a.nv[e], kVtxCap), nc = a.nc[e];
+    const int32_t *key = a.key + base, *sid = a.sid + base;
+    for (int v = tid; v < nv; v += blockDim.x) {
+        s_z[v] = a.vz[e * kVtxCap + v];
+        s_sp[v] = a.vsp[e * kVtxCap + v];
+        s_vkey[v] = a.vkey[e * kVtxCap + v];
+    }
     __syncthreads();
-    // order: sum pT^2 descending, then z, then the (root, part) key
-    const int nv = min(s_nv, kVtxCap);
     for (int v = tid; v < nv; v += blockDim.x) {
         const double sv = s_sp[v], zv = s_z[v];
         const int kv = s_vkey[v];
@@ -402,10 +443,10 @@ __global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_event(VtxArgs a) {
         if (r < a.max_vertices) {
             const int64_t o = (int64_t)e * a.max_vertices + r;
             a.out.z[o] = (float)zv;
-            a.out.ez[o] = s_ez[v];
-            a.out.chi2[o] = s_c2[v];
-            a.out.ndf[o] = s_nt[v] - 1;
-            a.out.ntracks[o] = s_nt[v];
+            a.out.ez[o] = a.vez[e * kVtxCap + v];
+            a.out.chi2[o] = a.vc2[e * kVtxCap + v];
+            a.out.ndf[o] = a.vnt[e * kVtxCap + v] - 1;
+            a.out.ntracks[o] = a.vnt[e * kVtxCap + v];
             a.out.sumpt2[o] = (float)sv;
         }
     }
@@ -415,7 +456,8 @@ __global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_event(VtxArgs a) {
     }
     __syncthreads();
     for (int c = wid; c < nc; c += nw) {
-        const int q = s_cq[c], n = s_cn[c], v0 = s_cv0[c], v1 = s_cv1[c];
+        const int q = a.cq[e * kVtxCap + c], n = a.cn[e * kVtxCap + c];
+        const int v0 = a.cv0[e * kVtxCap + c], v1 = a.cv1[e * kVtxCap + c];
         for (int k = lane; k < n; k += 32) {
             const int32_t kk = key[q + k];
             const int v = (v1 >= 0 && ((kk >> kSideBit) & 1)) ? v1 : v0;
@@ -448,11 +490,47 @@ __global__ void __launch_bounds__(kThreads) k_track_summary(int32_t n_tracks, co
 
 }  // namespace
 
-size_t vertex_scratch_bytes(int32_t n_tracks, int32_t n_events) {
-    return sizeof(int32_t) * (2 * ((size_t)n_events + 1) + (size_t)n_events / kScanItems + 2 +
-                              3 * ((size_t)n_tracks + 1)) +
-           256;
+// Scratch layout (byte offsets, each array 16-byte aligned).
+struct VtxLayout {
+    size_t ev_off, ev_cur, part, order, rho, root, wz, key, sid, nc, nv, cq, cn, cv0, cv1, vz, vsp, vez, vc2, vnt,
+        vkey, total;
+};
+
+VtxLayout vertex_layout(int32_t n_tracks, int32_t n_events) {
+    VtxLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = (o + bytes + 15) & ~(size_t)15;
+        return at;
+    };
+    const size_t nt = (size_t)n_tracks + 1, ne = (size_t)n_events + 1, ncap = (size_t)n_events * kVtxCap + 1;
+    L.ev_off = take(4 * ne);
+    L.ev_cur = take(4 * ne);
+    L.part = take(4 * ((size_t)n_events / kScanItems + 2));
+    L.order = take(4 * nt);
+    L.rho = take(4 * nt);
+    L.root = take(4 * nt);
+    L.wz = take(16 * nt);
+    L.key = take(4 * nt);
+    L.sid = take(4 * nt);
+    L.nc = take(4 * ne);
+    L.nv = take(4 * ne);
+    L.cq = take(4 * ncap);
+    L.cn = take(4 * ncap);
+    L.cv0 = take(4 * ncap);
+    L.cv1 = take(4 * ncap);
+    L.vz = take(8 * ncap);
+    L.vsp = take(8 * ncap);
+    L.vez = take(4 * ncap);
+    L.vc2 = take(4 * ncap);
+    L.vnt = take(4 * ncap);
+    L.vkey = take(4 * ncap);
+    L.total = o;
+    return L;
 }
+
+size_t vertex_scratch_bytes(int32_t n_tracks, int32_t n_events) { return vertex_layout(n_tracks, n_events).total; }
 
 pt_status launch_vertices(const pt_vertex_tracks &in, int32_t n_tracks, int32_t n_events,
                           const pt_vertex_cuts &cuts, int32_t max_vertices, void *scratch, const pt_vertices &out,
@@ -463,19 +541,36 @@ pt_status launch_vertices(const pt_vertex_tracks &in, int32_t n_tracks, int32_t 
     a.max_vertices = max_vertices;
     a.in = in;
     a.cuts = cuts;
-    int32_t *w = (int32_t *)scratch;
-    a.ev_off = w;
-    a.ev_cur = a.ev_off + (n_events + 1);
-    int32_t *part = a.ev_cur + (n_events + 1);
-    a.order = part + (n_events / kScanItems + 2);
-    a.rho = a.order + (n_tracks + 1);
-    a.root = a.rho + (n_tracks + 1);
+    const VtxLayout L = vertex_layout(n_tracks, n_events);
+    char *w = (char *)scratch;
+    a.ev_off = (int32_t *)(w + L.ev_off);
+    a.ev_cur = (int32_t *)(w + L.ev_cur);
+    int32_t *part = (int32_t *)(w + L.part);
+    a.order = (int32_t *)(w + L.order);
+    a.rho = (int32_t *)(w + L.rho);
+    a.root = (int32_t *)(w + L.root);
+    a.wz = (double2 *)(w + L.wz);
+    a.key = (int32_t *)(w + L.key);
+    a.sid = (int32_t *)(w + L.sid);
+    a.nc = (int32_t *)(w + L.nc);
+    a.nv = (int32_t *)(w + L.nv);
+    a.cq = (int32_t *)(w + L.cq);
+    a.cn = (int32_t *)(w + L.cn);
+    a.cv0 = (int32_t *)(w + L.cv0);
+    a.cv1 = (int32_t *)(w + L.cv1);
+    a.vz = (double *)(w + L.vz);
+    a.vsp = (double *)(w + L.vsp);
+    a.vez = (float *)(w + L.vez);
+    a.vc2 = (float *)(w + L.vc2);
+    a.vnt = (int32_t *)(w + L.vnt);
+    a.vkey = (int32_t *)(w + L.vkey);
     a.out = out;
     // per device and call (cheap; no shared state between threads or devices)
-    if (cudaFuncSetAttribute(k_vtx_event, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVtxDynSmem) !=
+    if (cudaFuncSetAttribute(k_vtx_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVtxDynSmem) !=
         cudaSuccess)
         return PT_ERR_CUDA;
-    if (cudaMemsetAsync(w, 0, sizeof(int32_t) * 2 * ((size_t)n_events + 1), s) != cudaSuccess ||
+    if (cudaMemsetAsync(a.ev_off, 0, sizeof(int32_t) * ((size_t)n_events + 1), s) != cudaSuccess ||
+        cudaMemsetAsync(a.ev_cur, 0, sizeof(int32_t) * ((size_t)n_events + 1), s) != cudaSuccess ||
         cudaMemsetAsync(out.status, 0, sizeof(int32_t), s) != cudaSuccess)
         return PT_ERR_CUDA;
     {
@@ -487,8 +582,16 @@ pt_status launch_vertices(const pt_vertex_tracks &in, int32_t n_tracks, int32_t 
         KernelTimer t("k_vtx_fill", s);
         k_vtx_fill<<<grid, kThreads, 0, s>>>(a);
     }
-    KernelTimer t("k_vtx_event", s);
-    k_vtx_event<<<n_events, kVtxThreads, kVtxDynSmem, s>>>(a);
+    {
+        KernelTimer t("k_vtx_group", s);
+        k_vtx_group<<<n_events, kVtxThreads, kVtxDynSmem, s>>>(a);
+    }
+    {
+        KernelTimer t("k_vtx_fit", s);
+        k_vtx_fit<<<dim3(kVtxCap / kFitWarps, n_events), 32 * kFitWarps, 0, s>>>(a);
+    }
+    KernelTimer t("k_vtx_order", s);
+    k_vtx_order<<<n_events, kOrderThreads, 0, s>>>(a);
     return PT_OK;
 }
 
