@@ -200,6 +200,7 @@ Params make_params(void *ws, const WsLayout &L, const pt_hits *h, const pt_confi
         p.pair_dphi[k] = (float)(atan(sqrt((double)c.pair[k].tan2_dphi)) + 1e-4);
         const int lo = c.pair[k].outer;
         p.pairs_by_outer[lo][p.n_pairs_by_outer[lo]++] = (int8_t)k;
+        p.layer_is_inner[c.pair[k].inner] = 1;
     }
     p.region[0] = c.region[0];
     p.region[1] = c.region[1];

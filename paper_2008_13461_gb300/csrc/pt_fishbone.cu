@@ -256,9 +256,23 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
     __syncwarp();
     if (!kExact && __any_sync(0xffffffffu, und)) return -1;
 
-    // pass 2: the live cells, sorted by slope key for the CA connection
+    // pass 2: the live cells, sorted by slope key for the CA connection.  A
+    // hit on a layer that is the inner layer of no pair starts no cell, so
+    // the connection never searches the cells ending on it: only their
+    // Fishbone verdicts are written.
     int alive = 0;
-    if (in_smem) {
+    if (!p.layer_is_inner[p.blayer[o]]) {
+        int nl = 0;
+        for (int j = lane; j < n; j += 32) {
+            const bool dead = in_smem ? sm.dead[w][j] != 0 : p.cell_alive[b + j] == 0;
+            if (dead && in_smem) p.cell_alive[b + j] = 0;
+            alive += !dead;
+        }
+        nl = alive;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) nl += __shfl_xor_sync(0xffffffffu, nl, d);
+        if (lane == 0) p.in_live[o] = nl;
+    } else if (in_smem) {
         // slope key and inner hit of each live cell (the records are free)
         float smin = __int_as_float(0x7f800000), smax = -smin;
         for (int j = lane; j < n; j += 32) {
