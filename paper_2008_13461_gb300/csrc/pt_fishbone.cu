@@ -123,6 +123,9 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
     const bool in_smem = !kGlobal || n <= M;
     const float irr = rsqrtf(ho.x * ho.x + ho.y * ho.y);
     const float rx = ho.x * irr, ry = ho.y * irr;
+    // a hit on a layer that is the inner layer of no pair starts no cell:
+    // the connection never reads the slope keys of the cells ending on it
+    const bool starts = p.layer_is_inner[p.blayer[o]] != 0;
     // pass 1: R-z slope keys (barrel o: (z_o - z_a)/(r_o - r_a); disk o:
     // (r_o - r_a)/(z_o - z_a)) with the per-hit bounds; records and the
     // range of the bucket keys
@@ -131,18 +134,20 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
         const int i = p.cell_inner[b + j];
         const int L = cell_layer(p, b + j);
         const float4 a = __ldg(p.bh + i);
-        const float dr = ho.w - a.w, dz = ho.z - a.z;
-        const float num = disk ? dr : dz, den = disk ? dz : dr;
-        // the key only places the cell in the connection's search window,
-        // whose margins (1e-5 relative) are far above the 2 ulp of this quotient
-        const float ck = den != 0.f ? __fdividef(num, den) : __int_as_float(0x7f800000);
-        k2max = fmaxf(k2max, ck * ck);
-        gmin = fminf(gmin, fabsf(den));
-        if (C && in_smem) {
-            sm.ck[w][j] = ck;
-            sm.inner[w][j] = i;
-        } else {
-            p.ck[b + j] = ck;
+        if (starts) {
+            const float dr = ho.w - a.w, dz = ho.z - a.z;
+            const float num = disk ? dr : dz, den = disk ? dz : dr;
+            // the key only places the cell in the connection's search window,
+            // whose margins (1e-5 relative) are far above the 2 ulp of this quotient
+            const float ck = den != 0.f ? __fdividef(num, den) : __int_as_float(0x7f800000);
+            k2max = fmaxf(k2max, ck * ck);
+            gmin = fminf(gmin, fabsf(den));
+            if (C && in_smem) {
+                sm.ck[w][j] = ck;
+                sm.inner[w][j] = i;
+            } else {
+                p.ck[b + j] = ck;
+            }
         }
         if (in_smem) {
             const float ux = a.x - ho.x, uy = a.y - ho.y, uz = a.z - ho.z;
@@ -161,7 +166,7 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
         gmin = fminf(gmin, __shfl_xor_sync(0xffffffffu, gmin, d));
     }
     const float kmax = sqrtf(1.0f + k2max);        // max of sqrt(1 + key^2)
-    if (lane == 0) p.hk[o] = make_float2(kmax, gmin);
+    if (lane == 0 && starts) p.hk[o] = make_float2(kmax, gmin);
     __syncwarp();
 
     bool und = false;
@@ -261,7 +266,7 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
     // the connection never searches the cells ending on it: only their
     // Fishbone verdicts are written.
     int alive = 0;
-    if (!p.layer_is_inner[p.blayer[o]]) {
+    if (!starts) {
         int nl = 0;
         for (int j = lane; j < n; j += 32) {
             const bool dead = in_smem ? sm.dead[w][j] != 0 : p.cell_alive[b + j] == 0;
