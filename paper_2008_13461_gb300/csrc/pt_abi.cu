@@ -202,6 +202,7 @@ Params make_params(void *ws, const WsLayout &L, const pt_hits *h, const pt_confi
         p.pairs_by_outer[lo][p.n_pairs_by_outer[lo]++] = (int8_t)k;
         p.layer_is_inner[c.pair[k].inner] = 1;
     }
+    for (int k = 0; k < c.n_pairs; k++) p.pair_inner_is_outer[k] = p.n_pairs_by_outer[c.pair[k].inner] > 0;
     p.region[0] = c.region[0];
     p.region[1] = c.region[1];
     for (int r = 0; r < 2; r++)   // tolerance as a distance, rounded up

@@ -94,6 +94,7 @@ struct Params {
     int8_t pairs_by_outer[PT_N_LAYERS][kMaxPairsPerLayer];
     int32_t n_pairs_by_outer[PT_N_LAYERS];
     int8_t layer_is_inner[PT_N_LAYERS];  // 1 if the layer is the inner layer of some pair
+    int8_t pair_inner_is_outer[PT_MAX_PAIRS];  // 1 if cells can end on the pair's inner layer
     pt_ca_cuts region[2];
     float region_tol[2];                 // sqrt(tol_rz2) rounded up
     float fishbone_eps2;

@@ -176,8 +176,9 @@ __global__ void __launch_bounds__(32 * kCaWarps, 12) k_connect(Params p) {
             bool need = false;
             if (x < n_cells && p.cell_alive[x]) {
                 st = 0;
-                const int b = p.cell_inner[x];
-                need = p.in_live[b] > 0;
+                // no cell ends on an inner hit on a layer that is the outer
+                // layer of no pair (most cells start on BPix1)
+                if (p.pair_inner_is_outer[p.cell_pair[x]]) need = p.in_live[p.cell_inner[x]] > 0;
             }
             s_m[w][pos] = st;
             const unsigned m = __ballot_sync(0xffffffffu, need);
