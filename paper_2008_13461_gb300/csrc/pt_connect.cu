@@ -155,7 +155,8 @@ __device__ __forceinline__ int scan_cell(const Params &p, int x, Emit &&emit) {
 __global__ void __launch_bounds__(32 * kCaWarps, 12) k_connect(Params p) {
     constexpr int kPer = 32 * kCaChunk;
     __shared__ int32_t s_q[kCaWarps][kCaQueue][kPer];   // accepted inner cells per chunk position
-    __shared__ int32_t s_m[kCaWarps][kPer];             // edges per chunk position (-1: no live cell)
+    __shared__ int32_t s_m[kCaWarps][kPer];             // edges per chunk position (-1: no live cell,
+                                                        //   -2: a cell that can have no incoming edge)
     __shared__ int16_t s_list[kCaWarps][kPer];          // positions whose inner hit has live cells
     if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -175,10 +176,15 @@ __global__ void __launch_bounds__(32 * kCaWarps, 12) k_connect(Params p) {
             int st = -1;
             bool need = false;
             if (x < n_cells && p.cell_alive[x]) {
-                st = 0;
                 // no cell ends on an inner hit on a layer that is the outer
-                // layer of no pair (most cells start on BPix1)
-                if (p.pair_inner_is_outer[p.cell_pair[x]]) need = p.in_live[p.cell_inner[x]] > 0;
+                // layer of no pair (most cells start on BPix1): such a cell
+                // has no incoming edges, and no edge range is written for
+                // it (-2; the search records read none)
+                st = -2;
+                if (p.pair_inner_is_outer[p.cell_pair[x]]) {
+                    st = 0;
+                    need = p.in_live[p.cell_inner[x]] > 0;
+                }
             }
             s_m[w][pos] = st;
             const unsigned m = __ballot_sync(0xffffffffu, need);

@@ -26,7 +26,9 @@ __global__ void __launch_bounds__(kThreads) k_edge_records(Params p) {
     const int64_t ne = min((int64_t)p.counters[C_EDGES], p.cap_edges);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
         const int src = p.edge_src[e];
-        const int2 r = p.edge_rng[src];
+        // a cell starting on a layer no cell ends on has no incoming edges
+        // (and the connection wrote no range for it)
+        const int2 r = p.pair_inner_is_outer[p.cell_pair[src]] ? p.edge_rng[src] : make_int2(0, 0);
         const int bi = p.cell_inner[src];
         p.erec[e] = make_int4(src, r.x, r.y, p.perm[bi] * 2 + (root_layer(p.blayer[bi]) ? 1 : 0));
     }
