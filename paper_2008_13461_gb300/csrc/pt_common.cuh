@@ -24,6 +24,7 @@ enum Counter {
     C_CA_PENDING = 12,    // CA connection: cells left to the exact pass
     C_DB_PENDING = 13,    // doublets: outer hits left to the exact pass
     C_FB_PENDING = 14,    // Fishbone: outer hits left to the exact pass
+    C_DB_NEXT = 15,       // doublets: next outer hits to take
     C_TRK_CNT = 16,       // tracks with 3, 4, 5, 6..8 hits (4 slots)
     C_TRK_CUR = 20,       // next track index of each of those classes (4 slots)
     C_FB_HUGE = 24,       // Fishbone: outer hits listed for the largest warps

@@ -1,7 +1,7 @@
 // Step a1: doublets on layer pairs (Sec. 3.2, cuts of Table 1).
 //
-// Doublets: a group of G lanes owns one outer hit (persistent grid-stride
-// over the binned hits).  For every layer pair ending on the outer hit's
+// Doublets: a group of G lanes owns one outer hit (the warps take the binned
+// hits from a queue, in order).  For every layer pair ending on the outer hit's
 // layer it derives the phi window (PhiW) and a conservative window along z
 // (barrel) or r (disk) from ZIP and ZW, with margins above float32
 // rounding, and sweeps the inner tiles row by row: consecutive lanes load consecutive
@@ -190,12 +190,20 @@ __global__ void __launch_bounds__(kThreads, 5) k_doublets(Params p) {
     __shared__ unsigned long long s_cand[PT_MAX_PAIRS];
     if (threadIdx.x < PT_MAX_PAIRS) s_cand[threadIdx.x] = 0;
     __syncthreads();
-    const int lane = threadIdx.x % G, grp = threadIdx.x / G;
-    const int gshift = (threadIdx.x & 31) & ~(G - 1);
+    const int lane = threadIdx.x % G, grp = threadIdx.x / G, wl = threadIdx.x & 31;
+    const int gshift = wl & ~(G - 1);
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << gshift);
     const int n_binned = p.bin_cnt[p.n_bins];
-    for (int o = blockIdx.x * kGroups + grp; o < n_binned; o += gridDim.x * kGroups) {
-        if (!doublets_hit<G, false>(p, o, lane, gmask, gshift, s_inner[grp], s_pair[grp], kBuf, s_cand) &&
+    // the warps take the binned outer hits in order, 32 / G at a time: the
+    // cells are laid out nearly in the order of their outer hits
+    for (;;) {
+        int o0 = 0;
+        if (wl == 0) o0 = atomicAdd(p.counters + C_DB_NEXT, 32 / G);
+        o0 = __shfl_sync(0xffffffffu, o0, 0);
+        if (o0 >= n_binned) break;
+        const int o = o0 + wl / G;
+        if (o < n_binned &&
+            !doublets_hit<G, false>(p, o, lane, gmask, gshift, s_inner[grp], s_pair[grp], kBuf, s_cand) &&
             lane == 0) {
             // listed in hit_bin, free once the hits are binned (one slot per hit)
             p.hit_bin[atomicAdd(p.counters + C_DB_PENDING, 1)] = o;
