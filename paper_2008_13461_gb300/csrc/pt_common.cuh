@@ -29,6 +29,7 @@ enum Counter {
     C_TRK_CUR = 20,       // next track index of each of those classes (4 slots)
     C_FB_HUGE = 24,       // Fishbone: outer hits listed for the largest warps
     C_FB_HUGE_NEXT = 25,  // Fishbone: next of those to take
+    C_CA_NEXT = 26,       // CA connection: next chunk of cells to take
     C_PAIR_CAND = 32      // doublet candidates per layer pair (64-bit, PT_MAX_PAIRS of them)
 };
 

@@ -25,9 +25,10 @@
 // resident blocks of 4 warps per SM (40 registers, a few spilled to L1),
 // which hides more of that latency than 8 blocks without spills did.
 //
-// A warp takes 128 consecutive cells at a time.  Only cells whose inner hit
-// has live cells ending on it have candidates at all (about a quarter), so
-// the warp first lists those and then runs their searches on full lanes.
+// A warp takes 128 consecutive cells at a time, in order from a queue.
+// Only cells whose inner hit has live cells ending on it have candidates at
+// all (about a quarter), so the warp first lists those and then runs their
+// searches on full lanes.
 // The incoming edges of a cell are written contiguously (the depth-first
 // search walks them backwards from the cell's edge range); the warp
 // reserves the edges of its 128 cells with one atomic, each cell remembers
@@ -162,9 +163,15 @@ __global__ void __launch_bounds__(32 * kCaWarps, 12) k_connect(Params p) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned below = (1u << lane) - 1u;
     const int64_t n_cells = min((int64_t)p.counters[C_CELLS], p.cap_cells);
-    const int64_t n_chunks = (n_cells + kPer - 1) / kPer;
-    for (int64_t ch = (int64_t)blockIdx.x * kCaWarps + w; ch < n_chunks; ch += (int64_t)gridDim.x * kCaWarps) {
-        const int64_t x0 = ch * kPer;
+    const int n_chunks = (int)((n_cells + kPer - 1) / kPer);
+    // the warps take the chunks in order from a queue: the chunks in flight
+    // are neighbours, and so are the middle hits whose sorted cells they read
+    for (;;) {
+        int ch = 0;
+        if (lane == 0) ch = atomicAdd(p.counters + C_CA_NEXT, 1);
+        ch = __shfl_sync(0xffffffffu, ch, 0);
+        if (ch >= n_chunks) break;
+        const int64_t x0 = (int64_t)ch * kPer;
         // 1) live cells, and a list of those with candidates at all (the
         //    inner hit has live cells ending on it), so that the searches
         //    run on full warps
