@@ -1,14 +1,15 @@
 // Step a1: doublets on layer pairs (Sec. 3.2, cuts of Table 1).
 //
 // Doublets: a group of G lanes owns one outer hit (the warps take the binned
-// hits from a queue, in order).  For every layer pair ending on the outer hit's
-// layer it derives the phi window (PhiW) and a conservative window along z
-// (barrel) or r (disk) from ZIP and ZW, with margins above float32
-// rounding, and sweeps the inner tiles row by row: consecutive lanes load consecutive
-// binned hits (coalesced), evaluate ZW, ZIP, PhiW, PT exactly, and compact
-// the accepted ones with a ballot into a shared-memory buffer.  The cells of
-// one outer hit are written contiguously, so the cells sharing an outer hit
-// (needed by the Fishbone and the CA connection) form one range.
+// hits from a queue, in order).  For every layer pair ending on the outer
+// hit's layer it derives the phi window (PhiW) and a conservative window
+// along z (barrel) or r (disk) from ZIP and ZW, with margins above float32
+// rounding, and sweeps the inner tiles' rows of that window laid end to end:
+// consecutive lanes load consecutive binned hits (coalesced), evaluate ZW,
+// ZIP, PhiW, PT exactly, and compact the accepted ones with a ballot into a
+// shared-memory buffer.  The cells of one outer hit are written
+// contiguously, so the cells sharing an outer hit (needed by the Fishbone
+// and the CA connection) form one range.
 #include "pt_common.cuh"
 #include "pt_kernels.cuh"
 
@@ -54,7 +55,7 @@ __device__ __forceinline__ void t_window(const Params &p, const pt_pair_cuts &pc
 // counts of the candidate inner hits tested, summed in shared memory.
 template <int G, bool kWrite, bool kExact>
 __device__ int sweep_outer(const Params &p, int o, int lane, unsigned gmask, int gshift, int32_t *s_inner,
-                           uint8_t *s_pair, int cap, int64_t base, bool *undecided,
+                           uint8_t *s_pair, int32_t *s_row, int cap, int64_t base, bool *undecided,
                            unsigned long long *s_cand = nullptr) {
     const float4 ho = __ldg(p.bh + o);
     const float xo = ho.x, yo = ho.y, zo = ho.z, ro = ho.w;
@@ -90,16 +91,46 @@ __device__ int sweep_outer(const Params &p, int o, int lane, unsigned gmask, int
             f1 = p.n_phi - 1;
         }
         const int row0 = (ev * PT_N_LAYERS + pc.inner) * p.n_phi;
+        const int nrows = f1 - f0 + 1;
         unsigned cand = 0;
-        for (int f = f0; f <= f1; f++) {
-            const int fb = ((f % p.n_phi) + p.n_phi) % p.n_phi;
-            const int tile = (row0 + fb) * p.n_t;
-            const int beg = p.bin_cnt[tile + tb0], end = p.bin_cnt[tile + tb1 + 1];
-            cand += (unsigned)(end - beg);
-            for (int i0 = beg; i0 < end; i0 += G) {
-                const int i = i0 + lane;
+        // The rows of the window are separate ranges of the binned hits,
+        // about as long as a group is wide: G of them at a time are laid
+        // end to end in one range of slots, so the lanes stay busy across
+        // row ends.  s_row holds, per row, the offset from slot to binned
+        // index and the row's end in slot space.
+        for (int r0 = 0; r0 < nrows; r0 += G) {
+            int beg = 0, len = 0;
+            if (r0 + lane < nrows) {
+                const int f = f0 + r0 + lane;
+                const int fb = ((f % p.n_phi) + p.n_phi) % p.n_phi;
+                const int tile = (row0 + fb) * p.n_t;
+                beg = p.bin_cnt[tile + tb0];
+                len = p.bin_cnt[tile + tb1 + 1] - beg;
+            }
+            int incl = len;
+#pragma unroll
+            for (int d = 1; d < G; d <<= 1) {
+                const int t = __shfl_up_sync(gmask, incl, d, G);
+                if (lane >= d) incl += t;
+            }
+            const int total = __shfl_sync(gmask, incl, G - 1, G);
+            cand += (unsigned)total;
+            if (total == 0) continue;
+            __syncwarp(gmask);       // the previous rows' table is no longer read
+            s_row[lane] = beg - (incl - len);
+            s_row[G + lane] = incl;
+            __syncwarp(gmask);
+            for (int s0 = 0; s0 < total; s0 += G) {
+                const int sl = s0 + lane;
                 int v = 0;     // 1 accepted, 0 rejected, 2|3 undecided (kExact = false)
-                if (i < end) {
+                int i = 0;
+                if (sl < total) {
+                    // the slot's row: the first whose end lies beyond it
+                    int j = 0;
+#pragma unroll
+                    for (int h = G / 2; h > 0; h >>= 1)
+                        if (s_row[G + j + h - 1] <= sl) j += h;
+                    i = sl + s_row[j];
                     const float4 hi = __ldg(p.bh + i);
                     const float xi = hi.x, yi = hi.y, zi = hi.z, ri = hi.w;
                     if (zi >= pc.zlo && zi <= pc.zhi) {
@@ -145,10 +176,11 @@ __device__ int sweep_outer(const Params &p, int o, int lane, unsigned gmask, int
 // false without writing anything when a candidate is undecided.
 template <int G, bool kExact>
 __device__ __forceinline__ bool doublets_hit(const Params &p, int o, int lane, unsigned gmask, int gshift,
-                                             int32_t *s_inner, uint8_t *s_pair, int cap,
+                                             int32_t *s_inner, uint8_t *s_pair, int32_t *s_row, int cap,
                                              unsigned long long *s_cand = nullptr) {
     bool und = false;
-    const int n = sweep_outer<G, false, kExact>(p, o, lane, gmask, gshift, s_inner, s_pair, cap, 0, &und, s_cand);
+    const int n = sweep_outer<G, false, kExact>(p, o, lane, gmask, gshift, s_inner, s_pair, s_row, cap, 0, &und,
+                                                 s_cand);
     if (!kExact && __ballot_sync(gmask, und)) return false;
     int64_t base = 0;
     if (lane == 0 && n > 0) base = atomicAdd(p.counters + C_CELLS, n);
@@ -166,7 +198,7 @@ __device__ __forceinline__ bool doublets_hit(const Params &p, int o, int lane, u
             }
         }
     } else {
-        sweep_outer<G, true, kExact>(p, o, lane, gmask, gshift, nullptr, nullptr, 0, base, &und);
+        sweep_outer<G, true, kExact>(p, o, lane, gmask, gshift, nullptr, nullptr, s_row, 0, base, &und);
     }
     if (lane == 0) {
         p.in_off[o] = (int32_t)base;
@@ -187,6 +219,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_doublets(Params p) {
     constexpr int kBuf = 32 * G;   // 40 KB of shared memory per block for every G
     __shared__ int32_t s_inner[kGroups][kBuf];
     __shared__ uint8_t s_pair[kGroups][kBuf];
+    __shared__ int32_t s_row[kGroups][2 * G];
     __shared__ unsigned long long s_cand[PT_MAX_PAIRS];
     if (threadIdx.x < PT_MAX_PAIRS) s_cand[threadIdx.x] = 0;
     __syncthreads();
@@ -203,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_doublets(Params p) {
         if (o0 >= n_binned) break;
         const int o = o0 + wl / G;
         if (o < n_binned &&
-            !doublets_hit<G, false>(p, o, lane, gmask, gshift, s_inner[grp], s_pair[grp], kBuf, s_cand) &&
+            !doublets_hit<G, false>(p, o, lane, gmask, gshift, s_inner[grp], s_pair[grp], s_row[grp], kBuf, s_cand) &&
             lane == 0) {
             // listed in hit_bin, free once the hits are binned (one slot per hit)
             p.hit_bin[atomicAdd(p.counters + C_DB_PENDING, 1)] = o;
@@ -219,12 +252,13 @@ __global__ void __launch_bounds__(kThreads) k_doublets_exact(Params p) {
     constexpr int G = 8, kGroups = kThreads / G, kBuf = 32 * G;
     __shared__ int32_t s_inner[kGroups][kBuf];
     __shared__ uint8_t s_pair[kGroups][kBuf];
+    __shared__ int32_t s_row[kGroups][2 * G];
     const int lane = threadIdx.x % G, grp = threadIdx.x / G;
     const int gshift = (threadIdx.x & 31) & ~(G - 1);
     const unsigned gmask = ((1u << G) - 1u) << gshift;
     const int n = p.counters[C_DB_PENDING];
     for (int k = blockIdx.x * kGroups + grp; k < n; k += gridDim.x * kGroups)
-        doublets_hit<G, true>(p, p.hit_bin[k], lane, gmask, gshift, s_inner[grp], s_pair[grp], kBuf);
+        doublets_hit<G, true>(p, p.hit_bin[k], lane, gmask, gshift, s_inner[grp], s_pair[grp], s_row[grp], kBuf);
 }
 
 void launch_doublets(const Params &p, int lanes, int grid, cudaStream_t s) {
