@@ -54,7 +54,7 @@ bool layout(const pt_hits *h, const pt_config *cfg, WsLayout &L) {
     L.in_off = take(4 * nh);
     L.in_cnt = take(4 * nh);
     L.in_live = take(4 * nh);
-    L.hk = take(8 * nh);
+    L.hk = take(16 * nh);
     L.ck = take(4 * nc);
     L.sk = take(8 * nc);
     L.sci = take(4 * nc);
@@ -171,7 +171,7 @@ Params make_params(void *ws, const WsLayout &L, const pt_hits *h, const pt_confi
     p.perm = (int32_t *)(w + L.perm);
     p.in_off = (int32_t *)(w + L.in_off);
     p.in_cnt = (int32_t *)(w + L.in_cnt);
-    p.hk = (float2 *)(w + L.hk);
+    p.hk = (float4 *)(w + L.hk);
     p.ck = (float *)(w + L.ck);
     p.sk = (float2 *)(w + L.sk);
     p.sci = (int32_t *)(w + L.sci);

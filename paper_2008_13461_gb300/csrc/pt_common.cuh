@@ -33,6 +33,18 @@ enum Counter {
     C_PAIR_CAND = 32      // doublet candidates per layer pair (64-bit, PT_MAX_PAIRS of them)
 };
 
+// Slope-key bucket of a live incoming cell of a hit with n of them (lowest
+// key k0, inverse bucket width iw): the Fishbone orders the cells by it and
+// the connection searches by it, so both evaluate these same roundings.
+// For an integer b in [1, nb - 1], sk_bucket(key) < b exactly when
+// sk_coord(key) < b (truncation of a coordinate below b is below b, of one
+// at or above b is at or above b), which compares without a conversion.
+__device__ __forceinline__ int sk_buckets(int n) { return max(32, 1 << (32 - __clz(max(n, 1) - 1))); }
+__device__ __forceinline__ float sk_coord(float key, float k0, float iw) { return __fmul_rn(__fsub_rn(key, k0), iw); }
+__device__ __forceinline__ int sk_bucket(float key, float k0, float iw, int nb) {
+    return min(max(__float2int_rz(sk_coord(key, k0, iw)), 0), nb - 1);
+}
+
 // class of a track by its hit count: 3, 4, 5, 6..8 -> 0..3
 __device__ __forceinline__ int track_class(int n) { return min(n, 6) - 3; }
 
@@ -66,7 +78,8 @@ struct Params {
                                          //   incoming edges, input index of its inner hit * 2 + root
     int32_t *leaf_list;
     float *ck;                           // R-z slope key of each cell w.r.t. its outer hit (scratch)
-    float2 *hk;                          // per hit: max sqrt(1+key^2), min gap of its incoming cells
+    float4 *hk;                          // per hit: max sqrt(1+key^2) and min gap of its incoming
+                                         //   cells; lowest key and inverse bucket width of the live ones
     int32_t *in_live;                    // per hit: live incoming cells
     float2 *sk;                          // live incoming cells of each hit sorted by slope key:
     int32_t *sci;                        //   (key, inner hit as int bits) and the cell index

@@ -4,10 +4,11 @@
 //
 // Cells (b,c) are taken in cell order (cells are grouped by their outer hit
 // c, so neighbouring threads work on neighbouring middle hits).
-// The live cells ending on b were written by the Fishbone kernel sorted by
-// their R-z slope key relative to b, with their inner hits, so the
-// candidates (a,b) of a cell are a contiguous run of that array, found by
-// binary search (the runs of neighbouring hits stay in L2).
+// The live cells ending on b were written by the Fishbone kernel ordered by
+// a bucket of their R-z slope key relative to b (monotone in the key, about
+// one cell per bucket), with their inner hits, so the candidates (a,b) of a
+// cell lie in a contiguous run of that array (the buckets of its key
+// window), found by binary search over the buckets.
 //
 // The R-z cut is very tight, so it is first used as a window on the slope
 // key.  For a barrel b, with key = dz/dr of a segment,
@@ -21,9 +22,9 @@
 // window test itself, a float32 R-z test with an error bound and then the
 // exact predicate chain decide.
 //
-// The kernel waits on dependent L2 loads, so it is compiled for 12
-// resident blocks of 4 warps per SM (40 registers, a few spilled to L1),
-// which hides more of that latency than 8 blocks without spills did.
+// The kernel waits on dependent L2 loads, so it is compiled for 10
+// resident blocks of 4 warps per SM (48 registers), which hides more of that
+// latency than 8 blocks did, and spills less than 12.
 //
 // A warp takes 128 consecutive cells at a time, in order from a queue.
 // Only cells whose inner hit has live cells ending on it have candidates at
@@ -101,12 +102,13 @@ __device__ __forceinline__ int warp_excl(int v, int lane, int &total) {
     return incl - v;
 }
 
-// first position of s[0, n) whose key is >= lo (keys ascending)
-__device__ __forceinline__ int lower_key(const float2 *s, int n, float lo) {
-    int l = 0, h = n;
+// first position of s[0, n) whose key's bucket is >= bk (buckets ascending)
+__device__ __forceinline__ int lower_bucket(const float2 *s, int n, int bk, float k0, float iw) {
+    const float fb = (float)bk;
+    int l = 0, h = bk > 0 ? n : 0;
     while (l < h) {
         const int m = (l + h) >> 1;
-        if (__ldg(s + m).x < lo) l = m + 1;
+        if (sk_coord(__ldg(s + m).x, k0, iw) < fb) l = m + 1;
         else h = m;
     }
     return l;
@@ -127,7 +129,7 @@ __device__ __forceinline__ int scan_cell(const Params &p, int x, Emit &&emit) {
     const bool disk = p.layer[p.blayer[b]].kind == PT_LAYER_DISK;
     const pt_ca_cuts rg = p.region[disk ? 1 : 0];
     const float tol = p.region_tol[disk ? 1 : 0];
-    const float2 hk = p.hk[b];
+    const float4 hk = p.hk[b];
     const float dr = C.r - B.r, dz = C.z - B.z;
     const float num = disk ? dr : dz, den = disk ? dz : dr;
     const float key_c = den != 0.f ? num / den : __int_as_float(0x7f800000);
@@ -140,11 +142,16 @@ __device__ __forceinline__ int scan_cell(const Params &p, int x, Emit &&emit) {
     const float lo = key_c - wdt - sl;
     float hi = key_c + wdt + sl;
     if (!(hi == hi)) hi = __int_as_float(0x7f800000);
+    // the cells are ordered by a bucket of their key, monotone in the key:
+    // the run searched is that of the buckets of [lo, hi]
     const float2 *S = p.sk + b0;
+    const int nb = sk_buckets(ns);
+    const int bhi = sk_bucket(hi, hk.z, hk.w, nb);
+    const float fend = bhi < nb - 1 ? (float)(bhi + 1) : __int_as_float(0x7f800000);
     int n = 0;
-    for (int r = lo > -3.4e38f ? lower_key(S, ns, lo) : 0; r < ns; r++) {
+    for (int r = lower_bucket(S, ns, sk_bucket(lo, hk.z, hk.w, nb), hk.z, hk.w); r < ns; r++) {
         const float2 e = __ldg(S + r);
-        if (e.x > hi) break;
+        if (sk_coord(e.x, hk.z, hk.w) >= fend) break;     // a bucket above hi's
         if (!(fabsf(e.x - key_c) <= wdt)) continue;
         const int v = connects<kExact>(p, __ldg(p.bh + __float_as_int(e.y)), B, C, rg);
         if (v == 2) return -2;
@@ -153,7 +160,7 @@ __device__ __forceinline__ int scan_cell(const Params &p, int x, Emit &&emit) {
     return n;
 }
 
-__global__ void __launch_bounds__(32 * kCaWarps, 12) k_connect(Params p) {
+__global__ void __launch_bounds__(32 * kCaWarps, 10) k_connect(Params p) {
     constexpr int kPer = 32 * kCaChunk;
     __shared__ int32_t s_q[kCaWarps][kCaQueue][kPer];   // accepted inner cells per chunk position
     __shared__ int32_t s_m[kCaWarps][kPer];             // edges per chunk position (-1: no live cell,

@@ -28,9 +28,11 @@
 // memory beyond 512.
 //
 // The same pass prepares the CA connection: it writes the live cells of o
-// sorted by their R-z slope key relative to o (with the inner hit and the
-// cell index), and per hit the bounds the slope window needs (taken over
-// all cells of o, a superset of the live ones, so the window only widens).
+// ordered by a bucket of their R-z slope key relative to o (with the inner
+// hit and the cell index; the bucket is monotone in the key, about one cell
+// per bucket, free order inside), the bucket parameters, and per hit the
+// bounds the slope window needs (taken over all cells of o, a superset of
+// the live ones, so the window only widens).
 #include "pt_common.cuh"
 #include "pt_kernels.cuh"
 
@@ -117,6 +119,8 @@ __device__ __forceinline__ void warp_exclusive_scan(int *a, int nb, int lane) {
 template <int W, int M, int NB, bool kGlobal, bool kExact, bool C>
 __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64_t b, int lane, int w,
                                             float unit_thr, float du, FbSmem<W, M, NB, C> &sm) {
+    // NB: at least the buckets of M cells (sk_buckets), and of the direction sort
+    static_assert(NB >= 32 && NB >= M && (NB & (NB - 1)) == 0, "bucket array too small");
     if (!kExact && n > M) return -1;
     const float4 ho = __ldg(p.bh + o);
     const bool disk = p.layer[p.blayer[o]].kind == PT_LAYER_DISK;
@@ -166,7 +170,7 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
         gmin = fminf(gmin, __shfl_xor_sync(0xffffffffu, gmin, d));
     }
     const float kmax = sqrtf(1.0f + k2max);        // max of sqrt(1 + key^2)
-    if (lane == 0 && starts) p.hk[o] = make_float2(kmax, gmin);
+    if (lane == 0 && starts) reinterpret_cast<float2 *>(p.hk + o)[0] = make_float2(kmax, gmin);
     __syncwarp();
 
     bool und = false;
@@ -301,43 +305,37 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
             smin = fminf(smin, __shfl_xor_sync(0xffffffffu, smin, d));
             smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, d));
         }
-        // counting sort into about one bucket per cell, then the exact rank
-        // inside the bucket: key, ties by position
-        const int nb = min(NB, max(32, 1 << (32 - __clz(max(nl, 1) - 1))));
+        // counting sort into about one bucket per cell; the connection
+        // searches by bucket, so the order inside a bucket is free
+        const int nb = sk_buckets(nl);
         const float span = fmaxf(smax - smin, fmaxf(fabsf(smin), fabsf(smax)) * 1e-6f);
         const float iw = span > 0.f && span <= 3.4e38f ? (float)nb / span : 0.f;
         for (int q = lane; q < nb; q += 32) sm.pos[w][q] = 0;
         __syncwarp();
         for (int j = lane; j < n; j += 32) {
             if (sm.dead[w][j]) continue;
-            const int bk = min(max((int)((sm.rec[w][j].x - smin) * iw), 0), nb - 1);
+            const int bk = sk_bucket(sm.rec[w][j].x, smin, iw, nb);
             sm.meta[w][j] = bk;
             atomicAdd(&sm.pos[w][bk], 1);
         }
         __syncwarp();
         warp_exclusive_scan(sm.pos[w], nb, lane);
         __syncwarp();
-        for (int j = lane; j < n; j += 32)
-            if (!sm.dead[w][j]) sm.idx[w][atomicAdd(&sm.pos[w][sm.meta[w][j]], 1)] = (int16_t)j;
-        __syncwarp();
         for (int j = lane; j < n; j += 32) {
             if (sm.dead[w][j]) continue;
             const float4 r = sm.rec[w][j];
-            const int bk = sm.meta[w][j];
-            const int e = sm.pos[w][bk];
-            int rank = bk > 0 ? sm.pos[w][bk - 1] : 0;
-            for (int q = rank; q < e; q++) {
-                const int i = sm.idx[w][q];
-                const float ki = sm.rec[w][i].x;
-                rank += ki < r.x || (ki == r.x && i < j);
-            }
-            p.sk[b + rank] = make_float2(r.x, r.y);
-            p.sci[b + rank] = (int32_t)(b + j);
+            const int q = atomicAdd(&sm.pos[w][sm.meta[w][j]], 1);
+            p.sk[b + q] = make_float2(r.x, r.y);
+            p.sci[b + q] = (int32_t)(b + j);
         }
-        if (lane == 0) p.in_live[o] = nl;
+        if (lane == 0) {
+            p.in_live[o] = nl;
+            reinterpret_cast<float2 *>(p.hk + o)[1] = make_float2(smin, iw);
+        }
     } else {
-        // (only outer hits with very many cells) rank by direct comparison
-        int nl = 0;
+        // (only outer hits with very many cells) rank by direct comparison:
+        // sorted keys, so sorted buckets too
+        float smin = __int_as_float(0x7f800000), smax = -smin;
         for (int j = lane; j < n; j += 32) {
             if (!p.cell_alive[b + j]) continue;
             const float key = p.ck[b + j];
@@ -350,12 +348,25 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
             }
             p.sk[b + rank] = make_float2(key, __int_as_float(ii));
             p.sci[b + rank] = (int32_t)(b + j);
+            if (fabsf(key) <= 3.4e38f) {
+                smin = fminf(smin, key);
+                smax = fmaxf(smax, key);
+            }
             alive++;
         }
-        nl = alive;
+        int nl = alive;
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) nl += __shfl_xor_sync(0xffffffffu, nl, d);
-        if (lane == 0) p.in_live[o] = nl;
+        for (int d = 16; d > 0; d >>= 1) {
+            nl += __shfl_xor_sync(0xffffffffu, nl, d);
+            smin = fminf(smin, __shfl_xor_sync(0xffffffffu, smin, d));
+            smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, d));
+        }
+        const float span = fmaxf(smax - smin, fmaxf(fabsf(smin), fabsf(smax)) * 1e-6f);
+        const float iw = span > 0.f && span <= 3.4e38f ? (float)sk_buckets(nl) / span : 0.f;
+        if (lane == 0) {
+            p.in_live[o] = nl;
+            reinterpret_cast<float2 *>(p.hk + o)[1] = make_float2(smin, iw);
+        }
     }
     __syncwarp();
     return alive;
