@@ -203,6 +203,20 @@ Params make_params(void *ws, const WsLayout &L, const pt_hits *h, const pt_confi
         p.layer_is_inner[c.pair[k].inner] = 1;
     }
     for (int k = 0; k < c.n_pairs; k++) p.pair_inner_is_outer[k] = p.n_pairs_by_outer[c.pair[k].inner] > 0;
+    // Fishbone slots: the distinct inner layers of each outer layer, ranked
+    for (int lo = 0; lo < PT_N_LAYERS; lo++) {
+        int inner_of_slot[kMaxPairsPerLayer], n_slots = 0;
+        for (int q = 0; q < p.n_pairs_by_outer[lo]; q++) {
+            const int k = p.pairs_by_outer[lo][q];
+            int sl = 0;
+            while (sl < n_slots && inner_of_slot[sl] != c.pair[k].inner) sl++;
+            if (sl == n_slots) inner_of_slot[n_slots++] = c.pair[k].inner;
+            p.pair_slot[k] = (int8_t)sl;
+        }
+        int sh = 0;
+        while ((1 << sh) < n_slots) sh++;
+        p.fb_slot_shift[lo] = (int8_t)sh;
+    }
     p.region[0] = c.region[0];
     p.region[1] = c.region[1];
     for (int r = 0; r < 2; r++)   // tolerance as a distance, rounded up

@@ -110,6 +110,8 @@ struct Params {
     int32_t n_pairs_by_outer[PT_N_LAYERS];
     int8_t layer_is_inner[PT_N_LAYERS];  // 1 if the layer is the inner layer of some pair
     int8_t pair_inner_is_outer[PT_MAX_PAIRS];  // 1 if cells can end on the pair's inner layer
+    int8_t pair_slot[PT_MAX_PAIRS];      // rank of the pair's inner layer among those of its outer layer
+    int8_t fb_slot_shift[PT_N_LAYERS];   // log2 of a power of two >= the inner layers of the layer
     pt_ca_cuts region[2];
     float region_tol[2];                 // sqrt(tol_rz2) rounded up
     float fishbone_eps2;

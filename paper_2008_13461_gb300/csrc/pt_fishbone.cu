@@ -157,7 +157,7 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
             const float ux = a.x - ho.x, uy = a.y - ho.y, uz = a.z - ho.z;
             const float4 r = make_float4(ux, uy, uz, rsqrtf(ux * ux + uy * uy + uz * uz));
             sm.rec[w][j] = r;
-            sm.meta[w][j] = j | (L << 10);
+            sm.meta[w][j] = j | (L << 10) | (p.pair_slot[p.cell_pair[b + j]] << 26);
             sm.dead[w][j] = 0;
             const float key = fb_key(r, disk, rx, ry);
             bmin = fminf(bmin, key);
@@ -214,20 +214,25 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
             bmin = fminf(bmin, __shfl_xor_sync(0xffffffffu, bmin, d));
             bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, d));
         }
-        // counting sort of the cells into buckets of the direction key
-        // (about one bucket per cell); two keys within du lie at most K
-        // buckets apart (K bounds du / width plus the rounding of the
-        // bucket coordinates, below 3e-4 for up to 1024 buckets)
+        // counting sort of the cells into buckets of (inner layer, direction
+        // key): each inner layer of o has its own aligned range of nbr
+        // buckets (about one bucket per cell), so a cell meets only siblings
+        // on its own layer.  Two keys within du lie at most K buckets apart
+        // (K bounds du / width plus the rounding of the bucket coordinates,
+        // below 3e-4 for up to 1024 buckets).
         const int nb = min(NB, max(32, 1 << (32 - __clz(n - 1))));
+        const int ssh = p.fb_slot_shift[p.blayer[o]];
+        const int nbr = nb >> ssh;
         const float span = fmaxf(bmax - bmin, fmaxf(fabsf(bmin), fabsf(bmax)) * 1e-6f);
-        const float iw = span > 0.f ? (float)nb / span : 0.f;
-        const int K = (int)fminf(du * iw + 3e-4f, (float)nb) + 1;
+        const float iw = span > 0.f ? (float)nbr / span : 0.f;
+        const int K = (int)fminf(du * iw + 3e-4f, (float)nbr) + 1;
         for (int q = lane; q < nb; q += 32) sm.pos[w][q] = 0;
         __syncwarp();
         for (int j = lane; j < n; j += 32) {
             const float key = fb_key(sm.rec[w][j], disk, rx, ry);
-            const int bk = min(max((int)((key - bmin) * iw), 0), nb - 1);
-            sm.meta[w][j] |= bk << 16;
+            const int m = sm.meta[w][j];
+            const int bk = (m >> 26) * nbr + min(max((int)((key - bmin) * iw), 0), nbr - 1);
+            sm.meta[w][j] = (m & 0xffff) | (bk << 16);
             atomicAdd(&sm.pos[w][bk], 1);
         }
         __syncwarp();
@@ -237,19 +242,17 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
         __syncwarp();
         // sm.pos[bk] is now the end of bucket bk.  Each pair once: every cell
         // against the cells after it in its own bucket and the next K
-        // buckets (a superset of its siblings within du of its key); of an
-        // aligned pair the longer cell dies (equal lengths: the larger input
-        // index of the inner hit).
+        // buckets of its layer (a superset of its siblings within du of its
+        // key); of an aligned pair the longer cell dies (equal lengths: the
+        // larger input index of the inner hit).
         for (int q0 = lane; q0 < n; q0 += 32) {
             const int j = sm.idx[w][q0];
             const float4 r1 = sm.rec[w][j];
             const float3 v1 = make_float3(r1.x * r1.w, r1.y * r1.w, r1.z * r1.w);
-            const int m1 = sm.meta[w][j];
-            const int qend = sm.pos[w][min((m1 >> 16) + K, nb - 1)];
+            const int bk1 = sm.meta[w][j] >> 16;
+            const int qend = sm.pos[w][min(bk1 + K, bk1 | (nbr - 1))];
             for (int q = q0 + 1; q < qend; q++) {
                 const int d = sm.idx[w][q];
-                const int m2 = sm.meta[w][d];
-                if ((m1 ^ m2) & kRecLayerMask) continue;
                 const float4 r2 = sm.rec[w][d];
                 const float dx = v1.x - r2.x * r2.w, dy = v1.y - r2.y * r2.w, dz = v1.z - r2.z * r2.w;
                 if (dx * dx + dy * dy + dz * dz > unit_thr) continue;
