@@ -278,13 +278,15 @@ __global__ void __launch_bounds__(32 * kCaWarps, 10) k_connect(Params p) {
     }
 }
 
-// The cells with an undecided candidate, one thread each, with the exact
-// predicates; each reserves its own edges.
+// The cells with an undecided candidate (a few hundred), one thread each,
+// with the exact predicates; each reserves its own edges.
 __global__ void __launch_bounds__(128) k_connect_exact(Params p) {
     if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int n = (int)min((int64_t)p.counters[C_CA_PENDING], p.cap_cells);
     const int32_t *list = reinterpret_cast<const int32_t *>(p.ck);
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    // cells dealt round the blocks first: they spread over the SMs, and a
+    // warp seldom holds two cells whose exact fallbacks would run in turn
+    for (int k = threadIdx.x * gridDim.x + blockIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int x = list[k];
         const int m = scan_cell<true>(p, x, [](int, int64_t) {});
         const int64_t base = m > 0 ? atomicAdd(p.counters + C_EDGES, m) : 0;

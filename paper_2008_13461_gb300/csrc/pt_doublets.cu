@@ -247,18 +247,18 @@ __global__ void __launch_bounds__(kThreads, 5) k_doublets(Params p) {
         atomicAdd(reinterpret_cast<unsigned long long *>(p.counters + C_PAIR_CAND) + threadIdx.x, s_cand[threadIdx.x]);
 }
 
-// Exact pass over the listed outer hits.
+// Exact pass over the listed outer hits (a few hundred): a warp per hit,
+// the hits dealt round the blocks first, so that they spread over the SMs
+// and no warp runs two hits' exact fallbacks one after the other.
 __global__ void __launch_bounds__(kThreads) k_doublets_exact(Params p) {
-    constexpr int G = 8, kGroups = kThreads / G, kBuf = 32 * G;
+    constexpr int G = 32, kGroups = kThreads / G, kBuf = 32 * G;
     __shared__ int32_t s_inner[kGroups][kBuf];
     __shared__ uint8_t s_pair[kGroups][kBuf];
     __shared__ int32_t s_row[kGroups][2 * G];
     const int lane = threadIdx.x % G, grp = threadIdx.x / G;
-    const int gshift = (threadIdx.x & 31) & ~(G - 1);
-    const unsigned gmask = ((1u << G) - 1u) << gshift;
     const int n = p.counters[C_DB_PENDING];
-    for (int k = blockIdx.x * kGroups + grp; k < n; k += gridDim.x * kGroups)
-        doublets_hit<G, true>(p, p.hit_bin[k], lane, gmask, gshift, s_inner[grp], s_pair[grp], s_row[grp], kBuf);
+    for (int k = grp * gridDim.x + blockIdx.x; k < n; k += gridDim.x * kGroups)
+        doublets_hit<G, true>(p, p.hit_bin[k], lane, 0xffffffffu, 0, s_inner[grp], s_pair[grp], s_row[grp], kBuf);
 }
 
 void launch_doublets(const Params &p, int lanes, int grid, cudaStream_t s) {
