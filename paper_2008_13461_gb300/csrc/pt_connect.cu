@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(32 * kCaWarps, 10) k_connect(Params p) {
         //    inner hit has live cells ending on it), so that the searches
         //    run on full warps
         int nlist = 0;
+        unsigned ranged = 0;     // lanes with a cell whose edge range is written
 #pragma unroll
         for (int it = 0; it < kCaChunk; it++) {
             const int pos = it * 32 + lane;
@@ -201,10 +202,14 @@ __global__ void __launch_bounds__(32 * kCaWarps, 10) k_connect(Params p) {
                 }
             }
             s_m[w][pos] = st;
+            ranged |= __ballot_sync(0xffffffffu, st >= 0);
             const unsigned m = __ballot_sync(0xffffffffu, need);
             if (need) s_list[w][nlist + __popc(m & below)] = (int16_t)pos;
             nlist += __popc(m);
         }
+        // a chunk of cells that can have no incoming edge (the cells of
+        // outer hits on BPix2 all start on BPix1) has nothing more to do
+        if (!ranged) continue;
         __syncwarp();
         // 2) the searches
         for (int i = lane; i < nlist; i += 32) {
