@@ -198,6 +198,7 @@ Params make_params(void *ws, const WsLayout &L, const pt_hits *h, const pt_confi
         // PhiW accepts |dphi| <= atan(sqrt(tan2)); the window adds a margin
         // far above float32 rounding of the angles involved
         p.pair_dphi[k] = (float)(atan(sqrt((double)c.pair[k].tan2_dphi)) + 1e-4);
+        p.pair_pt_a[k] = c.pair[k].k_pt > 0.f ? (float)(1.0 / sqrt((double)c.pair[k].k_pt)) : 0.f;
         const int lo = c.pair[k].outer;
         p.pairs_by_outer[lo][p.n_pairs_by_outer[lo]++] = (int8_t)k;
         p.layer_is_inner[c.pair[k].inner] = 1;

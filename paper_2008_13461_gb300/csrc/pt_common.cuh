@@ -105,6 +105,7 @@ struct Params {
     pt_layer layer[PT_N_LAYERS];
     pt_pair_cuts pair[PT_MAX_PAIRS];
     float pair_dphi[PT_MAX_PAIRS];       // azimuthal half window of PhiW (rad)
+    float pair_pt_a[PT_MAX_PAIRS];       // 1 / (2 R) of the PT cut's minimum circumradius R (0: no cut)
     int32_t n_pairs;
     int8_t pairs_by_outer[PT_N_LAYERS][kMaxPairsPerLayer];
     int32_t n_pairs_by_outer[PT_N_LAYERS];

@@ -83,7 +83,20 @@ __device__ int sweep_outer(const Params &p, int o, int lane, unsigned gmask, int
         const float mt = 1e-4f + 1e-6f * fmaxf(fabsf(tlo), fabsf(thi));
         const int tb0 = t_tile(tlo - mt, tmin, tmax, p.n_t);
         const int tb1 = t_tile(thi + mt, tmin, tmax, p.n_t);
-        const float dphi = p.pair_dphi[pi];
+        // The PT cut (circumradius of beam line, inner and outer hit >= R)
+        // accepts an azimuth difference up to |asin(r_o / 2R) - asin(r_i / 2R)|
+        // or from pi - asin(r_o / 2R) - asin(r_i / 2R) on (both radii below
+        // 2R: on a circle through the beam line a chord of length r makes
+        // the angle asin(r / 2R) with the tangent there).  While the second
+        // range lies beyond the pair's PhiW window, the first, taken over the
+        // inner layer's radii with a margin far above the rounding of the
+        // float32 arcsines, narrows the window to this outer hit.
+        float dphi = p.pair_dphi[pi];
+        const float pa = p.pair_pt_a[pi];
+        if (pa > 0.f && ro * pa < 1.f && li.rmax * pa < 1.f) {
+            const float so = asinf(ro * pa), si = asinf(li.rmin * pa), sx = asinf(li.rmax * pa);
+            if (kPi - so - sx > dphi + 1e-3f) dphi = fminf(dphi, fmaxf(so - si, sx - so) + 1e-4f);
+        }
         int f0 = __float2int_rd((phio - dphi + kPi) * (p.n_phi * kTwoPiInv));
         int f1 = __float2int_rd((phio + dphi + kPi) * (p.n_phi * kTwoPiInv));
         if (f1 - f0 + 1 >= p.n_phi) {
