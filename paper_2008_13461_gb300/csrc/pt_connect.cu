@@ -34,8 +34,7 @@
 // search walks them backwards from the cell's edge range); the warp
 // reserves the edges of its 128 cells with one atomic, each cell remembers
 // its first few accepted candidates in shared memory, and a cell with more
-// (rare) scans again to write them all.  Cells with incoming edges join the
-// list the search starts from.
+// (rare) scans again to write them all.
 //
 // The predicates run as float32 filters only; a cell with a candidate they
 // cannot decide (about one in 10^5) is left to a second pass that has the
@@ -228,23 +227,14 @@ __global__ void __launch_bounds__(32 * kCaWarps, 10) k_connect(Params p) {
         __syncwarp();
         // 3) edges of the chunk: one reservation, then each cell's edges
         //    contiguously and its edge range
-        int tot = 0, nleaf = 0;
+        int tot = 0;
 #pragma unroll
-        for (int it = 0; it < kCaChunk; it++) {
-            const int m = s_m[w][it * 32 + lane];
-            tot += max(m, 0);
-            nleaf += m > 0;
-        }
+        for (int it = 0; it < kCaChunk; it++) tot += max(s_m[w][it * 32 + lane], 0);
         int total;
         const int excl = warp_excl(tot, lane, total);
         int64_t base = 0;
         if (lane == 0 && total > 0) base = atomicAdd(p.counters + C_EDGES, total);
         base = __shfl_sync(0xffffffffu, base, 0) + excl;
-        int ltot;
-        const int lexcl = warp_excl(nleaf, lane, ltot);
-        int64_t lb = 0;
-        if (lane == 0 && ltot > 0) lb = atomicAdd(p.counters + C_LEAVES, ltot);
-        lb = __shfl_sync(0xffffffffu, lb, 0) + lexcl;
 #pragma unroll 1
         for (int it = 0; it < kCaChunk; it++) {
             const int pos = it * 32 + lane;
@@ -273,8 +263,6 @@ __global__ void __launch_bounds__(32 * kCaWarps, 10) k_connect(Params p) {
                     });
                 }
                 if (base + m > p.cap_edges) set_flag(p.counters, PT_FLAG_EDGES);
-                if (lb < p.cap_cells) p.leaf_list[lb] = (int32_t)x;
-                lb++;
             }
             p.edge_rng[x] = make_int2((int32_t)base, m);
             base += m;
@@ -305,10 +293,6 @@ __global__ void __launch_bounds__(128) k_connect_exact(Params p) {
         });
         if (base + m > p.cap_edges) set_flag(p.counters, PT_FLAG_EDGES);
         p.edge_rng[x] = make_int2((int32_t)base, m);
-        if (m > 0) {
-            const int lb = atomicAdd(p.counters + C_LEAVES, 1);
-            if (lb < p.cap_cells) p.leaf_list[lb] = x;
-        }
     }
 }
 
