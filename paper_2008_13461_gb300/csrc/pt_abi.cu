@@ -58,7 +58,6 @@ bool layout(const pt_hits *h, const pt_config *cfg, WsLayout &L) {
     L.ck = take(4 * nc);
     L.sk = take(8 * nc);
     L.sci = take(4 * nc);
-    L.leaf_rec = take(16 * (size_t)(cfg->capacity.edges > 0 ? cfg->capacity.edges : 1));
     L.edge_rng = take(8 * nc);
     L.has_out = take(nc);
     L.maxlen = take(4 * nc);
@@ -176,7 +175,6 @@ Params make_params(void *ws, const WsLayout &L, const pt_hits *h, const pt_confi
     p.sk = (float2 *)(w + L.sk);
     p.sci = (int32_t *)(w + L.sci);
     p.in_live = (int32_t *)(w + L.in_live);
-    p.leaf_rec = (int4 *)(w + L.leaf_rec);
     p.edge_rng = (int2 *)(w + L.edge_rng);
     p.has_out = (uint8_t *)(w + L.has_out);
     p.maxlen = (int32_t *)(w + L.maxlen);

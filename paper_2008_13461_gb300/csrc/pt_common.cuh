@@ -17,7 +17,7 @@ constexpr int kCounters = 32 + 2 * PT_MAX_PAIRS;
 // workspace counters (int32 slots at the start of ws)
 enum Counter {
     C_CELLS = 0, C_EDGES = 1, C_TUPLES = 2, C_TRACKS = 3, C_FLAGS = 4, C_FALLBACK = 5,
-    C_ALIVE_CELLS = 6, C_ALIVE_TUPLES = 7, C_LEAF_EDGES = 8,
+    C_ALIVE_CELLS = 6, C_ALIVE_TUPLES = 7,
     C_FB_NEXT = 9,        // Fishbone: next chunk of outer hits to take
     C_FB_BIG = 10,        // Fishbone: outer hits listed for the large warps
     C_FB_BIG_NEXT = 11,   // Fishbone: next listed outer hit to take
@@ -51,7 +51,7 @@ __device__ __forceinline__ int track_class(int n) { return min(n, 6) - 3; }
 // Byte offsets of every workspace array (all 256-byte aligned).
 struct WsLayout {
     size_t counters, bin_cnt, scan_part, hit_bin, hit_rank;
-    size_t bh, blayer, bev, perm, in_off, in_cnt, in_live, hk, ck, sk, sci, leaf_rec, trk_blk;
+    size_t bh, blayer, bev, perm, in_off, in_cnt, in_live, hk, ck, sk, sci, trk_blk;
     size_t edge_rng, has_out, maxlen, erec;
     size_t total;
     int64_t n_bins;        // events * layers * phi bins * t bins
@@ -76,8 +76,6 @@ struct Params {
     int2 *edge_rng;                      // per cell: (first incoming edge, count)
     int4 *erec;                          // per edge: its source cell, that cell's (first, count) of
                                          //   incoming edges, input index of its inner hit * 2 + root
-    int4 *leaf_rec;                      // per edge into a leaf cell: the edge, the leaf, input index
-                                         //   of the leaf's inner hit * 2, that of its outer hit
     float *ck;                           // R-z slope key of each cell w.r.t. its outer hit (scratch)
     float4 *hk;                          // per hit: max sqrt(1+key^2) and min gap of its incoming
                                          //   cells; lowest key and inverse bucket width of the live ones

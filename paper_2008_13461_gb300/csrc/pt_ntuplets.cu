@@ -3,12 +3,11 @@
 //
 // The paper runs one DFS per root along outgoing edges.  Here every maximal
 // path is enumerated from its other end: one thread per edge into a leaf cell
-// (live, no outer neighbour; listed by the pass that writes the edge records)
-// walks incoming edges -- stored contiguously per cell by the connection
-// kernel -- back to cells with no inner neighbour, and emits
-// the path when that cell is a root (inner hit on BPix1, or on BPix2 /
-// FPix1+- which, having no inner neighbour, qualifies) and the path has at
-// least three hits.  Root-to-leaf paths are the same set either way, and no
+// (live, no outer neighbour) walks incoming edges -- stored contiguously per
+// cell by the connection kernel -- back to cells with no inner neighbour,
+// and emits the path when that cell is a root (inner hit on BPix1, or on
+// BPix2 / FPix1+- which, having no inner neighbour, qualifies) and the path
+// has at least three hits.  Root-to-leaf paths are the same set either way, and no
 // outgoing-edge lists need to be built.  Path length is bounded on the host
 // (the layer-pair graph admits no path longer than PT_NMAX hits).
 #include "pt_common.cuh"
@@ -21,34 +20,16 @@ __device__ __forceinline__ bool root_layer(int L) { return L == 0 || L == 1 || L
 // One record per edge with what the search needs of its source cell, so that
 // each step back along a path is one dependent load: the source, its own
 // incoming-edge range, and its inner hit (input index) with the root flag.
-// An edge into a leaf (a live cell with no outer neighbour) is also listed,
-// with the leaf's hits, as a starting point of the search.
 __global__ void __launch_bounds__(kThreads) k_edge_records(Params p) {
     if (upstream_overflow(p, PT_FLAG_CELLS)) return;
     const int64_t ne = min((int64_t)p.counters[C_EDGES], p.cap_edges);
-    const int lane = threadIdx.x & 31;
-    // whole warps run every round, so the listing's ballots see all lanes
-    for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x; e0 < ne; e0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = e0 + threadIdx.x;
-        bool leaf = false;
-        int dst = 0;
-        if (e < ne) {
-            const int src = p.edge_src[e];
-            // a cell starting on a layer no cell ends on has no incoming
-            // edges (and the connection wrote no range for it)
-            const int2 r = p.pair_inner_is_outer[p.cell_pair[src]] ? p.edge_rng[src] : make_int2(0, 0);
-            const int bi = p.cell_inner[src];
-            p.erec[e] = make_int4(src, r.x, r.y, p.perm[bi] * 2 + (root_layer(p.blayer[bi]) ? 1 : 0));
-            dst = p.edge_dst[e];
-            leaf = !p.has_out[dst];
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, leaf);
-        if (!m) continue;
-        int k = 0;
-        if (lane == 0) k = atomicAdd(p.counters + C_LEAF_EDGES, __popc(m));
-        k = __shfl_sync(0xffffffffu, k, 0) + __popc(m & ((1u << lane) - 1u));
-        if (leaf && k < p.cap_edges)
-            p.leaf_rec[k] = make_int4((int32_t)e, dst, p.perm[p.cell_inner[dst]] * 2, p.perm[p.cell_outer[dst]]);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+        const int src = p.edge_src[e];
+        // a cell starting on a layer no cell ends on has no incoming edges
+        // (and the connection wrote no range for it)
+        const int2 r = p.pair_inner_is_outer[p.cell_pair[src]] ? p.edge_rng[src] : make_int2(0, 0);
+        const int bi = p.cell_inner[src];
+        p.erec[e] = make_int4(src, r.x, r.y, p.perm[bi] * 2 + (root_layer(p.blayer[bi]) ? 1 : 0));
     }
 }
 
@@ -107,21 +88,23 @@ __device__ __forceinline__ void dfs_level(const Params &p, DfsPath &pa, int firs
     }
 }
 
-// One thread per edge into a leaf: the leaf and the edge's source cell are
-// the first two cells of the path, searched back from there.
+// One thread per edge; an edge into a leaf (a live cell with no outer
+// neighbour) starts the search: the leaf and the edge's source are the
+// path's first two cells, searched back from there.
 __global__ void __launch_bounds__(kThreads) k_dfs(Params p) {
     if (upstream_overflow(p, PT_FLAG_CELLS)) return;
-    const int64_t n_list = min((int64_t)p.counters[C_LEAF_EDGES], p.cap_edges);
+    const int64_t ne = min((int64_t)p.counters[C_EDGES], p.cap_edges);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_list; k += stride) {
-        const int4 lr = p.leaf_rec[k];
-        const int4 r = p.erec[lr.x];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += stride) {
+        const int c = p.edge_dst[e];
+        if (p.has_out[c]) continue;
+        const int4 r = p.erec[e];
         DfsPath pa;
-        pa.cell[0] = lr.y;
-        pa.hit[0] = lr.z;
+        pa.cell[0] = c;
+        pa.hit[0] = p.perm[p.cell_inner[c]] * 2;
         pa.cell[1] = r.x;
         pa.hit[1] = r.w;
-        dfs_level<1>(p, pa, r.y, r.z, lr.w);
+        dfs_level<1>(p, pa, r.y, r.z, p.perm[p.cell_outer[c]]);
     }
 }
 
