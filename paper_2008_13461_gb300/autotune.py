@@ -19,7 +19,7 @@ import torch
 
 SPACE = (
     ("n_t_bins", (24, 32, 48, 64)),
-    ("n_phi_bins", (32, 48, 64, 96, 128)),
+    ("n_phi_bins", (32, 48, 64, 96, 128, 192, 256)),
     ("doublet_lanes", (4, 8, 16)),
     ("blocks_per_sm", (8, 12, 16, 24, 32)),
 )
