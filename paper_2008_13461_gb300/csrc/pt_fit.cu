@@ -192,7 +192,7 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
         const R th2 = (R)th * th;
         kv[i] = fmax(th2 * sec2, R(1e-20));                   // kink variances: transverse,
         kz[i] = fmax(th2 * sec2 * sec2, R(1e-20));            //   s-z slope
-        if (N > 3) {
+        if (N > 4) {
             vb[i] = recip_r(kv[i]);                           // weights 1/variance
             vg[i] = recip_r(kz[i]);
         }
@@ -224,6 +224,40 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
         Cv[0][0] = var[0] * (kz[1] + t1 + t2) * iD;
         Cv[1][1] = var[1] * (kz[1] + t0 + t2) * iD;
         Cv[0][1] = Cv[1][0] = -(var[0] * g0) * (var[1] * g1) * iD;
+    } else if constexpr (N == 4) {
+        // Two kinks (hits 1, 2): the normal matrix is D + G^T W G, D =
+        // diag(1/var_i), W = diag(1/var_k), G the kinks' 2 x 4 slope
+        // operator.  By Woodbury, with S = W^-1 + G D^-1 G^T (2 x 2) and r =
+        // S^-1 G z: v = z - D^-1 G^T r, cov(v) = D^-1 - D^-1 G^T S^-1 G D^-1,
+        // and chi2 from the residuals, v - z = -D^-1 G^T r and G v = W^-1 r:
+        // sum_i var_i (G^T r)_i^2 + sum_k var_k r_k^2, every term positive.
+        R var[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const R sz = disk[i] ? (R)p.fit.sigma_r * atl : (R)p.fit.sigma_z;
+            var[i] = sz * sz;
+        }
+        const R a0 = ids[1], a2 = ids[2], a1 = -(a0 + a2);      // kink 1 on v0, v1, v2
+        const R b0 = ids[2], b2 = ids[3], b1 = -(b0 + b2);      // kink 2 on v1, v2, v3
+        const R S11 = kz[1] + a0 * a0 * var[0] + a1 * a1 * var[1] + a2 * a2 * var[2];
+        const R S22 = kz[2] + b0 * b0 * var[1] + b1 * b1 * var[2] + b2 * b2 * var[3];
+        const R S12 = a1 * b0 * var[1] + a2 * b1 * var[2];
+        const R q1 = a0 * hz[0] + a1 * hz[1] + a2 * hz[2];
+        const R q2 = b0 * hz[1] + b1 * hz[2] + b2 * hz[3];
+        const R idet = recip_r(S11 * S22 - S12 * S12);
+        const R i11 = S22 * idet, i22 = S11 * idet, i12 = -S12 * idet;
+        const R r1 = i11 * q1 + i12 * q2, r2 = i12 * q1 + i22 * q2;
+        const R e0 = a0 * r1, e1 = a1 * r1 + b0 * r2, e2 = a2 * r1 + b1 * r2, e3 = b2 * r2;     // G^T r
+        v[0] = hz[0] - var[0] * e0;
+        v[1] = hz[1] - var[1] * e1;
+        chi2 = var[0] * e0 * e0 + var[1] * e1 * e1 + var[2] * e2 * e2 + var[3] * e3 * e3 + kz[1] * r1 * r1 +
+               kz[2] * r2 * r2;
+        // (G^T S^-1 G) on v0 (column (a0, 0)) and v1 (column (a1, b0))
+        const R m00 = a0 * a0 * i11, m01 = a0 * (a1 * i11 + b0 * i12);
+        const R m11 = a1 * a1 * i11 + 2 * a1 * b0 * i12 + b0 * b0 * i22;
+        Cv[0][0] = var[0] - var[0] * var[0] * m00;
+        Cv[1][1] = var[1] - var[1] * var[1] * m11;
+        Cv[0][1] = Cv[1][0] = -var[0] * var[1] * m01;
     } else {
         R A[N * (N + 1) / 2], bv[N], wz[N];
 #pragma unroll
@@ -279,6 +313,41 @@ __device__ void fit_track(const Params &p, int64_t k, int32_t t) {
         Cc[0][2] = Cc[2][0] = s2 * a0;
         Cc[1][2] = Cc[2][1] = s2 * a1;
         Cc[2][2] = s2 * (a0 * a0 + a1 * a1 + a2 * a2) + kv[1] * ih3 * ih3;
+    } else if constexpr (N == 4) {
+        // Two kinks, residuals beta_k = (H u)_k + h3_k dk (variances var_k).
+        // Minimising over dk leaves the rank-one penalty w' (c . u)^2 with c
+        // = H^T (h3_2, -h3_1) and w' = 1 / (h3_1^2 var_2 + h3_2^2 var_1); by
+        // Sherman-Morrison, with alpha = w' / (wu + w' |c|^2): u = m - alpha
+        // (c . m) c, cov(u) = (I - alpha c c^T) / wu, dk = t . u with t =
+        // -w' (h3_1 var_2 H_1 + h3_2 var_1 H_2) (H_k the rows of H), cov(u,
+        // dk) = cov(u) t, var(dk) = var_1 var_2 w' + t^T cov(u) t, and chi2 =
+        // wu w' (c . m)^2 / (wu + w' |c|^2).
+        const R s2 = (R)p.fit.sigma_rphi * p.fit.sigma_rphi;
+        const R wu = recip_r(s2);
+        const R h0 = ids[1], h2 = ids[2], h1 = -(h0 + h2);      // kink 1 on u0, u1, u2
+        const R k0 = ids[2], k2 = ids[3], k1 = -(k0 + k2);      // kink 2 on u1, u2, u3
+        const R g1 = R(-0.5) * ((R)ds[1] + ds[2]), g2 = R(-0.5) * ((R)ds[2] + ds[3]);
+        const R wp = recip_r(g1 * g1 * kv[2] + g2 * g2 * kv[1]);
+        const R c0 = g2 * h0, c1 = g2 * h1 - g1 * k0, c2 = g2 * h2 - g1 * k1, c3 = -g1 * k2;
+        const R cc0 = c1 * c1 + c2 * c2 + c3 * c3, cc1 = c0 * c0 + c2 * c2 + c3 * c3;
+        const R cc = c0 * c0 + cc0;
+        const R iden = recip_r(wu + wp * cc), alpha = wp * iden;
+        const R cm = c0 * m[0] + c1 * m[1] + c2 * m[2] + c3 * m[3];
+        const R u0 = m[0] - alpha * cm * c0, u1 = m[1] - alpha * cm * c1;
+        const R u2 = m[2] - alpha * cm * c2, u3 = m[3] - alpha * cm * c3;
+        const R p1 = g1 * kv[2] * wp, p2 = g2 * kv[1] * wp;
+        const R t0 = -p1 * h0, t1 = -(p1 * h1 + p2 * k0), t2 = -(p1 * h2 + p2 * k1), t3 = -p2 * k2;
+        xu[0] = u0;
+        xu[1] = u1;
+        xu[2] = t0 * u0 + t1 * u1 + t2 * u2 + t3 * u3;
+        const R ct = c0 * t0 + c1 * t1 + c2 * t2 + c3 * t3;
+        Cc[0][0] = s2 * (wu + wp * cc0) * iden;
+        Cc[1][1] = s2 * (wu + wp * cc1) * iden;
+        Cc[0][1] = Cc[1][0] = -s2 * alpha * c0 * c1;
+        Cc[0][2] = Cc[2][0] = s2 * (t0 - alpha * c0 * ct);
+        Cc[1][2] = Cc[2][1] = s2 * (t1 - alpha * c1 * ct);
+        Cc[2][2] = kv[1] * kv[2] * wp + s2 * (t0 * t0 + t1 * t1 + t2 * t2 + t3 * t3 - alpha * ct * ct);
+        chi2 += wu * wp * cm * cm * iden;
     } else {
         constexpr int M = N + 1;
         R B[M * (M + 1) / 2], bu[M];
