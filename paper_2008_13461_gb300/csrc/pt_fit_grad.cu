@@ -130,9 +130,13 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
     const double ta = 0.5 * k0 * dab;
     const bool ta_in = fabs(ta) < 1.0;
     const double tac = fmin(fmax(ta, -1.0), 1.0);
-    const double psi0 = atan2(aby, abx) - asin(tac);
-    double sn, cs;
-    sincos(psi0, &sn, &cs);
+    // sin and cos of psi0 = atan2(aby, abx) - asin(ta) by the angle
+    // difference formula: (ex, ey) = (cos, sin) of the first, (ct, ta) of
+    // the second (nothing needs the angle itself)
+    const double idab0 = dab > 0.0 ? rcp_d(dab) : 0.0;
+    const double ex = dab > 0.0 ? abx * idab0 : 1.0, ey = aby * idab0;
+    const double ct = sqrt_d(1.0 - tac * tac);
+    const double cs = ex * ct + ey * tac, sn = ey * ct - ex * tac;
     // arc lengths and offsets from the pre-fit circle
     double s[N], m[N], dxs[N], dys[N], dist[N], qs[N], Xs[N], Ys[N], Us[N], Sq[N], i1Sq[N], asc[N], asq[N];
 #pragma unroll
@@ -273,9 +277,23 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
     // 5) perigee
     const double kf = k0 + dk;
     const double px = x[0] - xs[0] * sn, py = y[0] + xs[0] * cs;
-    const double psi = psi0 + (xs[1] - xs[0]) * ids[1] - dk * 0.5 * ds[1];
+    // psi = psi0 + dl, dl = (u1 - u0) ids1 - dk ds1 / 2 (for triplets
+    // dl = 0): its sin and cos from those of psi0 and of dl (Maclaurin
+    // series while |dl| < 1e-2, where their next terms are below 1e-21)
     double sp = sn, cp = cs;
-    if constexpr (N != 3) sincos(psi, &sp, &cp);
+    if constexpr (N != 3) {
+        const double dl = (xs[1] - xs[0]) * ids[1] - dk * 0.5 * ds[1];
+        double sd, cd;
+        if (fabs(dl) < 1e-2) {
+            const double d2 = dl * dl;
+            sd = dl * (1.0 - d2 * (1.0 / 6.0) * (1.0 - d2 * (1.0 / 20.0) * (1.0 - d2 * (1.0 / 42.0))));
+            cd = 1.0 - d2 * 0.5 * (1.0 - d2 * (1.0 / 12.0) * (1.0 - d2 * (1.0 / 30.0) * (1.0 - d2 * (1.0 / 56.0))));
+        } else {
+            sincos(dl, &sd, &cd);
+        }
+        sp = sn * cd + cs * sd;
+        cp = cs * cd - sn * sd;
+    }
     const double Xo = -(px * cp + py * sp), Yo = px * sp - py * cp;
     const double U = kf * (Xo * Xo + Yo * Yo) - 2.0 * Yo;
     const double q1 = 1.0 + kf * U;
