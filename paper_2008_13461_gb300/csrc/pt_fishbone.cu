@@ -92,6 +92,19 @@ __device__ __forceinline__ bool fb_kills(const Params &p, int64_t b, int j, cons
     return l2 < l1 || (l2 == l1 && p.perm[p.cell_inner[b + d]] < p.perm[p.cell_inner[b + j]]);
 }
 
+// Warp-wide minimum, maximum and sum with one redux instruction each.  The
+// float map keeps their order (non-negative floats keep their bits,
+// negative ones have the magnitude bits flipped; no NaN reaches it), and a
+// minimum or maximum is one of the inputs, so nothing is rounded.
+__device__ __forceinline__ int ford(float f) {
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float fval(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+__device__ __forceinline__ float warp_min(float f) { return fval(__reduce_min_sync(0xffffffffu, ford(f))); }
+__device__ __forceinline__ float warp_max(float f) { return fval(__reduce_max_sync(0xffffffffu, ford(f))); }
+__device__ __forceinline__ int warp_sum(int v) { return __reduce_add_sync(0xffffffffu, v); }
+
 // exclusive prefix sum of a[0, nb) in place (nb a power of two >= 32;
 // one warp, nb / 32 entries per lane)
 __device__ __forceinline__ void warp_exclusive_scan(int *a, int nb, int lane) {
@@ -164,11 +177,8 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
             bmax = fmaxf(bmax, key);
         }
     }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        k2max = fmaxf(k2max, __shfl_xor_sync(0xffffffffu, k2max, d));
-        gmin = fminf(gmin, __shfl_xor_sync(0xffffffffu, gmin, d));
-    }
+    k2max = warp_max(k2max);
+    gmin = warp_min(gmin);
     const float kmax = sqrtf(1.0f + k2max);        // max of sqrt(1 + key^2)
     if (lane == 0 && starts) reinterpret_cast<float2 *>(p.hk + o)[0] = make_float2(kmax, gmin);
     __syncwarp();
@@ -209,11 +219,8 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
             if (dead) sm.dead[w][j] = 1;
         }
     } else {
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            bmin = fminf(bmin, __shfl_xor_sync(0xffffffffu, bmin, d));
-            bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, d));
-        }
+        bmin = warp_min(bmin);
+        bmax = warp_max(bmax);
         // counting sort of the cells into buckets of (inner layer, direction
         // key): each inner layer of o has its own aligned range of nbr
         // buckets (about one bucket per cell), so a cell meets only siblings
@@ -280,9 +287,7 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
             if (dead && in_smem) p.cell_alive[b + j] = 0;
             alive += !dead;
         }
-        nl = alive;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) nl += __shfl_xor_sync(0xffffffffu, nl, d);
+        nl = warp_sum(alive);
         if (lane == 0) p.in_live[o] = nl;
     } else if (in_smem) {
         // slope key and inner hit of each live cell (the records are free)
@@ -301,13 +306,9 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
             }
             alive++;
         }
-        int nl = alive;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            nl += __shfl_xor_sync(0xffffffffu, nl, d);
-            smin = fminf(smin, __shfl_xor_sync(0xffffffffu, smin, d));
-            smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, d));
-        }
+        const int nl = warp_sum(alive);
+        smin = warp_min(smin);
+        smax = warp_max(smax);
         // counting sort into about one bucket per cell; the connection
         // searches by bucket, so the order inside a bucket is free
         const int nb = sk_buckets(nl);
@@ -357,13 +358,9 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
             }
             alive++;
         }
-        int nl = alive;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            nl += __shfl_xor_sync(0xffffffffu, nl, d);
-            smin = fminf(smin, __shfl_xor_sync(0xffffffffu, smin, d));
-            smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, d));
-        }
+        const int nl = warp_sum(alive);
+        smin = warp_min(smin);
+        smax = warp_max(smax);
         const float span = fmaxf(smax - smin, fmaxf(fabsf(smin), fabsf(smax)) * 1e-6f);
         const float iw = span > 0.f && span <= 3.4e38f ? (float)sk_buckets(nl) / span : 0.f;
         if (lane == 0) {
@@ -382,8 +379,7 @@ __device__ __forceinline__ void list_pending(const Params &p, int o, int lane) {
 }
 
 __device__ __forceinline__ void add_alive(const Params &p, int v) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    v = warp_sum(v);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(p.counters + C_ALIVE_CELLS, v);
 }
 
