@@ -80,7 +80,7 @@ struct Params {
     float4 *hk;                          // per hit: max sqrt(1+key^2) and min gap of its incoming
                                          //   cells; lowest key and inverse bucket width of the live ones
     int32_t *in_live;                    // per hit: live incoming cells
-    float2 *sk;                          // live incoming cells of each hit sorted by slope key:
+    float2 *sk;                          // live incoming cells of each hit by slope-key bucket:
     int32_t *sci;                        //   (key, inner hit as int bits) and the cell index
     uint8_t *has_out;
     int32_t *maxlen;

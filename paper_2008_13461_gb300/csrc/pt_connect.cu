@@ -113,8 +113,9 @@ __device__ __forceinline__ int lower_bucket(const float2 *s, int n, int bk, floa
     return l;
 }
 
-// Every inner cell (a,b) connecting to the live cell x = (b,c), in key
-// order: emit(t, i) for the t-th one, i its index in the sorted arrays.
+// Every inner cell (a,b) connecting to the live cell x = (b,c), in the
+// order of b's bucket-ordered arrays: emit(t, i) for the t-th one, i its
+// index there.
 // Returns their number, or -2 (kExact = false) when a candidate is
 // undecided.
 template <bool kExact, class Emit>

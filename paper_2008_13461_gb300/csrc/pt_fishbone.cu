@@ -275,10 +275,10 @@ __device__ __forceinline__ int fishbone_hit(const Params &p, int o, int n, int64
     __syncwarp();
     if (!kExact && __any_sync(0xffffffffu, und)) return -1;
 
-    // pass 2: the live cells, sorted by slope key for the CA connection.  A
-    // hit on a layer that is the inner layer of no pair starts no cell, so
-    // the connection never searches the cells ending on it: only their
-    // Fishbone verdicts are written.
+    // pass 2: the live cells, grouped by slope-key bucket for the CA
+    // connection.  A hit on a layer that is the inner layer of no pair
+    // starts no cell, so the connection never searches the cells ending on
+    // it: only their Fishbone verdicts are written.
     int alive = 0;
     if (!starts) {
         int nl = 0;
