@@ -170,17 +170,53 @@ __device__ __forceinline__ double member_sumpt2(const VtxArgs &a, const int32_t 
     return warp_sum(s);
 }
 
-// ascending bitonic sort of P entries (P a power of two) under gt
-template <class Gt, class Swap>
-__device__ __forceinline__ void bitonic(int P, Gt gt, Swap swap) {
-    for (int k = 2; k <= P; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
+// sort elements: (z0, track index) in order of both, or plain int keys
+struct ZId {
+    float z;
+    int id;
+};
+__device__ __forceinline__ bool elem_gt(const ZId &a, const ZId &b) { return a.z > b.z || (a.z == b.z && a.id > b.id); }
+__device__ __forceinline__ bool elem_gt(int a, int b) { return a > b; }
+__device__ __forceinline__ ZId elem_shfl_xor(const ZId &e, int j) {
+    return {__shfl_xor_sync(0xffffffffu, e.z, j), __shfl_xor_sync(0xffffffffu, e.id, j)};
+}
+__device__ __forceinline__ int elem_shfl_xor(int e, int j) { return __shfl_xor_sync(0xffffffffu, e, j); }
+
+// Ascending bitonic sort of P entries (P a power of two, at least 32; the
+// block a multiple of 32 threads).  Position p is handled by thread p mod
+// blockDim, so the partners of the stages at distance 16 or less are lanes
+// of one warp: those stages of each merge run in registers with shuffles,
+// one barrier per merge instead of one per stage.
+template <class E, class Load, class Store>
+__device__ __forceinline__ void bitonic(int P, Load load, Store store) {
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j >= 32; j >>= 1) {
             for (int p = threadIdx.x; p < P; p += blockDim.x) {
                 const int q = p ^ j;
-                if (q > p && gt(p, q) == ((p & k) == 0)) swap(p, q);
+                if (q > p) {
+                    const E a = load(p), b = load(q);
+                    if (elem_gt(a, b) == ((p & k) == 0)) {
+                        store(p, b);
+                        store(q, a);
+                    }
+                }
             }
             __syncthreads();
         }
+        // whole warps take part: P and blockDim are multiples of 32
+        for (int p = threadIdx.x; p < P; p += blockDim.x) {
+            E e = load(p);
+            const bool up = (p & k) == 0;
+            for (int j = min(k >> 1, 16); j > 0; j >>= 1) {
+                const E o = elem_shfl_xor(e, j);
+                // the lower of a pair keeps the smaller entry in an ascending
+                // run and the larger in a descending one
+                if (((p & j) == 0) == up ? elem_gt(e, o) : elem_gt(o, e)) e = o;
+            }
+            store(p, e);
+        }
+        __syncthreads();
+    }
 }
 
 // Per event: sort, densities, links, roots, candidates (one block).
@@ -202,7 +238,7 @@ __global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_group(VtxArgs a) {
         return;
     }
     if (tid == 0) s_nc = 0;
-    int P = 1;
+    int P = 32;
     while (P < cnt) P <<= 1;
     for (int p = tid; p < P; p += blockDim.x) {
         if (p < cnt) {
@@ -215,15 +251,11 @@ __global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_group(VtxArgs a) {
         }
     }
     __syncthreads();
-    bitonic(
-        P, [&](int p, int q) { return sz[p] > sz[q] || (sz[p] == sz[q] && sid[p] > sid[q]); },
-        [&](int p, int q) {
-            const float t = sz[p];
-            sz[p] = sz[q];
-            sz[q] = t;
-            const int u = sid[p];
-            sid[p] = sid[q];
-            sid[q] = u;
+    bitonic<ZId>(
+        P, [&](int p) { return ZId{sz[p], sid[p]}; },
+        [&](int p, const ZId &e) {
+            sz[p] = e.z;
+            sid[p] = e.id;
         });
 
     const float dzc = a.cuts.dz_cut, c2m = a.cuts.chi2_max;
@@ -302,13 +334,8 @@ __global__ void __launch_bounds__(kVtxThreads, 1) k_vtx_group(VtxArgs a) {
     // group the tracks by root: sort the (root, position) keys
     for (int p = tid; p < P; p += blockDim.x) key[p] = p < cnt ? (root[p] << kPosBits | p) : 0x7fffffff;
     __syncthreads();
-    bitonic(
-        P, [&](int p, int q) { return key[p] > key[q]; },
-        [&](int p, int q) {
-            const int t = key[p];
-            key[p] = key[q];
-            key[q] = t;
-        });
+    bitonic<int>(
+        P, [&](int p) { return key[p]; }, [&](int p, int e) { key[p] = e; });
     // candidates: groups whose root has rho > 1 and at least min_tracks tracks
     for (int q = tid; q < cnt; q += blockDim.x) {
         const int r = key[q] >> kPosBits;
