@@ -758,7 +758,10 @@ def run_native(args, rank, world, local_rank):
     fit_roofline = {"bound": "alu", "kernel": "k_fit<3..8>", "unit": "TFLOP/s", "precision": "f64",
                     "peak": alu["fp64_tflops"], "peak_source": alu["method"], "fp32_peak": alu["fp32_tflops"],
                     "algorithmic_flops": fit_flops, "ms": fit_ms,
-                    "flops_source": "the method's dense-algebra count per track (bench.fit_flops_per_track)"}
+                    "flops_source": "the method's dense-algebra count per track (bench.fit_flops_per_track)",
+                    "note": "the closed-form triplet and quadruplet fits and the float32 covariance transform "
+                            "execute fewer float64 operations than this count, so the method's rate can pass "
+                            "the pipe's peak; the pipe itself is bound (ncu: float64 pipe busy)"}
     if fit_ms > 0:
         fit_roofline["achieved"] = fit_flops / (fit_ms * 1e-3) / 1e12
         fit_roofline["frac"] = fit_roofline["achieved"] / alu["fp64_tflops"]
