@@ -211,7 +211,10 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
     // Three hits: one kink per plane.  A = diag(wz) + vg_1 g g^T is
     // inverted by Sherman-Morrison; B = wu diag(1, 1, 1, 0) + vb_1 h h^T has
     // the explicit inverse [[I, a], [a^T, |a|^2 + var_1 wu / h3^2]] / wu with
-    // a = -(h0, h1, h2) / h3.  Otherwise Cholesky.
+    // a = -(h0, h1, h2) / h3.  Four hits: two kinks per plane; A^-1 by
+    // Woodbury (a 2 x 2 system), B^-1 through the Schur complement of its
+    // curvature entry, a rank-one update of wu I (the forward fit's closed
+    // forms).  Otherwise Cholesky.
     auto solve_line = [&](double *yv) {
         if constexpr (N == 3) {
             const double g0 = ids[1], g2 = ids[2], g1 = -(g0 + g2);
@@ -222,11 +225,27 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
             yv[0] = w0 - r0 * g0 * f;
             yv[1] = w1 - r1 * g1 * f;
             yv[2] = w2 - r2 * g2 * f;
+        } else if constexpr (N == 4) {
+            // A^-1 y = w - D^-1 G^T S^-1 G w, w = D^-1 y, S = diag(var_k) + G D^-1 G^T
+            const double a0 = ids[1], a2 = ids[2], a1 = -(a0 + a2);      // kink 1 on 0, 1, 2
+            const double b0 = ids[2], b2 = ids[3], b1 = -(b0 + b2);      // kink 2 on 1, 2, 3
+            const double kz1 = fmax(th[1] * th[1] * sec2 * sec2, 1e-20), kz2 = fmax(th[2] * th[2] * sec2 * sec2, 1e-20);
+            const double w0 = vz[0] * yv[0], w1 = vz[1] * yv[1], w2 = vz[2] * yv[2], w3 = vz[3] * yv[3];
+            const double S11 = kz1 + a0 * a0 * vz[0] + a1 * a1 * vz[1] + a2 * a2 * vz[2];
+            const double S22 = kz2 + b0 * b0 * vz[1] + b1 * b1 * vz[2] + b2 * b2 * vz[3];
+            const double S12 = a1 * b0 * vz[1] + a2 * b1 * vz[2];
+            const double q1 = a0 * w0 + a1 * w1 + a2 * w2, q2 = b0 * w1 + b1 * w2 + b2 * w3;
+            const double idet = rcp_d(S11 * S22 - S12 * S12);
+            const double r1 = (S22 * q1 - S12 * q2) * idet, r2 = (S11 * q2 - S12 * q1) * idet;
+            yv[0] = w0 - vz[0] * a0 * r1;
+            yv[1] = w1 - vz[1] * (a1 * r1 + b0 * r2);
+            yv[2] = w2 - vz[2] * (a2 * r1 + b1 * r2);
+            yv[3] = w3 - vz[3] * b2 * r2;
         } else {
             solve_d<N>(A, yv);
         }
     };
-    if constexpr (N != 3) chol_d<N>(A);
+    if constexpr (N > 4) chol_d<N>(A);
     solve_line(v);
     // 4) circle fit: B x = b, x = (u_0 .. u_{n-1}, dk).  Three hits: the
     // pre-fit circle passes through all of them, so the offsets m are zero
@@ -262,12 +281,35 @@ __device__ void grad_track(const Params &p, int32_t t, const float *gp, float gc
             yv[1] = s2 * (yv[1] + a1 * y3);
             yv[2] = s2 * (yv[2] + a2 * y3);
             yv[3] = s2 * ay + (s2 * (a0 * a0 + a1 * a1 + a2 * a2) + kv * ih3 * ih3) * y3;
+        } else if constexpr (N == 4) {
+            // B = [[S0, A12], [A12^T, C]] over (u, dk); with t = -A12 / C the
+            // Schur complement S = S0 - A12 A12^T / C = wu I + w' c c^T (c =
+            // H^T (h3_2, -h3_1), w' = 1 / (h3_1^2 var_2 + h3_2^2 var_1)), so
+            // B^-1 (y, yd) = (S^-1 (y + t yd), t . S^-1 (y + t yd) + yd / C).
+            const double h0 = ids[1], h2 = ids[2], h1 = -(h0 + h2);      // kink 1 on u0, u1, u2
+            const double k0 = ids[2], k2 = ids[3], k1 = -(k0 + k2);      // kink 2 on u1, u2, u3
+            const double g1 = -0.5 * (ds[1] + ds[2]), g2 = -0.5 * (ds[2] + ds[3]);
+            const double kv1 = fmax(th[1] * th[1] * sec2, 1e-20), kv2 = fmax(th[2] * th[2] * sec2, 1e-20);
+            const double wp = rcp_d(g1 * g1 * kv2 + g2 * g2 * kv1);
+            const double c0 = g2 * h0, c1 = g2 * h1 - g1 * k0, c2 = g2 * h2 - g1 * k1, c3 = -g1 * k2;
+            const double p1 = g1 * kv2 * wp, p2 = g2 * kv1 * wp;
+            const double t0 = -p1 * h0, t1 = -(p1 * h1 + p2 * k0), t2 = -(p1 * h2 + p2 * k1), t3 = -p2 * k2;
+            const double yd = yv[4];
+            const double e0 = yv[0] + t0 * yd, e1 = yv[1] + t1 * yd, e2 = yv[2] + t2 * yd, e3 = yv[3] + t3 * yd;
+            const double iwu = rcp_d(wu);
+            const double f = wp * (c0 * e0 + c1 * e1 + c2 * e2 + c3 * e3) *
+                             rcp_d(wu + wp * (c0 * c0 + c1 * c1 + c2 * c2 + c3 * c3));
+            yv[0] = (e0 - f * c0) * iwu;
+            yv[1] = (e1 - f * c1) * iwu;
+            yv[2] = (e2 - f * c2) * iwu;
+            yv[3] = (e3 - f * c3) * iwu;
+            yv[4] = t0 * yv[0] + t1 * yv[1] + t2 * yv[2] + t3 * yv[3] + yd * kv1 * kv2 * wp;
         } else {
             solve_d<M>(B, yv);
         }
     };
     if constexpr (N != 3) {
-        chol_d<M>(B);
+        if constexpr (N > 4) chol_d<M>(B);
         solve_circle(xs);
     } else {
 #pragma unroll
